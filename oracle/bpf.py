@@ -1,0 +1,173 @@
+"""FP64 bootstrap particle filter with butterfly (mixed-radix) interaction.
+
+Algorithm 1 (particle filter) with its Resample step replaced by ONE stage of
+Algorithm 3 (augmented resampling) per time step: at step n the stage matrix
+is A_k with k = n mod m (digit k of the mixed-radix particle index), and the
+stage weights V carry over to the next step, where they multiply the next
+potential g_n.  This is the paper's "rotate the starting stage" idea
+(Section 6.4) with the weight recursion V_s = A_s V_{s-1} of eq.
+(V_defn_proofs), a reading this library takes for its one-digit-per-step
+schedule.  With one digit (radices = (N,)) it is Algorithm 1 + Algorithm 2,
+the textbook BPF.
+
+Notation: zeta_n = prediction particles (N x d), lV = log V (carried stage
+weights, constant on the groups of the previous digit), g_n = g(., y_n).
+All arithmetic is float64 except the integer draw, whose quantisation is
+taken in FP32 (see ``resample``).
+
+Carried-weight normalisation (bookkeeping of this library, not in the paper):
+the step subtracts a scalar mu_n from every log-weight so lV stays O(1);
+mu_{n+1} = log(N^-1 sum_i exp(lw_i)).  The observation density's
+state-independent constant c_n (e.g. -1/2 log|2 pi R|) is left out of the
+log-weights and added to the likelihood increment only.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+from typing import Dict, Optional, Sequence
+
+import numpy as np
+
+from . import philox, resample
+from .butterfly import strides
+
+
+@dataclass
+class State:
+    x: np.ndarray            # (N, d) prediction particles zeta_n
+    lV: np.ndarray           # (N,) log carried weights (per particle)
+    mu: float                # carried normaliser mu_n
+    n: int                   # time index of the next observation
+    loglik: float = 0.0      # log p^(y_0..y_{n-1})
+
+
+def obs_terms(model, x: np.ndarray, y: np.ndarray):
+    """log g(x, y) split as (state-dependent part s(x) (N,), constant c).
+
+    Linear-Gaussian: g = N(y; Hx, Lr Lr^T)
+        s(x) = -1/2 || Lr^{-1} (y - H x) ||^2,  c = -sum log diag(Lr) - dy/2 log(2 pi).
+    Stochastic volatility: y = beta exp(x/2) w, w ~ N(0, 1)
+        s(x) = -x/2 - y^2 exp(-x) / (2 beta^2),  c = -1/2 log(2 pi beta^2).
+    """
+    if model.kind == "lg":
+        resid = y[None, :] - x @ model.H.T                            # (N, dy)
+        z = np.linalg.solve(model.Lr, resid.T).T                      # Lr z = resid
+        s = -0.5 * np.sum(z * z, axis=1)
+        c = -np.sum(np.log(np.abs(np.diag(model.Lr)))) - 0.5 * model.dy * np.log(2 * np.pi)
+        return s, c
+    if model.kind == "sv":
+        xx = x[:, 0]
+        yy = float(y[0])
+        s = -0.5 * xx - yy * yy * np.exp(-xx) / (2.0 * model.beta ** 2)
+        c = -0.5 * np.log(2 * np.pi * model.beta ** 2)
+        return s, c
+    raise ValueError(model.kind)
+
+
+def initial_particles(model, N: int, seed: int) -> np.ndarray:
+    """Algorithm 1, first loop: zeta_0^i ~ pi_0 (i.i.d.)."""
+    d = model.d
+    eps = philox.normals(seed, 0, philox.PURPOSE_INIT, N * d).reshape(N, d)
+    if model.kind == "lg":
+        return model.m0[None, :] + eps @ model.L0.T
+    sd0 = model.sigma / np.sqrt(1.0 - model.phi ** 2)
+    return sd0 * eps
+
+
+def mutate(model, xhat: np.ndarray, n: int, seed: int) -> np.ndarray:
+    """Algorithm 1, mutation: zeta_{n+1}^i ~ f(zeta_hat_n^i, .)."""
+    N, d = xhat.shape
+    eps = philox.normals(seed, n, philox.PURPOSE_PROPAGATE, N * d).reshape(N, d)
+    if model.kind == "lg":
+        return xhat @ model.A.T + eps @ model.Lq.T
+    return model.phi * xhat + model.sigma * eps
+
+
+def init_state(model, N: int, seed: int) -> State:
+    return State(x=initial_particles(model, N, seed), lV=np.zeros(N), mu=0.0, n=0)
+
+
+def _log_mean_exp(v: np.ndarray) -> float:
+    m = np.max(v)
+    return float(m + np.log(np.mean(np.exp(v - m))))
+
+
+def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
+         mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
+    """One time step n = st.n: weight, one augmented-resampling stage, mutate.
+
+    ``mu_used`` (lockstep parity only) is the normaliser the caller's filter
+    actually subtracted; the likelihood increment corrects for it.
+    """
+    radices = [int(a) for a in radices]
+    N, d = st.x.shape
+    m = len(radices)
+    n = st.n
+    k = n % m
+    a = radices[k]
+    s_k = strides(radices)[k]
+    Hh = N // (a * s_k)
+    mu_sub = st.mu if mu_used is None else float(mu_used)
+
+    # V_{s-1}^j g_n(zeta^j), in logs: lw_j = log V_j + s(zeta_j) - mu    (Algorithm 3, V_0 = g)
+    s_x, c_n = obs_terms(model, st.x, np.asarray(y_n, dtype=np.float64))
+    lw = st.lV + s_x - mu_sub
+    lw = np.where(np.isfinite(lw), lw, -np.inf)
+
+    # Group view (h, r, l): digit k is the middle axis.
+    lwg = lw.reshape(Hh, a, s_k)
+    # V_s^i = sum_j A^{ij} V_{s-1}^j = (1/a) sum_{j in G(i)} V_{s-1}^j   (eq. V_defn_proofs)
+    Mg = np.max(lwg, axis=1, keepdims=True)
+    Lg = Mg + np.log(np.sum(np.exp(lwg - Mg), axis=1, keepdims=True))
+    lV_new = np.broadcast_to(Lg - np.log(a), lwg.shape).reshape(N).copy()
+
+    # xi_s^i ~ (V_s^i)^{-1} sum_j A^{ij} V_{s-1}^j delta_{xi_{s-1}^j}   (integer rule)
+    q = resample.quantise(lwg, axis=1)
+    Q = np.sum(q, axis=1, keepdims=True, dtype=np.uint64)
+    if a <= resample.NARROW_MAX_RADIX:
+        r = philox.resample_words(seed, n, N).reshape(Hh, a, s_k)
+        u = resample.scaled_uniform(r, Q, a)
+    else:
+        lo, hi = philox.resample_words_wide(seed, n, N)
+        u = resample.scaled_uniform(lo.reshape(Hh, a, s_k), Q, a, hi.reshape(Hh, a, s_k))
+    member = resample.draw(q, u, axis=1)                                  # (Hh, a, s_k)
+    h_idx = np.arange(Hh)[:, None, None]
+    l_idx = np.arange(s_k)[None, None, :]
+    anc = (h_idx * (a * s_k) + member * s_k + l_idx).reshape(N)
+
+    # Likelihood increment, filter mean and ESS (Section 1.2) from the weighted particles.
+    lme = _log_mean_exp(lw)
+    inc = lme + c_n + (mu_sub - st.mu)
+    w = np.exp(lw - np.max(lw))
+    mean = (w @ st.x) / np.sum(w)
+    ess = float(np.sum(w) ** 2 / (N * np.sum(w * w)))
+
+    x_next = mutate(model, st.x[anc], n, seed)
+    new = State(x=x_next, lV=lV_new, mu=lme, n=n + 1, loglik=st.loglik + inc)
+    out = dict(k=k, a=a, stride=s_k, anc=anc, lw=lw, q=q.reshape(N), u=u.reshape(N),
+               Q=np.broadcast_to(Q, q.shape).reshape(N), inc=inc, mean=mean, ess=ess,
+               lV_new=lV_new, c=c_n)
+    return new, out
+
+
+def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
+        keep_ancestors: bool = False) -> Dict[str, np.ndarray]:
+    """Run the filter over y[0:T].  Returns per-step inc, mean, ess and the final loglik."""
+    if int(np.prod(radices)) != N:
+        raise ValueError("product of radices must equal N")
+    y = np.asarray(y, dtype=np.float64).reshape(len(y), -1)
+    T = y.shape[0]
+    st = init_state(model, N, seed)
+    incs = np.empty(T)
+    means = np.empty((T, model.d))
+    ess = np.empty(T)
+    ancs = [] if keep_ancestors else None
+    for t in range(T):
+        st, o = step(model, radices, seed, st, y[t])
+        incs[t], means[t], ess[t] = o["inc"], o["mean"], o["ess"]
+        if keep_ancestors:
+            ancs.append(o["anc"])
+    out = dict(inc=incs, mean=means, ess=ess, loglik=st.loglik, state=st)
+    if keep_ancestors:
+        out["anc"] = np.stack(ancs)
+    return out
