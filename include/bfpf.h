@@ -1,0 +1,206 @@
+/*
+ * bfpf.h - C ABI of the butterfly-interaction bootstrap particle filter.
+ *
+ * The filter is the one of Heine, Whiteley & Cemgil, "Parallelising particle
+ * filters with butterfly interactions" (arXiv 1812.01502): Algorithm 1
+ * (bootstrap particle filter) whose resampling step is one stage of
+ * Algorithm 3 (augmented resampling) per time step.  Particle indices
+ * 0..N-1 are read in mixed radix N = a_0 a_1 ... a_{m-1} (digit 0 least
+ * significant); at time step n the particles resample only inside groups
+ * that share every digit except digit k = n mod m, i.e. the stage matrix is
+ * A_k = I (x) 1_{1/a_k} (x) I (eq. (A matrices) of Section 1.2 generalised to
+ * mixed radix, as the Remark after Lemma 3 allows), and the stage weights
+ * V_k = A_k V_{k-1} carry into the next time step.
+ *
+ * Conventions (all entry points):
+ *  - Every function returns a pf_status; PF_OK is 0.  On failure the handle
+ *    (or, for calls without a handle, the calling thread) records a message
+ *    that pf_last_error() returns.  No entry point aborts the process.
+ *  - All device work is enqueued on the handle's CUDA stream and is
+ *    asynchronous, except where an output goes to host memory or the
+ *    description says "synchronises".
+ *  - A handle is not thread-safe; use one handle per host thread or lock.
+ *  - There is no CPU fallback: without a usable CUDA device every call that
+ *    needs one returns PF_ECUDA.
+ *  - Pointers documented "host or device" are copied with cudaMemcpyDefault
+ *    (unified virtual addressing); device pointers must belong to the
+ *    handle's device.
+ */
+#ifndef BFPF_H
+#define BFPF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PF_OK = 0,
+    PF_EINVAL = 1,    /* invalid argument: sizes, radices, model, null pointers   */
+    PF_ENOMEM = 2,    /* workspace too small or device allocation failed          */
+    PF_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error)   */
+    PF_ETIMEOUT = 4,  /* a bounded device-side wait gave up                        */
+    PF_ESTATE = 5     /* call not valid in the handle's current state              */
+} pf_status;
+
+typedef enum {
+    PF_MODEL_LINEAR_GAUSSIAN = 1,
+    PF_MODEL_STOCH_VOL = 2
+} pf_model_kind;
+
+/*
+ * The hidden Markov model of Section 1.1 (eq. (HMM)):
+ *   X_0 ~ pi_0,  X_n | X_{n-1} ~ f(X_{n-1}, .),  Y_n | X_n ~ g(X_n, .),  n >= 0.
+ *
+ * PF_MODEL_LINEAR_GAUSSIAN:
+ *   pi_0 = N(m0, L0 L0^T);  X_n = A X_{n-1} + Lq eps_n;  Y_n = H X_n + Lr w_n,
+ *   eps, w standard normal.  d = state dimension (1..8), dy = observation
+ *   dimension (1..8).  Matrices are row-major double arrays that the library
+ *   copies at pf_create (the caller keeps ownership): A d*d, Lq d*d lower
+ *   triangular, H dy*d, Lr dy*dy lower triangular with nonzero diagonal,
+ *   m0 d, L0 d*d lower triangular.  NULL means identity (zero for m0; H = NULL
+ *   needs dy == d).  (Section 6.1's experiment: A = Lq = H = L0 = I,
+ *   Lr = I/2, m0 = 0.)
+ * PF_MODEL_STOCH_VOL (d = dy = 1):
+ *   pi_0 = N(0, sigma^2/(1-phi^2));  X_n = phi X_{n-1} + sigma v_n;
+ *   Y_n = beta exp(X_n/2) w_n;  requires |phi| < 1, sigma > 0, beta > 0.
+ */
+typedef struct {
+    int32_t kind;         /* pf_model_kind */
+    int32_t d;
+    int32_t dy;
+    const double* A;
+    const double* Lq;
+    const double* H;
+    const double* Lr;
+    const double* m0;
+    const double* L0;
+    double phi, sigma, beta;
+} pf_model;
+
+/* pf_options.flags */
+#define PF_RECORD_ANCESTORS 1u   /* keep the ancestor index of every particle of the last step */
+
+typedef struct {
+    int32_t tile;        /* target particles per thread-block tile; 0 = automatic            */
+    int32_t chunk_len;   /* time steps per CUDA-graph replay in pf_run; 0 = 64 (max 1024)    */
+    uint32_t flags;      /* PF_RECORD_ANCESTORS                                              */
+    int32_t grid;        /* persistent thread blocks; 0 = automatic (SMs x occupancy)        */
+    void* stream;        /* cudaStream_t to run on; NULL = the legacy default stream          */
+} pf_options;
+
+typedef struct pf_handle pf_handle;
+
+/*
+ * Device workspace needed by pf_create for this problem: particle states
+ * (4*d*N bytes), carried log-weights (2 * 4N/min(a) bytes), optional
+ * ancestors (4N), per-block partial sums and small rings for observations
+ * and per-step outputs.  opts may be NULL.
+ * Errors: PF_EINVAL (bad model / N / radices, see pf_create).
+ */
+pf_status pf_workspace_size(const pf_model* model, int64_t N, const int32_t* radices,
+                            int32_t m, const pf_options* opts, size_t* bytes);
+
+/*
+ * Create a filter for `model` with N = radices[0] * ... * radices[m-1]
+ * particles (Assumption A1 of the paper with paper-m = N / M generalised to
+ * mixed radix).  Every radix must be >= 2 and <= 1024, except that m == 1
+ * (radices = {N}: the global-resampling bootstrap filter of Algorithm 2) allows
+ * any N.  N < 2^31.  `seed` keys the counter-based random stream (Philox4x32-10),
+ * so a run is reproducible given (model, N, radices, seed, observations).
+ *
+ * workspace: device memory of at least pf_workspace_size() bytes, 256-byte
+ *   aligned, owned by the caller, who must keep it alive until pf_destroy; or
+ *   NULL, in which case the library allocates (cudaMalloc) and frees its own.
+ * Draws pi_0 (Algorithm 1, first loop) on the stream before returning.
+ * Errors: PF_EINVAL, PF_ENOMEM (workspace_bytes too small / allocation
+ *   failed), PF_ECUDA.  On error *out is set to NULL.
+ */
+pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, int32_t m,
+                    uint64_t seed, const pf_options* opts, void* workspace,
+                    size_t workspace_bytes, pf_handle** out);
+
+/*
+ * One time step n (n = number of steps taken so far): weight the particles
+ * with g(., y_n), run one augmented-resampling stage on digit n mod m, and
+ * mutate (Algorithm 1 loop body).  y_n: dy floats, host or device.
+ * Optional outputs (NULL to skip; host or device): mean_out (d floats) = the
+ * weighted filtering mean estimate of E[X_n | y_0..y_n]; loglik_inc (1
+ * double) = log p^(y_n | y_0..y_{n-1}); ess_out (1 float) = the effective
+ * sample size fraction of Section 1.2 computed from the carried weights.
+ * Host outputs synchronise the stream.
+ */
+pf_status pf_step(pf_handle* h, const float* y_n, float* mean_out, double* loglik_inc,
+                  float* ess_out);
+
+/*
+ * T time steps over y (T x dy floats, row-major, host or device), in chunks
+ * of opts.chunk_len steps replayed from a captured CUDA graph.  Optional
+ * per-step outputs (NULL to skip; host or device): means (T x d floats),
+ * loglik_incs (T doubles), ess (T floats).  Host outputs synchronise.
+ */
+pf_status pf_run(pf_handle* h, const float* y, int32_t T, float* means, double* loglik_incs,
+                 float* ess);
+
+/*
+ * Streaming form of pf_run, for callers that feed observations as they arrive:
+ * pf_push_observations copies T observations (T x dy floats, host or device)
+ * into the handle's device ring for the next T time steps not yet pushed; at
+ * most 1024 observations may be pushed ahead of the steps taken (else
+ * PF_ESTATE).  pf_advance then takes T time steps on pushed observations
+ * (fewer pushed than T: PF_ESTATE) and writes the optional per-step outputs
+ * exactly as pf_run does.  pf_advance with T = 1 is one kernel launch.
+ */
+pf_status pf_push_observations(pf_handle* h, const float* y, int32_t T);
+pf_status pf_advance(pf_handle* h, int32_t T, float* means, double* loglik_incs, float* ess);
+
+/* Cumulative log-likelihood estimate log p^(y_0..y_{n-1}) accumulated in
+ * FP64 across time.  Synchronises the stream. */
+pf_status pf_loglik(const pf_handle* h, double* out);
+
+/*
+ * Copy the filter state to host memory (synchronises; any pointer may be NULL):
+ *   x        N*d floats, state-major: x[t*N + i] = component t of particle i;
+ *   lV       N / a_{k'} floats: carried log stage weights, one per group of the
+ *            digit k' = (n-1) mod m used by the last step (all zero before the
+ *            first step), group index  (i / (a_{k'} s_{k'})) * s_{k'} + i % s_{k'},
+ *            s_{k'} = a_0 ... a_{k'-1};
+ *   scalars  4 doubles: { n, loglik, mu, mu_used }, where mu is the carried
+ *            normaliser subtracted from the log-weights at the next step (FP64)
+ *            and mu_used its FP32 value the kernels subtract.
+ */
+pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars);
+
+/* Ancestor (global particle index, int32) of every particle at the last step;
+ * needs PF_RECORD_ANCESTORS.  anc: N int32, host.  Synchronises. */
+pf_status pf_get_ancestors(const pf_handle* h, int32_t* anc);
+
+/* Sticky device-side status bits of the handle (0 = none): bit 0 = a
+ * non-finite log-weight was seen and treated as weight zero; bit 1 = a group
+ * had zero total weight and kept its particles.  Synchronises. */
+pf_status pf_get_status(const pf_handle* h, uint32_t* bits);
+
+/* Release the handle and, if the library allocated it, its workspace.
+ * Synchronises the stream.  NULL is accepted. */
+pf_status pf_destroy(pf_handle* h);
+
+/* Message for the last failed call on `h`, or on the calling thread when
+ * h is NULL.  Never NULL; valid until the next call on the same handle/thread. */
+const char* pf_last_error(const pf_handle* h);
+
+/*
+ * Philox4x32-10 blocks, for checking the device generator against an
+ * independent implementation: out[4*j + w] = word w of Philox4x32-10 with
+ * key (seed mod 2^32, seed div 2^32) and counter (c0 + j, c1, c2, c3),
+ * j = 0..count-1.  out: device pointer to 4*count uint32.  Runs on `stream`
+ * (cudaStream_t, may be NULL) and is asynchronous.
+ */
+pf_status pf_philox_blocks(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                           int64_t count, uint32_t* out, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFPF_H */

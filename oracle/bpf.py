@@ -74,10 +74,16 @@ def initial_particles(model, N: int, seed: int) -> np.ndarray:
     return sd0 * eps
 
 
-def mutate(model, xhat: np.ndarray, n: int, seed: int) -> np.ndarray:
-    """Algorithm 1, mutation: zeta_{n+1}^i ~ f(zeta_hat_n^i, .)."""
+def mutate(model, xhat: np.ndarray, n: int, seed: int, idx=None) -> np.ndarray:
+    """Algorithm 1, mutation: zeta_{n+1}^i ~ f(zeta_hat_n^i, .).
+
+    ``idx`` (optional) are the particle indices i of the rows of xhat; by default 0..N-1."""
     N, d = xhat.shape
-    eps = philox.normals(seed, n, philox.PURPOSE_PROPAGATE, N * d).reshape(N, d)
+    if idx is None:
+        eps = philox.normals(seed, n, philox.PURPOSE_PROPAGATE, N * d).reshape(N, d)
+    else:
+        nu = np.asarray(idx, dtype=np.int64)[:, None] * d + np.arange(d)[None, :]
+        eps = philox.normals_at(seed, n, philox.PURPOSE_PROPAGATE, nu.reshape(-1)).reshape(N, d)
     if model.kind == "lg":
         return xhat @ model.A.T + eps @ model.Lq.T
     return model.phi * xhat + model.sigma * eps
@@ -90,6 +96,27 @@ def init_state(model, N: int, seed: int) -> State:
 def _log_mean_exp(v: np.ndarray) -> float:
     m = np.max(v)
     return float(m + np.log(np.mean(np.exp(v - m))))
+
+
+def weigh(model, x: np.ndarray, lV: np.ndarray, mu_sub: float, y_n: np.ndarray):
+    """lw_i = log V_i + log g_n(zeta_i) - c_n - mu  (Algorithm 3, V_0 = g).  Returns (lw, c_n)."""
+    s_x, c_n = obs_terms(model, x, np.asarray(y_n, dtype=np.float64))
+    lw = lV + s_x - mu_sub
+    return np.where(np.isfinite(lw), lw, -np.inf), c_n
+
+
+def summaries(lw: np.ndarray, x: np.ndarray, c_n: float, mu_sub: float, mu: float):
+    """Likelihood increment, weighted filtering mean and ESS (Section 1.2) of weighted particles.
+
+    inc = log(sum_i V_i g_n(zeta_i) / sum_i V_i) with log(N^-1 sum V) = mu; returns
+    (inc, mean (d,), ess, lme) with lme = log(N^-1 sum_i exp(lw_i)) the next normaliser."""
+    N = len(lw)
+    lme = _log_mean_exp(lw)
+    inc = lme + c_n + (mu_sub - mu)
+    w = np.exp(lw - np.max(lw))
+    mean = (w @ x) / np.sum(w)
+    ess = float(np.sum(w) ** 2 / (N * np.sum(w * w)))
+    return inc, mean, ess, lme
 
 
 def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
@@ -110,9 +137,7 @@ def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
     mu_sub = st.mu if mu_used is None else float(mu_used)
 
     # V_{s-1}^j g_n(zeta^j), in logs: lw_j = log V_j + s(zeta_j) - mu    (Algorithm 3, V_0 = g)
-    s_x, c_n = obs_terms(model, st.x, np.asarray(y_n, dtype=np.float64))
-    lw = st.lV + s_x - mu_sub
-    lw = np.where(np.isfinite(lw), lw, -np.inf)
+    lw, c_n = weigh(model, st.x, st.lV, mu_sub, y_n)
 
     # Group view (h, r, l): digit k is the middle axis.
     lwg = lw.reshape(Hh, a, s_k)
@@ -136,11 +161,7 @@ def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
     anc = (h_idx * (a * s_k) + member * s_k + l_idx).reshape(N)
 
     # Likelihood increment, filter mean and ESS (Section 1.2) from the weighted particles.
-    lme = _log_mean_exp(lw)
-    inc = lme + c_n + (mu_sub - st.mu)
-    w = np.exp(lw - np.max(lw))
-    mean = (w @ st.x) / np.sum(w)
-    ess = float(np.sum(w) ** 2 / (N * np.sum(w * w)))
+    inc, mean, ess, lme = summaries(lw, st.x, c_n, mu_sub, st.mu)
 
     x_next = mutate(model, st.x[anc], n, seed)
     new = State(x=x_next, lV=lV_new, mu=lme, n=n + 1, loglik=st.loglik + inc)
@@ -171,3 +192,40 @@ def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
     if keep_ancestors:
         out["anc"] = np.stack(ancs)
     return out
+
+
+def step_on_groups(model, radices: Sequence[int], seed: int, n: int, x: np.ndarray, lV: np.ndarray,
+                   mu_used: float, y_n: np.ndarray, groups: np.ndarray) -> Dict[str, np.ndarray]:
+    """Step n (weight, one stage on digit k = n mod m, mutate) restricted to some groups.
+
+    Used to check full-size runs one group at a time.  x: (N, d) prediction
+    particles; lV: (N,) carried log weights; groups: (G, 2) array of (h, l), the
+    digits above and below k that name a group.  Returns per-member arrays of
+    shape (G, a): global index, lw, q, u, ancestor (global), and x_next (G, a, d),
+    lV_new (G,).
+    """
+    radices = [int(a) for a in radices]
+    m = len(radices)
+    k = n % m
+    a = radices[k]
+    s_k = strides(radices)[k]
+    d = x.shape[1]
+    groups = np.asarray(groups, dtype=np.int64)
+    idx = groups[:, :1] * (a * s_k) + np.arange(a)[None, :] * s_k + groups[:, 1:2]   # (G, a)
+    flat = idx.reshape(-1)
+    lw, _ = weigh(model, x[flat].astype(np.float64), lV[flat].astype(np.float64), mu_used, y_n)
+    lw = lw.reshape(idx.shape)
+    Mg = np.max(lw, axis=1, keepdims=True)
+    Lg = Mg + np.log(np.sum(np.exp(lw - Mg), axis=1, keepdims=True))
+    q = resample.quantise(lw, axis=1)
+    Q = np.sum(q, axis=1, keepdims=True, dtype=np.uint64)
+    if a <= resample.NARROW_MAX_RADIX:
+        u = resample.scaled_uniform(philox.resample_words_at(seed, n, flat).reshape(idx.shape), Q, a)
+    else:
+        lo, hi = philox.resample_words_wide_at(seed, n, flat)
+        u = resample.scaled_uniform(lo.reshape(idx.shape), Q, a, hi.reshape(idx.shape))
+    member = resample.draw(q, u, axis=1)
+    anc = groups[:, :1] * (a * s_k) + member * s_k + groups[:, 1:2]
+    x_next = mutate(model, x[anc.reshape(-1)].astype(np.float64), n, seed, idx=flat).reshape(idx.shape + (d,))
+    return dict(idx=idx, lw=lw, q=q, u=u, Q=np.broadcast_to(Q, q.shape), anc=anc, x_next=x_next,
+                lV_new=(Lg - np.log(a))[:, 0])

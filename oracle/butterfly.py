@@ -70,3 +70,11 @@ def section4_pairs(S: int, s: int):
             left.append(2 ** s * (i - 1) + (j - 1) + 1)
             right.append(2 ** s * (i - 1) + (j - 1) + 1 + 2 ** (s - 1))
     return list(zip(left, right))
+
+
+def group_index(i, radices: Sequence[int], k: int):
+    """Index of i's group among the N / a_k groups of digit k: (i // (a_k s_k)) * s_k + i % s_k."""
+    a = int(radices[k])
+    s = strides(radices)[k]
+    i = np.asarray(i, dtype=np.int64)
+    return (i // (a * s)) * s + i % s

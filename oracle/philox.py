@@ -112,3 +112,30 @@ def resample_words_wide(seed: int, n: int, N: int):
     lo = np.stack([w0, w2], axis=1).reshape(-1)[:N].astype(np.uint64)
     hi = np.stack([w1, w3], axis=1).reshape(-1)[:N].astype(np.uint64)
     return lo, hi
+
+
+def normals_at(seed: int, n: int, purpose: int, nu) -> np.ndarray:
+    """Normals number ``nu`` (any integer array) of stream (n, purpose), float64."""
+    nu = np.asarray(nu, dtype=np.uint64)
+    w0, w1, w2, w3 = philox4x32(nu >> np.uint64(2), n, purpose, 0, seed_key(seed))
+    z0, z1 = box_muller(w0, w1)
+    z2, z3 = box_muller(w2, w3)
+    pos = (nu & np.uint64(3)).astype(np.int64)
+    return np.choose(pos, [z0, z1, z2, z3])
+
+
+def resample_words_at(seed: int, n: int, idx) -> np.ndarray:
+    """32-bit resampling uniforms of particles ``idx`` (uint64 values < 2^32)."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    w = philox4x32(idx >> np.uint64(2), n, PURPOSE_RESAMPLE, 0, seed_key(seed))
+    return np.choose((idx & np.uint64(3)).astype(np.int64), w).astype(np.uint64)
+
+
+def resample_words_wide_at(seed: int, n: int, idx):
+    """64-bit resampling uniforms of particles ``idx`` as (lo, hi) uint64 arrays."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    w0, w1, w2, w3 = philox4x32(idx >> np.uint64(1), n, PURPOSE_RESAMPLE_WIDE, 0, seed_key(seed))
+    odd = (idx & np.uint64(1)).astype(bool)
+    lo = np.where(odd, w2, w0).astype(np.uint64)
+    hi = np.where(odd, w3, w1).astype(np.uint64)
+    return lo, hi

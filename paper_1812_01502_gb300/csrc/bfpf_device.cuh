@@ -1,0 +1,174 @@
+// bfpf_device.cuh - device-side building blocks of the butterfly particle filter.
+//
+// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), Box-Muller normals,
+// division by run-time invariant integers (Granlund & Montgomery, PLDI'94),
+// float-float compensated sums (Knuth's TwoSum), and the parameter blocks the
+// kernels receive.  The random-stream layout (which counter feeds which
+// draw) is a fixed convention of this library:
+//
+//   key = (seed mod 2^32, seed div 2^32)
+//   initial normals      counter (nu/4, 0, 0, 0),  nu = i*d + t
+//   propagation normals  counter (nu/4, n, 1, 0)   at time step n
+//   resampling uniforms  counter (i/4,  n, 2, 0)   word i%4         (groups of <= 256)
+//   wide uniforms        counter (i/2,  n, 3, 0)   words 2(i%2)+{0,1} (groups of > 256)
+//
+// Box-Muller pair (w0, w1) -> normals 4c, 4c+1 and (w2, w3) -> 4c+2, 4c+3 of
+// block c; u = (2*(w0>>9)+1) 2^-24 and v = (w1>>8) 2^-24 are exact FP32 values.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bfpf {
+
+constexpr int kMaxDigits = 32;
+constexpr int kMaxDim = 8;
+constexpr int kBlock = 256;
+constexpr uint32_t kNarrowMaxRadix = 256;   // groups up to this size use 24-bit weights, 32-bit draws
+constexpr uint32_t kMaxCtaRadix = 1024;     // largest group resampled inside one thread block
+constexpr uint32_t kRing = 1024;            // observation / per-step output ring length
+
+constexpr uint32_t kPurposeInit = 0;
+constexpr uint32_t kPurposePropagate = 1;
+constexpr uint32_t kPurposeResample = 2;
+constexpr uint32_t kPurposeResampleWide = 3;
+
+constexpr uint32_t kStatusNonFinite = 1u;
+constexpr uint32_t kStatusZeroGroup = 2u;
+
+enum ModelKind : int { kLinearGaussian = 1, kStochVol = 2 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    if (r) {
+      k0 += 0x9E3779B9u;
+      k1 += 0xBB67AE85u;
+    }
+    const uint64_t p0 = (uint64_t)c.x * 0xD2511F53u;
+    const uint64_t p1 = (uint64_t)c.z * 0xCD9E8D57u;
+    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
+                   (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+  }
+  return c;
+}
+
+// Two standard normals from two 32-bit words (see the layout above).
+__device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  const float u = __uint2float_rn(((wa >> 9) << 1) | 1u) * 0x1p-24f;   // exact, in (0, 1)
+  const float v = __uint2float_rn(wb >> 8) * 0x1p-24f;                 // exact, in [0, 1)
+  const float rad = sqrtf(-2.0f * logf(u));
+  float s, c;
+  sincospif(2.0f * v, &s, &c);
+  z0 = rad * c;
+  z1 = rad * s;
+}
+
+__device__ __forceinline__ void normals4(uint4 w, float z[4]) {
+  box_muller(w.x, w.y, z[0], z[1]);
+  box_muller(w.z, w.w, z[2], z[3]);
+}
+
+// ---------------------------------------------------------------------------
+// Division by an invariant divisor: q = floor(x / d) for 0 <= x < 2^32.
+// With l = ceil(log2 d) and mul = floor(2^32 (2^l - d) / d) + 1,
+// q = (mulhi(x, mul) + x) >> l   (33-bit intermediate).
+// ---------------------------------------------------------------------------
+struct FastDiv {
+  uint32_t d;
+  uint32_t mul;
+  uint32_t shift;
+};
+
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f{d, 1u, 0u};
+  uint32_t l = 0;
+  while ((1ull << l) < d) ++l;
+  f.shift = l;
+  f.mul = (uint32_t)((((1ull << l) - d) << 32) / d + 1ull);
+  return f;
+}
+
+__device__ __forceinline__ uint32_t fdiv(uint32_t x, const FastDiv& f) {
+  return (uint32_t)(((uint64_t)__umulhi(x, f.mul) + x) >> f.shift);
+}
+
+// ---------------------------------------------------------------------------
+// TwoSum-compensated float accumulation (hi + lo represents the sum).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void ff_add(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bb = __fsub_rn(s, hi);
+  const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+  hi = s;
+  lo = __fadd_rn(lo, err);
+}
+
+// ---------------------------------------------------------------------------
+// Parameter blocks
+// ---------------------------------------------------------------------------
+struct DigitGeom {
+  uint32_t a;         // radix a_k
+  uint32_t s;         // stride s_k = a_0 ... a_{k-1}
+  uint32_t H;         // N / (a_k s_k): number of blocks of the digits above k
+  uint32_t nh, nl;    // a tile is nh upper-digit blocks x a_k rows x nl lower-digit columns
+  uint32_t tiles_l;   // s_k / nl
+  uint32_t ntiles;    // (H / nh) * tiles_l
+  uint32_t tile_n;    // nh * a_k * nl particles
+  uint32_t quad;      // 1 if every tile splits into aligned runs of 4 consecutive indices
+  uint32_t prev_s;    // stride of digit k-1 (mod m), whose groups carry the weights
+  float log_a;        // log(a_k)
+  uint32_t wide;      // a_k > kNarrowMaxRadix: 32-bit weights, 64-bit draws, 64-bit prefix sums
+  FastDiv div_nl, div_a, div_tiles_l, div_prev_as, div_prev_s;
+};
+
+// ModelParams::flags: structure of the linear-Gaussian matrices (lets the
+// kernels skip multiplications by known zeros)
+constexpr int kHIdentity = 1, kLrDiagonal = 2, kLqDiagonal = 4, kADiagonal = 8;
+
+struct ModelParams {
+  int kind;
+  int d, dy;
+  int flags;
+  float A[kMaxDim * kMaxDim];     // transition matrix (row-major)
+  float Lq[kMaxDim * kMaxDim];    // transition-noise factor (lower triangular)
+  float H[kMaxDim * kMaxDim];     // observation matrix (dy x d)
+  float Lri[kMaxDim * kMaxDim];   // inverse of the observation-noise factor (lower triangular)
+  float m0[kMaxDim];
+  float L0[kMaxDim * kMaxDim];
+  float phi, sigma, inv2b2, sd0;  // stochastic volatility
+  double c_obs;                   // state-independent part of log g (enters the likelihood only)
+};
+
+struct DevState {
+  uint32_t n;          // time index of the next observation
+  uint32_t done;       // thread blocks finished with the current step
+  uint32_t status;     // sticky kStatus* bits
+  float mu_f;          // FP32 copy of mu, subtracted by the kernels
+  double mu;           // carried normaliser (log-mean carried weight)
+  double loglik;       // cumulative log-likelihood (FP64)
+};
+
+struct StepParams {
+  float* x;            // [d][N] particle states (updated in place)
+  float* lV[2];        // carried log stage weights, ping-pong by time-step parity
+  int32_t* anc;        // [N] ancestors of the last step (nullptr = not recorded)
+  DevState* st;
+  float* partials;     // [grid][3 + d] per-block partial sums
+  const float* y_ring; // [kRing][dy]
+  double* inc_ring;    // [kRing]
+  float* mean_ring;    // [kRing][d]
+  float* ess_ring;     // [kRing]
+  uint32_t N;
+  int m;
+  uint32_t seed_lo, seed_hi;
+  uint32_t tile_cap;   // shared-memory tile capacity (particles)
+  float inv_N;
+  ModelParams model;
+  DigitGeom geom[kMaxDigits];
+};
+
+}  // namespace bfpf

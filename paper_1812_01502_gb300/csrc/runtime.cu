@@ -1,0 +1,566 @@
+// runtime.cu - host runtime and C ABI (include/bfpf.h) of the butterfly
+// particle filter: argument checking, tile planning, workspace layout,
+// kernel launches, CUDA-graph replay of chunks of time steps.
+//
+// The problem a handle solves is the HMM of Section 1.1 of Heine, Whiteley &
+// Cemgil (arXiv 1812.01502) filtered by Algorithm 1 with one stage of
+// Algorithm 3 per time step; see step_butterfly.cu for the step itself.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/bfpf.h"
+#include "bfpf_device.cuh"
+#include "bfpf_kernels.h"
+
+using namespace bfpf;
+
+namespace {
+
+thread_local std::string t_error;
+
+constexpr size_t kAlign = 256;
+
+size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct Layout {
+  size_t st, x, lv0, lv1, anc, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
+};
+
+struct Plan {
+  int d = 0, dy = 0, kind = 0, m = 0;
+  uint32_t N = 0;
+  bool wide = false;          // some radix > kNarrowMaxRadix
+  uint32_t min_a = 0;
+  uint32_t cap = 0;           // tile capacity (particles)
+  uint32_t max_tiles = 0;
+  int grid = 0;
+  size_t smem = 0;
+  bool record = false;
+  int chunk_len = 64;
+  KernelSet ks{};
+  ModelParams mp{};
+  DigitGeom geom[kMaxDigits]{};
+  Layout lay{};
+};
+
+}  // namespace
+
+struct pf_handle {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool own_ws = false;
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0;
+  Plan plan;
+  StepParams P{};
+  uint64_t n_host = 0;     // time steps enqueued
+  uint64_t n_pushed = 0;   // observations copied into the ring
+  cudaGraphExec_t graph = nullptr;
+  int graph_len = 0;
+  std::string err;
+};
+
+namespace {
+
+pf_status fail(const pf_handle* h, pf_status s, const std::string& msg) {
+  if (h) const_cast<pf_handle*>(h)->err = msg;
+  else t_error = msg;
+  return s;
+}
+
+#define PF_CUDA(h, call)                                                              \
+  do {                                                                                \
+    cudaError_t e_ = (call);                                                          \
+    if (e_ != cudaSuccess)                                                            \
+      return fail((h), PF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+bool is_lower_triangular(const double* M, int n) {
+  for (int i = 0; i < n; ++i)
+    for (int j = i + 1; j < n; ++j)
+      if (M[i * n + j] != 0.0) return false;
+  return true;
+}
+
+// Fill the device model block from the caller's model (doubles -> floats).
+pf_status build_model(const pf_model* model, ModelParams& mp, std::string& msg) {
+  if (!model) { msg = "model is NULL"; return PF_EINVAL; }
+  std::memset(&mp, 0, sizeof(mp));
+  mp.kind = model->kind;
+  if (model->kind == PF_MODEL_STOCH_VOL) {
+    if (model->d != 1 || model->dy != 1) { msg = "stochastic volatility needs d = dy = 1"; return PF_EINVAL; }
+    if (!(std::fabs(model->phi) < 1.0) || !(model->sigma > 0.0) || !(model->beta > 0.0)) {
+      msg = "stochastic volatility needs |phi| < 1, sigma > 0, beta > 0";
+      return PF_EINVAL;
+    }
+    mp.d = mp.dy = 1;
+    mp.phi = (float)model->phi;
+    mp.sigma = (float)model->sigma;
+    mp.inv2b2 = (float)(1.0 / (2.0 * model->beta * model->beta));
+    mp.sd0 = (float)(model->sigma / std::sqrt(1.0 - model->phi * model->phi));
+    mp.c_obs = -0.5 * std::log(2.0 * M_PI * model->beta * model->beta);
+    return PF_OK;
+  }
+  if (model->kind != PF_MODEL_LINEAR_GAUSSIAN) { msg = "unknown model kind"; return PF_EINVAL; }
+  const int d = model->d, dy = model->dy;
+  if (d < 1 || d > kMaxDim || dy < 1 || dy > kMaxDim) {
+    msg = "linear-Gaussian model needs 1 <= d, dy <= 8";
+    return PF_EINVAL;
+  }
+  if (!model->H && dy != d) { msg = "H = NULL (identity) needs dy == d"; return PF_EINVAL; }
+  mp.d = d;
+  mp.dy = dy;
+  auto get = [](const double* M, int r, int c, int cols, bool ident) -> double {
+    if (M) return M[r * cols + c];
+    return (ident && r == c) ? 1.0 : 0.0;
+  };
+  int flags = kHIdentity | kLrDiagonal | kLqDiagonal | kADiagonal;
+  for (int i = 0; i < d; ++i)
+    for (int j = 0; j < d; ++j) {
+      const double a = get(model->A, i, j, d, true), q = get(model->Lq, i, j, d, true),
+                   l0 = get(model->L0, i, j, d, true);
+      if (!std::isfinite(a) || !std::isfinite(q) || !std::isfinite(l0)) { msg = "non-finite matrix entry"; return PF_EINVAL; }
+      if (j > i && (q != 0.0 || l0 != 0.0)) { msg = "Lq and L0 must be lower triangular"; return PF_EINVAL; }
+      mp.A[i * kMaxDim + j] = (float)a;
+      mp.Lq[i * kMaxDim + j] = (float)q;
+      mp.L0[i * kMaxDim + j] = (float)l0;
+      if (i != j && a != 0.0) flags &= ~kADiagonal;
+      if (i != j && q != 0.0) flags &= ~kLqDiagonal;
+    }
+  for (int i = 0; i < dy; ++i)
+    for (int j = 0; j < d; ++j) {
+      const double hv = get(model->H, i, j, d, true);
+      if (!std::isfinite(hv)) { msg = "non-finite H entry"; return PF_EINVAL; }
+      mp.H[i * kMaxDim + j] = (float)hv;
+      if (hv != ((i == j) ? 1.0 : 0.0)) flags &= ~kHIdentity;
+    }
+  if (dy != d) flags &= ~kHIdentity;
+  // Lr^{-1} by forward substitution (double), and the likelihood constant.
+  std::vector<double> Lr(dy * dy), Li(dy * dy, 0.0);
+  for (int i = 0; i < dy; ++i)
+    for (int j = 0; j < dy; ++j) Lr[i * dy + j] = get(model->Lr, i, j, dy, true);
+  if (!is_lower_triangular(Lr.data(), dy)) { msg = "Lr must be lower triangular"; return PF_EINVAL; }
+  double logdet = 0.0;
+  for (int i = 0; i < dy; ++i) {
+    if (!(Lr[i * dy + i] != 0.0) || !std::isfinite(Lr[i * dy + i])) { msg = "Lr needs a nonzero finite diagonal"; return PF_EINVAL; }
+    logdet += std::log(std::fabs(Lr[i * dy + i]));
+    for (int j = 0; j < i; ++j)
+      if (Lr[i * dy + j] != 0.0) flags &= ~kLrDiagonal;
+  }
+  for (int c = 0; c < dy; ++c) {        // solve Lr * col = e_c
+    for (int i = 0; i < dy; ++i) {
+      double v = (i == c) ? 1.0 : 0.0;
+      for (int j = 0; j < i; ++j) v -= Lr[i * dy + j] * Li[j * dy + c];
+      Li[i * dy + c] = v / Lr[i * dy + i];
+    }
+  }
+  for (int i = 0; i < dy; ++i)
+    for (int j = 0; j < dy; ++j) mp.Lri[i * kMaxDim + j] = (float)Li[i * dy + j];
+  for (int i = 0; i < d; ++i) mp.m0[i] = model->m0 ? (float)model->m0[i] : 0.0f;
+  mp.c_obs = -logdet - 0.5 * dy * std::log(2.0 * M_PI);
+  mp.flags = flags;
+  return PF_OK;
+}
+
+uint32_t largest_divisor_at_most(uint32_t n, uint32_t limit) {
+  if (limit >= n) return n;
+  for (uint32_t v = std::max<uint32_t>(limit, 1); v > 1; --v)
+    if (n % v == 0) return v;
+  return 1;
+}
+
+pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, int32_t m,
+                    const pf_options* opts, Plan& pl, std::string& msg) {
+  const pf_status bs = build_model(model, pl.mp, msg);
+  if (bs != PF_OK) return bs;
+  pl.d = pl.mp.d;
+  pl.dy = pl.mp.dy;
+  pl.kind = pl.mp.kind;
+  if (!radices || m < 1 || m > kMaxDigits) { msg = "need 1 <= m <= 32 radices"; return PF_EINVAL; }
+  if (N64 < 2 || N64 >= (int64_t(1) << 31)) { msg = "need 2 <= N < 2^31"; return PF_EINVAL; }
+  int64_t prod = 1;
+  pl.min_a = 0xffffffffu;
+  for (int k = 0; k < m; ++k) {
+    const int64_t a = radices[k];
+    if (a < 2) { msg = "every radix must be >= 2"; return PF_EINVAL; }
+    if (m > 1 && a > (int64_t)kMaxCtaRadix) { msg = "radices must be <= 1024 when m > 1"; return PF_EINVAL; }
+    prod *= a;
+    if (prod > N64) break;
+    pl.min_a = std::min<uint32_t>(pl.min_a, (uint32_t)a);
+    if (a > (int64_t)kNarrowMaxRadix) pl.wide = true;
+  }
+  if (prod != N64) { msg = "the product of the radices must equal N"; return PF_EINVAL; }
+  if (m == 1 && N64 > (int64_t)kMaxCtaRadix) {
+    msg = "global resampling (m = 1) with N > 1024 is not available in this build";
+    return PF_EINVAL;
+  }
+  pl.N = (uint32_t)N64;
+  pl.m = m;
+  const int d = pl.d;
+  uint32_t target = (opts && opts->tile > 0) ? (uint32_t)opts->tile : (d == 1 ? 4096u : d <= 4 ? 2048u : 1024u);
+  target = std::max<uint32_t>(target, 4);
+  uint32_t s = 1;
+  pl.cap = 0;
+  pl.max_tiles = 0;
+  for (int k = 0; k < m; ++k) {
+    DigitGeom& g = pl.geom[k];
+    const uint32_t a = (uint32_t)radices[k];
+    g.a = a;
+    g.s = s;
+    g.H = pl.N / (a * s);
+    if ((uint64_t)a * s <= target) {
+      g.nl = s;
+      g.nh = largest_divisor_at_most(g.H, target / (a * s));
+    } else {
+      g.nh = 1;
+      g.nl = largest_divisor_at_most(s, std::max<uint32_t>(1, target / a));
+    }
+    g.tiles_l = s / g.nl;
+    g.ntiles = (g.H / g.nh) * g.tiles_l;
+    g.tile_n = g.nh * a * g.nl;
+    g.quad = (g.nl == s) ? ((g.tile_n % 4 == 0) && (pl.N % 4 == 0)) : ((g.nl % 4 == 0) && (s % 4 == 0));
+    g.log_a = (float)std::log((double)a);
+    g.wide = a > kNarrowMaxRadix ? 1u : 0u;
+    g.div_nl = make_fastdiv(g.nl);
+    g.div_a = make_fastdiv(a);
+    g.div_tiles_l = make_fastdiv(g.tiles_l);
+    pl.cap = std::max(pl.cap, g.tile_n);
+    pl.max_tiles = std::max(pl.max_tiles, g.ntiles);
+    s *= a;
+  }
+  for (int k = 0; k < m; ++k) {
+    const int kp = (k + m - 1) % m;
+    DigitGeom& g = pl.geom[k];
+    g.prev_s = pl.geom[kp].s;
+    g.div_prev_as = make_fastdiv(pl.geom[kp].a * pl.geom[kp].s);
+    g.div_prev_s = make_fastdiv(pl.geom[kp].s);
+  }
+  pl.cap = (pl.cap + 3) / 4 * 4;
+  pl.smem = (size_t)(d + 1) * pl.cap * 4 + (size_t)pl.cap * (pl.wide ? 8 : 4);
+  pl.record = opts && (opts->flags & PF_RECORD_ANCESTORS);
+  pl.chunk_len = (opts && opts->chunk_len > 0) ? std::min<int>(opts->chunk_len, (int)kRing) : 64;
+  if (!select_kernels(d, pl.kind, pl.wide, pl.ks)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
+  return PF_OK;
+}
+
+// Needs a CUDA device: occupancy decides the persistent grid size.
+pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
+  int dev = 0, sms = 0, nb = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess)   // opt in beyond the 48 KB default whatever the size
+    e = cudaFuncSetAttribute(pl.ks.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pl.ks.step, kBlock, pl.smem);
+  if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
+  if (nb < 1) { msg = "tile does not fit in shared memory; choose a smaller tile"; return PF_EINVAL; }
+  int grid = (opts && opts->grid > 0) ? opts->grid : nb * sms;
+  grid = std::max(1, std::min<int>(grid, (int)pl.max_tiles));
+  pl.grid = grid;
+  Layout& L = pl.lay;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  L.st = take(sizeof(DevState));
+  L.x = take((size_t)4 * pl.d * pl.N);
+  L.lv0 = take((size_t)4 * (pl.N / pl.min_a));
+  L.lv1 = take((size_t)4 * (pl.N / pl.min_a));
+  L.anc = pl.record ? take((size_t)4 * pl.N) : 0;
+  L.partials = take((size_t)4 * (3 + pl.d) * grid);
+  L.y_ring = take((size_t)4 * kRing * pl.dy);
+  L.inc_ring = take((size_t)8 * kRing);
+  L.mean_ring = take((size_t)4 * kRing * pl.d);
+  L.ess_ring = take((size_t)4 * kRing);
+  L.total = off;
+  return PF_OK;
+}
+
+cudaError_t launch_step(pf_handle* h, cudaStream_t stream) {
+  void* args[] = {&h->P};
+  return cudaLaunchKernel(h->plan.ks.step, dim3(h->plan.grid), dim3(kBlock), args, h->plan.smem, stream);
+}
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_workspace_size(const pf_model* model, int64_t N, const int32_t* radices, int32_t m,
+                            const pf_options* opts, size_t* bytes) {
+  if (!bytes) return fail(nullptr, PF_EINVAL, "bytes is NULL");
+  Plan pl;
+  std::string msg;
+  pf_status s = make_plan(model, N, radices, m, opts, pl, msg);
+  if (s == PF_OK) s = finish_plan(pl, opts, msg);
+  if (s != PF_OK) return fail(nullptr, s, msg);
+  *bytes = pl.lay.total;
+  return PF_OK;
+}
+
+pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, int32_t m, uint64_t seed,
+                    const pf_options* opts, void* workspace, size_t workspace_bytes, pf_handle** out) {
+  if (!out) return fail(nullptr, PF_EINVAL, "out is NULL");
+  *out = nullptr;
+  pf_handle* h = new (std::nothrow) pf_handle();
+  if (!h) return fail(nullptr, PF_ENOMEM, "host allocation failed");
+  std::string msg;
+  pf_status s = make_plan(model, N, radices, m, opts, h->plan, msg);
+  if (s == PF_OK) s = finish_plan(h->plan, opts, msg);
+  if (s != PF_OK) {
+    delete h;
+    return fail(nullptr, s, msg);
+  }
+  Plan& pl = h->plan;
+  cudaGetDevice(&h->device);
+  h->stream = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+  if (workspace) {
+    if (workspace_bytes < pl.lay.total) {
+      delete h;
+      return fail(nullptr, PF_ENOMEM, "workspace smaller than pf_workspace_size()");
+    }
+    if (reinterpret_cast<uintptr_t>(workspace) % kAlign) {
+      delete h;
+      return fail(nullptr, PF_EINVAL, "workspace must be 256-byte aligned");
+    }
+    h->ws = static_cast<unsigned char*>(workspace);
+    h->ws_bytes = workspace_bytes;
+  } else {
+    cudaError_t e = cudaMalloc(&h->ws, pl.lay.total);
+    if (e != cudaSuccess) {
+      delete h;
+      return fail(nullptr, PF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    h->own_ws = true;
+    h->ws_bytes = pl.lay.total;
+  }
+  cudaError_t e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return fail(nullptr, PF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+  }
+  StepParams& P = h->P;
+  const Layout& L = pl.lay;
+  P.x = reinterpret_cast<float*>(h->ws + L.x);
+  P.lV[0] = reinterpret_cast<float*>(h->ws + L.lv0);
+  P.lV[1] = reinterpret_cast<float*>(h->ws + L.lv1);
+  P.anc = pl.record ? reinterpret_cast<int32_t*>(h->ws + L.anc) : nullptr;
+  P.st = reinterpret_cast<DevState*>(h->ws + L.st);
+  P.partials = reinterpret_cast<float*>(h->ws + L.partials);
+  P.y_ring = reinterpret_cast<const float*>(h->ws + L.y_ring);
+  P.inc_ring = reinterpret_cast<double*>(h->ws + L.inc_ring);
+  P.mean_ring = reinterpret_cast<float*>(h->ws + L.mean_ring);
+  P.ess_ring = reinterpret_cast<float*>(h->ws + L.ess_ring);
+  P.N = pl.N;
+  P.m = pl.m;
+  P.seed_lo = (uint32_t)seed;
+  P.seed_hi = (uint32_t)(seed >> 32);
+  P.tile_cap = pl.cap;
+  P.inv_N = (float)(1.0 / pl.N);
+  P.model = pl.mp;
+  std::memcpy(P.geom, pl.geom, sizeof(P.geom));
+
+  // Algorithm 1, first loop: zeta_0 ~ pi_0; carried weights start at zero.
+  auto bail = [&](cudaError_t err, const char* what) {
+    std::string m2 = std::string(what) + ": " + cudaGetErrorString(err);
+    cudaStreamDestroy(h->cap_stream);
+    if (h->own_ws) cudaFree(h->ws);
+    delete h;
+    return fail(nullptr, PF_ECUDA, m2);
+  };
+  e = cudaMemsetAsync(h->ws + L.st, 0, sizeof(DevState), h->stream);
+  if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
+  e = cudaMemsetAsync(h->ws + L.lv0, 0, (size_t)4 * (pl.N / pl.min_a), h->stream);
+  if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
+  const uint32_t blocks = std::min<uint32_t>((pl.N + kBlock - 1) / kBlock, (uint32_t)std::max(1, sms) * 8);
+  void* args[] = {&h->P};
+  e = cudaLaunchKernel(pl.ks.init, dim3(blocks), dim3(kBlock), args, 0, h->stream);
+  if (e != cudaSuccess) return bail(e, "init kernel");
+  *out = h;
+  return PF_OK;
+}
+
+pf_status pf_step(pf_handle* h, const float* y_n, float* mean_out, double* loglik_inc, float* ess_out) {
+  if (!h) return fail(nullptr, PF_EINVAL, "handle is NULL");
+  if (!y_n) return fail(h, PF_EINVAL, "y_n is NULL");
+  if (h->n_pushed != h->n_host) return fail(h, PF_ESTATE, "observations pushed but not consumed");
+  pf_status s = pf_push_observations(h, y_n, 1);
+  if (s == PF_OK) s = pf_advance(h, 1, mean_out, loglik_inc, ess_out);
+  return s;
+}
+
+pf_status pf_push_observations(pf_handle* h, const float* y, int32_t T) {
+  if (!h) return fail(nullptr, PF_EINVAL, "handle is NULL");
+  if (T < 0 || (T > 0 && !y)) return fail(h, PF_EINVAL, "need T >= 0 and y != NULL");
+  if (h->n_pushed + (uint64_t)T - h->n_host > kRing)
+    return fail(h, PF_ESTATE, "more than 1024 observations pushed ahead of the steps taken");
+  const Plan& pl = h->plan;
+  int32_t done = 0;
+  while (done < T) {   // at most two contiguous pieces of the ring
+    const uint32_t slot = (uint32_t)(h->n_pushed % kRing);
+    const int32_t L = std::min<int32_t>(T - done, (int32_t)(kRing - slot));
+    PF_CUDA(h, cudaMemcpyAsync(const_cast<float*>(h->P.y_ring) + (size_t)slot * pl.dy, y + (size_t)done * pl.dy,
+                               (size_t)4 * pl.dy * L, cudaMemcpyDefault, h->stream));
+    h->n_pushed += L;
+    done += L;
+  }
+  return PF_OK;
+}
+
+namespace {
+
+// L steps on pushed observations: a captured graph when L is the chunk length.
+pf_status enqueue_steps(pf_handle* h, int32_t L) {
+  const Plan& pl = h->plan;
+  if (L == pl.chunk_len && L > 1) {
+    if (!h->graph) {
+      cudaGraph_t graph = nullptr;
+      PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
+      cudaError_t le = cudaSuccess;
+      for (int j = 0; j < L && le == cudaSuccess; ++j) le = launch_step(h, h->cap_stream);
+      cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
+      if (le != cudaSuccess) return fail(h, PF_ECUDA, std::string("capture launch: ") + cudaGetErrorString(le));
+      if (ce != cudaSuccess) return fail(h, PF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+      cudaError_t ie = cudaGraphInstantiate(&h->graph, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ie != cudaSuccess) {
+        h->graph = nullptr;
+        return fail(h, PF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+      }
+      h->graph_len = L;
+    }
+    PF_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+  } else {
+    for (int j = 0; j < L; ++j) PF_CUDA(h, launch_step(h, h->stream));
+  }
+  return PF_OK;
+}
+
+}  // namespace
+
+pf_status pf_advance(pf_handle* h, int32_t T, float* means, double* loglik_incs, float* ess) {
+  if (!h) return fail(nullptr, PF_EINVAL, "handle is NULL");
+  if (T < 0) return fail(h, PF_EINVAL, "need T >= 0");
+  if (h->n_host + (uint64_t)T > h->n_pushed) return fail(h, PF_ESTATE, "fewer observations pushed than steps asked");
+  const Plan& pl = h->plan;
+  int32_t done = 0;
+  while (done < T) {
+    const uint32_t slot0 = (uint32_t)(h->n_host % kRing);
+    const int32_t L = std::min<int32_t>({pl.chunk_len, T - done, (int32_t)(kRing - slot0)});
+    pf_status s = enqueue_steps(h, L);
+    if (s != PF_OK) return s;
+    if (means)
+      PF_CUDA(h, cudaMemcpyAsync(means + (size_t)done * pl.d, h->P.mean_ring + (size_t)slot0 * pl.d,
+                                 (size_t)4 * pl.d * L, cudaMemcpyDefault, h->stream));
+    if (loglik_incs)
+      PF_CUDA(h, cudaMemcpyAsync(loglik_incs + done, h->P.inc_ring + slot0, (size_t)8 * L, cudaMemcpyDefault,
+                                 h->stream));
+    if (ess)
+      PF_CUDA(h, cudaMemcpyAsync(ess + done, h->P.ess_ring + slot0, (size_t)4 * L, cudaMemcpyDefault, h->stream));
+    h->n_host += L;
+    done += L;
+  }
+  PF_CUDA(h, cudaGetLastError());
+  if (means || loglik_incs || ess) PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+pf_status pf_run(pf_handle* h, const float* y, int32_t T, float* means, double* loglik_incs, float* ess) {
+  if (!h) return fail(nullptr, PF_EINVAL, "handle is NULL");
+  if (T < 0 || (T > 0 && !y)) return fail(h, PF_EINVAL, "need T >= 0 and y != NULL");
+  if (h->n_pushed != h->n_host) return fail(h, PF_ESTATE, "observations pushed but not consumed");
+  const Plan& pl = h->plan;
+  int32_t done = 0;
+  while (done < T) {
+    const uint32_t slot0 = (uint32_t)(h->n_host % kRing);
+    const int32_t L = std::min<int32_t>({pl.chunk_len, T - done, (int32_t)(kRing - slot0)});
+    pf_status s = pf_push_observations(h, y + (size_t)done * pl.dy, L);
+    if (s == PF_OK) s = pf_advance(h, L, means ? means + (size_t)done * pl.d : nullptr,
+                                  loglik_incs ? loglik_incs + done : nullptr, ess ? ess + done : nullptr);
+    if (s != PF_OK) return s;
+    done += L;
+  }
+  return PF_OK;
+}
+
+pf_status pf_loglik(const pf_handle* h, double* out) {
+  if (!h || !out) return fail(h, PF_EINVAL, "NULL argument");
+  DevState st;
+  PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = st.loglik;
+  return PF_OK;
+}
+
+pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars) {
+  if (!h) return fail(nullptr, PF_EINVAL, "handle is NULL");
+  const Plan& pl = h->plan;
+  DevState st;
+  PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  if (x) PF_CUDA(h, cudaMemcpyAsync(x, h->P.x, (size_t)4 * pl.d * pl.N, cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (lV) {
+    const uint32_t n = st.n;
+    const int kp = (int)((n + pl.m - 1) % pl.m);
+    const size_t cnt = pl.N / pl.geom[kp].a;
+    PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[n & 1u], 4 * cnt, cudaMemcpyDeviceToHost, h->stream));
+    PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  }
+  if (scalars) {
+    scalars[0] = (double)st.n;
+    scalars[1] = st.loglik;
+    scalars[2] = st.mu;
+    scalars[3] = (double)st.mu_f;
+  }
+  return PF_OK;
+}
+
+pf_status pf_get_ancestors(const pf_handle* h, int32_t* anc) {
+  if (!h || !anc) return fail(h, PF_EINVAL, "NULL argument");
+  if (!h->P.anc) return fail(h, PF_ESTATE, "ancestors are not recorded (create with PF_RECORD_ANCESTORS)");
+  PF_CUDA(h, cudaMemcpyAsync(anc, h->P.anc, (size_t)4 * h->plan.N, cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+pf_status pf_get_status(const pf_handle* h, uint32_t* bits) {
+  if (!h || !bits) return fail(h, PF_EINVAL, "NULL argument");
+  DevState st;
+  PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  *bits = st.status;
+  return PF_OK;
+}
+
+pf_status pf_destroy(pf_handle* h) {
+  if (!h) return PF_OK;
+  cudaError_t e = cudaStreamSynchronize(h->stream);
+  if (h->graph) cudaGraphExecDestroy(h->graph);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  if (h->own_ws && h->ws) cudaFree(h->ws);
+  delete h;
+  if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+  return PF_OK;
+}
+
+const char* pf_last_error(const pf_handle* h) {
+  if (h) return h->err.c_str();
+  return t_error.c_str();
+}
+
+pf_status pf_philox_blocks(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3, int64_t count,
+                           uint32_t* out, void* stream) {
+  if (!out || count < 0 || count > 0x7fffffff) return fail(nullptr, PF_EINVAL, "bad arguments");
+  if (count == 0) return PF_OK;
+  cudaError_t e = launch_philox_blocks(seed, make_uint4(c0, c1, c2, c3), (uint32_t)count, out,
+                                       static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("philox kernel: ") + cudaGetErrorString(e));
+  return PF_OK;
+}
+
+}  // extern "C"

@@ -18,3 +18,13 @@ def pytest_configure(config):
 @pytest.fixture(scope="session")
 def golden_dir():
     return GOLDEN
+
+
+@pytest.fixture(scope="session")
+def bfpf():
+    """The compiled library's Python binding (builds libbfpf.so in-tree if needed)."""
+    from paper_1812_01502_gb300 import _build
+    _build.build()
+    import paper_1812_01502_gb300 as pkg
+    pkg.load_library()
+    return pkg

@@ -1,0 +1,163 @@
+"""Lockstep parity: the FP64 oracle re-runs each GPU time step from the GPU's own
+state and checks every output of that step.
+
+Ancestors are integers decided by floating-point weights.  Both sides take the
+decision with the same integer rule and FP32 quantisation, but their weights
+differ by FP32-versus-FP64 rounding, so a draw that lands within a few quanta
+of a prefix-sum boundary may legitimately go either way.  If every integer
+weight differs between the sides by at most a relative ETA (plus one quantum
+from the floor), a boundary P_j moves, relative to Q, by at most
+2 ETA min(P_j, Q - P_j) + a + 2 quanta, and the uniform u = floor(r Q / 2^32)
+by one more.  A draw is *decidable* when every boundary lies farther than
+
+    margin_j = 2 * ETA * min(P_j, Q - P_j) + a + 4
+
+from its uniform.  Decidable draws must match bit for bit; every GPU ancestor
+must lie among the oracle's plausible members.  States and log-weights must
+agree to 1e-5 (relative, floor 1), likelihood increments to 1e-6.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import bpf, butterfly
+
+ETA = 2.0 ** -15
+TOL_STATE = 1e-5
+TOL_INC = 1e-6
+
+
+def plausible_members(q: np.ndarray, u: np.ndarray, axis: int):
+    """(lo, hi) member indices an ancestor draw may take given boundary uncertainty."""
+    P = np.cumsum(q, axis=axis, dtype=np.uint64).astype(np.float64)
+    Q = np.take(P, [-1], axis=axis)
+    a = q.shape[axis]
+    margin = 2 * ETA * np.minimum(P, Q - P) + a + 4
+    Pm = np.moveaxis(P, axis, -1)
+    um = np.moveaxis(u.astype(np.float64), axis, -1)
+    mg = np.moveaxis(margin, axis, -1)
+    lo = (Pm[..., None, :] + mg[..., None, :] <= um[..., :, None]).sum(-1)
+    hi = np.minimum((Pm[..., None, :] - mg[..., None, :] <= um[..., :, None]).sum(-1), a - 1)
+    return np.moveaxis(lo, -1, axis), np.moveaxis(hi, -1, axis)
+
+
+def rel_err(a, b, floor=1.0):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    fin = np.isfinite(b)
+    if not np.array_equal(np.isfinite(a), fin):
+        return np.inf
+    if not fin.any():
+        return 0.0
+    return float(np.max(np.abs(a[fin] - b[fin]) / np.maximum(np.abs(b[fin]), floor)))
+
+
+def per_particle_lV(lv_compact, radices, n):
+    """Expand the GPU's compact carried weights (groups of digit (n-1) mod m) to particles."""
+    N = int(np.prod(radices))
+    kp = (n - 1) % len(radices)
+    return lv_compact[butterfly.group_index(np.arange(N), radices, kp)]
+
+
+class Report(dict):
+    def merge(self, other):
+        for k, v in other.items():
+            if k.startswith("max_"):
+                self[k] = max(self.get(k, 0.0), v)
+            else:
+                self[k] = self.get(k, 0) + v
+
+
+def check_step_full(filt, model, radices, seed, y_n, n):
+    """Run GPU step n and check it against the oracle's step from the same state."""
+    N = int(np.prod(radices))
+    m = len(radices)
+    x0, lv0, sc = filt.state()
+    assert sc["n"] == n
+    mean, inc, ess = filt.step(y_n)
+    anc = filt.ancestors().astype(np.int64)
+    x1, lv1, sc1 = filt.state()
+    lV = per_particle_lV(lv0, radices, n).astype(np.float64)
+    st = bpf.State(x=x0.astype(np.float64), lV=lV, mu=sc["mu"], n=n)
+    new, o = bpf.step(model, radices, seed, st, y_n, mu_used=sc["mu_used"])
+    k, a, s = o["k"], o["a"], o["stride"]
+    H = N // (a * s)
+    # ancestors
+    q = o["q"].reshape(H, a, s)
+    u = o["u"].reshape(H, a, s)
+    lo, hi = plausible_members(q, u, axis=1)
+    member_gpu = ((anc // s) % a).reshape(H, a, s)
+    same_group = np.array_equal(anc // (a * s), np.arange(N) // (a * s)) and \
+        np.array_equal(anc % s, np.arange(N) % s)
+    assert same_group, "GPU ancestor outside its group"
+    dec = (lo == hi)
+    member_o = (o["anc"].reshape(H, a, s) // s) % a
+    mism = member_gpu != member_o
+    assert not np.any(mism & dec), f"step {n}: {int(np.sum(mism & dec))} decidable ancestors differ"
+    assert np.all((member_gpu >= lo) & (member_gpu <= hi)), f"step {n}: implausible ancestor"
+    # offspring counts sum to a in every group
+    grp = (anc // (a * s)) * s + anc % s
+    assert np.all(np.bincount(grp, minlength=N // a) == a)
+    # states: oracle mutation of the GPU's own ancestors
+    x_chk = bpf.mutate(model, x0.astype(np.float64)[anc], n, seed)
+    e_x = rel_err(x1, x_chk)
+    lv_chk = o["lV_new"].reshape(H, a, s)[:, 0, :].reshape(-1)
+    e_lv = rel_err(lv1, lv_chk)
+    e_inc = abs(inc - o["inc"]) / max(1.0, abs(o["inc"]))
+    e_mean = rel_err(mean, o["mean"])
+    e_ess = abs(ess - o["ess"]) / max(o["ess"], 1e-12)
+    assert e_x <= TOL_STATE, f"step {n}: state error {e_x}"
+    assert e_lv <= TOL_STATE, f"step {n}: log-weight error {e_lv}"
+    assert e_inc <= TOL_INC, f"step {n}: likelihood increment error {e_inc}"
+    assert e_mean <= TOL_STATE, f"step {n}: mean error {e_mean}"
+    assert e_ess <= 1e-4, f"step {n}: ess error {e_ess}"
+    assert abs(sc1["mu"] - new.mu) <= 1e-6 * max(1.0, abs(new.mu))
+    return Report(draws=N, undecidable=int(np.sum(~dec)), mismatched_undecidable=int(np.sum(mism)),
+                  max_state_err=e_x, max_logweight_err=e_lv, max_inc_err=e_inc, max_mean_err=e_mean,
+                  max_ess_err=e_ess)
+
+
+def check_step_sampled(filt, model, radices, seed, y_n, n, n_groups, rng):
+    """Run GPU step n at full size and check sampled groups (ancestors, states,
+    log-weights) and the global outputs (increment, mean, ESS) against the oracle."""
+    N = int(np.prod(radices))
+    m = len(radices)
+    k = n % m
+    a = int(radices[k])
+    s = butterfly.strides(radices)[k]
+    H = N // (a * s)
+    x0, lv0, sc = filt.state()
+    mean, inc, ess = filt.step(y_n)
+    anc = filt.ancestors().astype(np.int64)
+    x1, lv1, _ = filt.state()
+    lV = per_particle_lV(lv0, radices, n)
+    # global outputs from the whole GPU state
+    lw, c_n = bpf.weigh(model, x0.astype(np.float64), lV.astype(np.float64), sc["mu_used"], y_n)
+    inc_o, mean_o, ess_o, _ = bpf.summaries(lw, x0.astype(np.float64), c_n, sc["mu_used"], sc["mu"])
+    e_inc = abs(inc - inc_o) / max(1.0, abs(inc_o))
+    e_mean = rel_err(mean, mean_o)
+    e_ess = abs(ess - ess_o) / max(ess_o, 1e-12)
+    assert e_inc <= TOL_INC, f"step {n}: likelihood increment error {e_inc}"
+    assert e_mean <= TOL_STATE, f"step {n}: mean error {e_mean}"
+    assert e_ess <= 1e-4, f"step {n}: ess error {e_ess}"
+    gid = rng.choice(H * s, size=min(n_groups, H * s), replace=False)
+    groups = np.stack([gid // s, gid % s], axis=1)
+    o = bpf.step_on_groups(model, radices, seed, n, x0, lV, sc["mu_used"], y_n, groups)
+    idx = o["idx"]
+    lo, hi = plausible_members(o["q"], o["u"], axis=1)
+    member_gpu = (anc[idx] // s) % a
+    member_o = (o["anc"] // s) % a
+    dec = lo == hi
+    assert np.all(anc[idx] // (a * s) == idx // (a * s)) and np.all(anc[idx] % s == idx % s)
+    assert not np.any((member_gpu != member_o) & dec), f"step {n}: decidable ancestors differ"
+    assert np.all((member_gpu >= lo) & (member_gpu <= hi))
+    x_chk = bpf.mutate(model, x0[anc[idx].reshape(-1)].astype(np.float64), n, seed,
+                       idx=idx.reshape(-1)).reshape(idx.shape + (x0.shape[1],))
+    e_x = rel_err(x1[idx], x_chk)
+    e_lv = rel_err(lv1[groups[:, 0] * s + groups[:, 1]], o["lV_new"])
+    assert e_x <= TOL_STATE, f"step {n}: state error {e_x}"
+    assert e_lv <= TOL_STATE, f"step {n}: log-weight error {e_lv}"
+    return Report(draws=int(idx.size), undecidable=int(np.sum(~dec)),
+                  mismatched_undecidable=int(np.sum(member_gpu != member_o)),
+                  max_state_err=e_x, max_logweight_err=e_lv, max_inc_err=e_inc, max_mean_err=e_mean,
+                  max_ess_err=e_ess)

@@ -1,0 +1,40 @@
+"""Full-size parity in the launch configuration the bench times (automatic tile
+and persistent grid): every digit of the radix schedule is exercised; at each
+step the oracle recomputes sampled groups (ancestors, states, new carried
+weights) from the GPU's state, and the step's global outputs (likelihood
+increment, filter mean, ESS) from the whole GPU state."""
+import numpy as np
+import pytest
+
+import synthetic as S
+import lockstep as LS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name,groups", [("lg8d_n1m", 96), ("sv_n16m", 256)])
+def test_fullsize_sampled_lockstep(bfpf, name, groups):
+    w = S.workload(name)
+    y = w.observations(len(w.radices) + 3)
+    f = bfpf.ButterflyFilter(w.model, w.N, w.radices, w.filter_seed, record_ancestors=True)
+    rng = np.random.default_rng(123)
+    rep = LS.Report()
+    for n in range(len(y)):
+        rep.merge(LS.check_step_sampled(f, w.model, w.radices, w.filter_seed, y[n], n, groups, rng))
+    f.close()
+    print(name, dict(rep))
+    assert rep["undecidable"] <= max(8, 4 * 2 * LS.ETA * max(w.radices) * rep["draws"])
+
+
+def test_fullsize_long_run_loglik_finite(bfpf):
+    """The headline workload over 200 steps through pf_run: finite, stable outputs and
+    ESS in (0, 1]; the FP64 log-likelihood equals the sum of the per-step increments."""
+    w = S.workload("sv_n16m")
+    y = w.observations(200)
+    f = bfpf.ButterflyFilter(w.model, w.N, w.radices, w.filter_seed)
+    r = f.run(y)
+    ll = f.loglik()
+    f.close()
+    assert np.all(np.isfinite(r["inc"])) and np.all(np.isfinite(r["mean"]))
+    assert np.all((r["ess"] > 0) & (r["ess"] <= 1.0 + 1e-6))
+    assert abs(ll - np.sum(r["inc"])) <= 1e-9 * abs(ll)

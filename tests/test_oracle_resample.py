@@ -186,3 +186,26 @@ def test_step_invariants(radices):
         assert np.all(lvg == lvg[:, :1, :])
         # the carried normaliser is the log-mean weight
         assert np.isclose(st.mu, np.log(np.mean(np.exp(st.lV))), rtol=0, atol=1e-12)
+
+
+@pytest.mark.parametrize("radices,n", [((4, 8, 2), 0), ((4, 8, 2), 1), ((4, 8, 2), 2), ((3, 5), 1), ((300, 2), 0)])
+def test_step_on_groups_equals_full_step(radices, n):
+    """The group-restricted step (used to check full-size GPU runs) agrees with the full step."""
+    N = int(np.prod(radices))
+    model = S.lg_dense(3, seed=4)
+    y = S.simulate(model, 4, seed=2)[1]
+    st = bpf.init_state(model, N, seed=6)
+    for t in range(n):
+        st, _ = bpf.step(model, radices, 6, st, y[t])
+    new, o = bpf.step(model, radices, 6, st, y[n])
+    k = n % len(radices)
+    a, s_k = radices[k], butterfly.strides(radices)[k]
+    H = N // (a * s_k)
+    groups = np.array([(h, l) for h in range(H) for l in range(s_k)])
+    g = bpf.step_on_groups(model, radices, 6, n, st.x, st.lV, st.mu, y[n], groups)
+    assert np.array_equal(np.sort(g["idx"].reshape(-1)), np.arange(N))
+    flat = g["idx"].reshape(-1)
+    assert np.array_equal(g["anc"].reshape(-1), o["anc"][flat])
+    np.testing.assert_allclose(g["x_next"].reshape(-1, 3), new.x[flat], rtol=1e-13, atol=1e-13)
+    lv_c = o["lV_new"].reshape(H, a, s_k)[:, 0, :].reshape(-1)
+    np.testing.assert_allclose(g["lV_new"], lv_c[groups[:, 0] * s_k + groups[:, 1]], rtol=1e-13)
