@@ -182,6 +182,15 @@ pf_status pf_get_ancestors(const pf_handle* h, int32_t* anc);
  * had zero total weight and kept its particles.  Synchronises. */
 pf_status pf_get_status(const pf_handle* h, uint32_t* bits);
 
+/*
+ * Describe the launch plan as a JSON object (NUL-terminated, truncated to
+ * `len` bytes): per digit k its radix, stride, kernel ("group" = the
+ * register-resident kernel for power-of-two radices <= 32, "tile" = the
+ * general shared-memory tile kernel), lanes per group or tile size, and grid.
+ * Host-only; never synchronises.
+ */
+pf_status pf_describe(const pf_handle* h, char* buf, size_t len);
+
 /* Release the handle and, if the library allocated it, its workspace.
  * Synchronises the stream.  NULL is accepted. */
 pf_status pf_destroy(pf_handle* h);

@@ -29,7 +29,7 @@ from typing import Dict, Optional, Sequence
 import numpy as np
 
 from . import philox, resample
-from .butterfly import strides
+from .butterfly import group_major, strides
 
 
 @dataclass
@@ -77,7 +77,8 @@ def initial_particles(model, N: int, seed: int) -> np.ndarray:
 def mutate(model, xhat: np.ndarray, n: int, seed: int, idx=None) -> np.ndarray:
     """Algorithm 1, mutation: zeta_{n+1}^i ~ f(zeta_hat_n^i, .).
 
-    ``idx`` (optional) are the particle indices i of the rows of xhat; by default 0..N-1."""
+    ``idx`` (optional) are the counter numbers of the rows of xhat (their normals are
+    idx*d + t); by default 0..N-1."""
     N, d = xhat.shape
     if idx is None:
         eps = philox.normals(seed, n, philox.PURPOSE_PROPAGATE, N * d).reshape(N, d)
@@ -149,11 +150,12 @@ def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
     # xi_s^i ~ (V_s^i)^{-1} sum_j A^{ij} V_{s-1}^j delta_{xi_{s-1}^j}   (integer rule)
     q = resample.quantise(lwg, axis=1)
     Q = np.sum(q, axis=1, keepdims=True, dtype=np.uint64)
+    pi = group_major(N, radices, k)            # counter numbering of the draws at this step
     if a <= resample.NARROW_MAX_RADIX:
-        r = philox.resample_words(seed, n, N).reshape(Hh, a, s_k)
+        r = philox.resample_words_at(seed, n, pi).reshape(Hh, a, s_k)
         u = resample.scaled_uniform(r, Q, a)
     else:
-        lo, hi = philox.resample_words_wide(seed, n, N)
+        lo, hi = philox.resample_words_wide_at(seed, n, pi)
         u = resample.scaled_uniform(lo.reshape(Hh, a, s_k), Q, a, hi.reshape(Hh, a, s_k))
     member = resample.draw(q, u, axis=1)                                  # (Hh, a, s_k)
     h_idx = np.arange(Hh)[:, None, None]
@@ -163,7 +165,7 @@ def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
     # Likelihood increment, filter mean and ESS (Section 1.2) from the weighted particles.
     inc, mean, ess, lme = summaries(lw, st.x, c_n, mu_sub, st.mu)
 
-    x_next = mutate(model, st.x[anc], n, seed)
+    x_next = mutate(model, st.x[anc], n, seed, idx=pi)
     new = State(x=x_next, lV=lV_new, mu=lme, n=n + 1, loglik=st.loglik + inc)
     out = dict(k=k, a=a, stride=s_k, anc=anc, lw=lw, q=q.reshape(N), u=u.reshape(N),
                Q=np.broadcast_to(Q, q.shape).reshape(N), inc=inc, mean=mean, ess=ess,
@@ -219,13 +221,14 @@ def step_on_groups(model, radices: Sequence[int], seed: int, n: int, x: np.ndarr
     Lg = Mg + np.log(np.sum(np.exp(lw - Mg), axis=1, keepdims=True))
     q = resample.quantise(lw, axis=1)
     Q = np.sum(q, axis=1, keepdims=True, dtype=np.uint64)
+    pi = ((groups[:, :1] * s_k + groups[:, 1:2]) * a + np.arange(a)[None, :]).reshape(-1)
     if a <= resample.NARROW_MAX_RADIX:
-        u = resample.scaled_uniform(philox.resample_words_at(seed, n, flat).reshape(idx.shape), Q, a)
+        u = resample.scaled_uniform(philox.resample_words_at(seed, n, pi).reshape(idx.shape), Q, a)
     else:
-        lo, hi = philox.resample_words_wide_at(seed, n, flat)
+        lo, hi = philox.resample_words_wide_at(seed, n, pi)
         u = resample.scaled_uniform(lo.reshape(idx.shape), Q, a, hi.reshape(idx.shape))
     member = resample.draw(q, u, axis=1)
     anc = groups[:, :1] * (a * s_k) + member * s_k + groups[:, 1:2]
-    x_next = mutate(model, x[anc.reshape(-1)].astype(np.float64), n, seed, idx=flat).reshape(idx.shape + (d,))
+    x_next = mutate(model, x[anc.reshape(-1)].astype(np.float64), n, seed, idx=pi).reshape(idx.shape + (d,))
     return dict(idx=idx, lw=lw, q=q, u=u, Q=np.broadcast_to(Q, q.shape), anc=anc, x_next=x_next,
                 lV_new=(Lg - np.log(a))[:, 0])

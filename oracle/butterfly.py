@@ -78,3 +78,12 @@ def group_index(i, radices: Sequence[int], k: int):
     s = strides(radices)[k]
     i = np.asarray(i, dtype=np.int64)
     return (i // (a * s)) * s + i % s
+
+
+def group_major(N: int, radices: Sequence[int], k: int) -> np.ndarray:
+    """pi(i) = g*a_k + r for i = 0..N-1: particles numbered group by group at a step on
+    digit k (g = group_index(i), r = digit k of i).  A permutation of 0..N-1."""
+    a = int(radices[k])
+    s = strides(radices)[k]
+    i = np.arange(N, dtype=np.int64)
+    return group_index(i, radices, k) * a + (i // s) % a

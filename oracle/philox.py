@@ -13,9 +13,15 @@ path) is:
 
     key  = (seed mod 2^32, seed div 2^32)
     init normals        ctr = (nu // 4, 0, 0, 0)   nu = i*d + t
-    propagation normals ctr = (nu // 4, n, 1, 0)   at time step n
-    resampling uniforms ctr = (i // 4, n, 2, 0)    word i % 4   (32-bit draws)
-    wide uniforms       ctr = (i // 2, n, 3, 0)    words 2(i%2), 2(i%2)+1 (64-bit draws)
+    propagation normals ctr = (nu // 4, n, 1, 0)   nu = pi*d + t, at time step n
+    resampling uniforms ctr = (pi // 4, n, 2, 0)   word pi % 4   (32-bit draws)
+    wide uniforms       ctr = (pi // 2, n, 3, 0)   words 2(pi%2), 2(pi%2)+1 (64-bit draws)
+
+where pi is particle i's *group-major* number at step n: with digit k = n mod m,
+pi = g*a_k + r, g = (i // (a_k s_k)) * s_k + i % s_k the index of i's group and
+r = (i // s_k) % a_k its digit k (see ``butterfly.group_major``).  Numbering the
+draws group by group lets one GPU thread that owns a group read its draws
+from consecutive counter blocks.
 
 Normals come in Box-Muller pairs: words (w0, w1) give normals 4c, 4c+1 and
 (w2, w3) give 4c+2, 4c+3 of counter block c, with

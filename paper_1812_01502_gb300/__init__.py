@@ -80,6 +80,7 @@ def load_library(path: str = LIB_PATH):
         "pf_get_ancestors": (i32, [vp, vp]),
         "pf_get_status": (i32, [vp, c.POINTER(u32)]),
         "pf_destroy": (i32, [vp]),
+        "pf_describe": (i32, [vp, c.c_char_p, c.c_size_t]),
         "pf_last_error": (c.c_char_p, [vp]),
         "pf_philox_blocks": (i32, [u64, u32, u32, u32, u32, i64, vp, vp]),
     }
@@ -271,6 +272,13 @@ class ButterflyFilter:
         _check(_lib.pf_get_state(self._h, x.ctypes.data_as(ctypes.c_void_p), lv.ctypes.data_as(ctypes.c_void_p),
                                  sc.ctypes.data_as(ctypes.c_void_p)), self._h)
         return x.T.copy(), lv, dict(n=int(sc[0]), loglik=float(sc[1]), mu=float(sc[2]), mu_used=float(sc[3]))
+
+    def describe(self) -> dict:
+        """The launch plan: per digit the kernel ('group' or 'tile'), lanes/tile and grid."""
+        import json
+        buf = ctypes.create_string_buffer(8192)
+        _check(_lib.pf_describe(self._h, buf, len(buf)), self._h)
+        return json.loads(buf.value.decode())
 
     def ancestors(self) -> np.ndarray:
         anc = np.empty(self.N, dtype=np.int32)

@@ -8,9 +8,12 @@
 //
 //   key = (seed mod 2^32, seed div 2^32)
 //   initial normals      counter (nu/4, 0, 0, 0),  nu = i*d + t
-//   propagation normals  counter (nu/4, n, 1, 0)   at time step n
-//   resampling uniforms  counter (i/4,  n, 2, 0)   word i%4         (groups of <= 256)
-//   wide uniforms        counter (i/2,  n, 3, 0)   words 2(i%2)+{0,1} (groups of > 256)
+//   propagation normals  counter (nu/4, n, 1, 0),  nu = pi*d + t   at time step n
+//   resampling uniforms  counter (pi/4, n, 2, 0)   word pi%4            (groups of <= 256)
+//   wide uniforms        counter (pi/2, n, 3, 0)   words 2(pi%2)+{0,1}  (groups of > 256)
+//
+// pi = g*a_k + r numbers the particles group by group at step n (digit k =
+// n mod m): g = (i / (a_k s_k)) s_k + i % s_k is i's group, r its digit k.
 //
 // Box-Muller pair (w0, w1) -> normals 4c, 4c+1 and (w2, w3) -> 4c+2, 4c+3 of
 // block c; u = (2*(w0>>9)+1) 2^-24 and v = (w1>>8) 2^-24 are exact FP32 values.
@@ -39,24 +42,50 @@ constexpr uint32_t kStatusZeroGroup = 2u;
 enum ModelKind : int { kLinearGaussian = 1, kStochVol = 2 };
 
 // ---------------------------------------------------------------------------
-// Philox4x32-10
+// Philox4x32-10.  The ten round keys (k0 + r W0, k1 + r W1) depend only on the
+// seed; kernels take them precomputed from their parameter block so that the
+// xor with the round key reads a constant operand.
 // ---------------------------------------------------------------------------
+struct RoundKeys {
+  uint32_t k[20];   // k[2r], k[2r+1]: round r
+};
+
+inline RoundKeys make_round_keys(uint64_t seed) {
+  RoundKeys rk;
+  uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
+  for (int r = 0; r < 10; ++r) {
+    rk.k[2 * r] = k0;
+    rk.k[2 * r + 1] = k1;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return rk;
+}
+
+__device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1) {
+  const uint64_t p0 = (uint64_t)c.x * 0xD2511F53u;
+  const uint64_t p1 = (uint64_t)c.z * 0xCD9E8D57u;
+  return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+}
+
+__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) c = philox_round(c, rk.k[2 * r], rk.k[2 * r + 1]);
+  return c;
+}
+
 __device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
   for (int r = 0; r < 10; ++r) {
-    if (r) {
-      k0 += 0x9E3779B9u;
-      k1 += 0xBB67AE85u;
-    }
-    const uint64_t p0 = (uint64_t)c.x * 0xD2511F53u;
-    const uint64_t p1 = (uint64_t)c.z * 0xCD9E8D57u;
-    c = make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1,
-                   (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
+    c = philox_round(c, k0, k1);
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
   }
   return c;
 }
 
-// Two standard normals from two 32-bit words (see the layout above).
+// Two standard normals from two 32-bit words (see the layout above), with
+// CUDA's full-precision logf / sqrtf / sincospif.
 __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, float& z1) {
   const float u = __uint2float_rn(((wa >> 9) << 1) | 1u) * 0x1p-24f;   // exact, in (0, 1)
   const float v = __uint2float_rn(wb >> 8) * 0x1p-24f;                 // exact, in [0, 1)
@@ -70,6 +99,36 @@ __device__ __forceinline__ void box_muller(uint32_t wa, uint32_t wb, float& z0, 
 __device__ __forceinline__ void normals4(uint4 w, float z[4]) {
   box_muller(w.x, w.y, z[0], z[1]);
   box_muller(w.z, w.w, z[2], z[3]);
+}
+
+// The same transform on the special-function units: -2 ln u from lg2.approx
+// (absolute error about 2^-22 in log2 u), except for u > 63/64 where
+// -ln u = t + t^2/2 + ... + t^6/6 with t = 1 - u (exact in FP32; truncation
+// below 4e-13 relative) keeps the small radii accurate; the angle is taken in
+// [-pi, pi) where sin/cos.approx have absolute error about 2^-21:
+// cos(2 pi v) = -cos(2 pi (v - 1/2)).  Normals differ from the full-precision
+// transform by < 4e-6 absolute.
+__device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float& z0, float& z1) {
+  const float u = __uint2float_rn(((wa >> 9) << 1) | 1u) * 0x1p-24f;
+  const float v = __uint2float_rn(wb >> 8) * 0x1p-24f;
+  float r2;
+  if (u > 0.984375f) {
+    const float t = 1.0f - u;
+    const float poly = fmaf(fmaf(fmaf(fmaf(fmaf(t, 1.0f / 6.0f, 0.2f), t, 0.25f), t, 1.0f / 3.0f), t, 0.5f), t, 1.0f);
+    r2 = 2.0f * t * poly;
+  } else {
+    r2 = -1.3862943611198906f * __log2f(u);   // -2 ln 2 log2 u
+  }
+  const float rad = r2 * rsqrtf(r2);
+  float s, c;
+  __sincosf(6.283185307179586f * (v - 0.5f), &s, &c);
+  z0 = -rad * c;
+  z1 = -rad * s;
+}
+
+__device__ __forceinline__ void normals4_fast(uint4 w, float z[4]) {
+  box_muller_fast(w.x, w.y, z[0], z[1]);
+  box_muller_fast(w.z, w.w, z[2], z[3]);
 }
 
 // ---------------------------------------------------------------------------
@@ -122,7 +181,18 @@ struct DigitGeom {
   uint32_t prev_s;    // stride of digit k-1 (mod m), whose groups carry the weights
   float log_a;        // log(a_k)
   uint32_t wide;      // a_k > kNarrowMaxRadix: 32-bit weights, 64-bit draws, 64-bit prefix sums
-  FastDiv div_nl, div_a, div_tiles_l, div_prev_as, div_prev_s;
+  FastDiv div_nl, div_a, div_tiles_l, div_prev_as, div_prev_s, div_tgroups;
+};
+
+// Geometry of one digit for the register-resident group kernel (power-of-two
+// radices): group g = h*s + l has members i = h*a*s + r*s + l; the carried
+// weight of member r is lV[((h*a + r)*lv_mul + (l & lv_lmask)) & lv_mask].
+struct GroupGeom {
+  uint32_t log2s;     // log2 s_k
+  uint32_t log2as;    // log2 (a_k s_k)
+  uint32_t nbatch;    // (N / a_k) / groups per thread block
+  uint32_t lv_mul, lv_lmask, lv_mask;
+  float log_a;
 };
 
 // ModelParams::flags: structure of the linear-Gaussian matrices (lets the
@@ -153,6 +223,7 @@ struct DevState {
 };
 
 struct StepParams {
+  RoundKeys rk;        // Philox round keys of the seed
   float* x;            // [d][N] particle states (updated in place)
   float* lV[2];        // carried log stage weights, ping-pong by time-step parity
   int32_t* anc;        // [N] ancestors of the last step (nullptr = not recorded)

@@ -12,8 +12,20 @@ struct KernelSet {
   const void* init;   // init_particles_kernel<D, KIND>(StepParams)
 };
 
-// Picks the compiled variant; false if (d, kind) is not supported.
+// Picks the compiled variant of the general kernel; false if (d, kind) is not supported.
 bool select_kernels(int d, int kind, bool wide, KernelSet& ks);
+
+// Register-resident group kernel step_group_kernel<d, kind, a, G>(StepParams, GroupGeom)
+// for a power-of-two radix a <= 32; sets *G (lanes per group).  nullptr if none.
+const void* select_group_kernel(int d, int kind, int a, int* G);
+const void* group_kernel_d1(int kind, int a, int* G);
+const void* group_kernel_d2(int kind, int a, int* G);
+const void* group_kernel_d3(int kind, int a, int* G);
+const void* group_kernel_d4(int kind, int a, int* G);
+const void* group_kernel_d5(int kind, int a, int* G);
+const void* group_kernel_d6(int kind, int a, int* G);
+const void* group_kernel_d7(int kind, int a, int* G);
+const void* group_kernel_d8(int kind, int a, int* G);
 
 cudaError_t launch_philox_blocks(uint64_t seed, uint4 c, uint32_t count, uint32_t* out,
                                  cudaStream_t stream);

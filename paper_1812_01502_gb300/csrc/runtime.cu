@@ -31,6 +31,16 @@ struct Layout {
   size_t st, x, lv0, lv1, anc, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
 };
 
+// The kernel that runs the steps on one digit.
+struct DigitPlan {
+  const void* kernel = nullptr;
+  bool group = false;         // register-resident group kernel (else the general tile kernel)
+  int lanes = 0;              // lanes per group (group kernel)
+  GroupGeom gg{};
+  int grid = 0;
+  size_t smem = 0;            // dynamic shared memory (general kernel)
+};
+
 struct Plan {
   int d = 0, dy = 0, kind = 0, m = 0;
   uint32_t N = 0;
@@ -45,6 +55,8 @@ struct Plan {
   KernelSet ks{};
   ModelParams mp{};
   DigitGeom geom[kMaxDigits]{};
+  DigitPlan dp[kMaxDigits]{};
+  int max_grid = 0;
   Layout lay{};
 };
 
@@ -61,8 +73,7 @@ struct pf_handle {
   StepParams P{};
   uint64_t n_host = 0;     // time steps enqueued
   uint64_t n_pushed = 0;   // observations copied into the ring
-  cudaGraphExec_t graph = nullptr;
-  int graph_len = 0;
+  std::vector<cudaGraphExec_t> graphs;   // chunk graphs, one per radix phase (n mod m)
   std::string err;
 };
 
@@ -241,6 +252,44 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     g.div_prev_as = make_fastdiv(pl.geom[kp].a * pl.geom[kp].s);
     g.div_prev_s = make_fastdiv(pl.geom[kp].s);
   }
+  for (int k = 0; k < m; ++k) pl.geom[k].div_tgroups = make_fastdiv(pl.geom[k].nh * pl.geom[k].nl);
+  // Register-resident group kernel: every radix a power of two, a_k <= 32, and the
+  // groups of digit k fill whole thread-block iterations.
+  bool pow2 = true;
+  for (int k = 0; k < m; ++k) pow2 = pow2 && ((radices[k] & (radices[k] - 1)) == 0);
+  for (int k = 0; k < m; ++k) {
+    DigitPlan& dp = pl.dp[k];
+    const DigitGeom& g = pl.geom[k];
+    int G = 0;
+    const void* gk = (pow2 && g.a <= 32) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G) : nullptr;
+    if (gk && G > 0) {
+      const uint32_t gpb = kBlock / G;
+      const uint32_t ngroups = pl.N / g.a;
+      if (ngroups % gpb == 0) {
+        dp.kernel = gk;
+        dp.group = true;
+        dp.lanes = G;
+        uint32_t l2s = 0, l2as = 0;
+        while ((1u << l2s) < g.s) ++l2s;
+        while ((1u << l2as) < g.a * g.s) ++l2as;
+        dp.gg.log2s = l2s;
+        dp.gg.log2as = l2as;
+        dp.gg.nbatch = ngroups / gpb;
+        const int kp = (k + m - 1) % m;
+        const uint32_t sp = pl.geom[kp].s;
+        if (k == 0) {
+          dp.gg.lv_mul = 1;
+          dp.gg.lv_lmask = 0;
+          dp.gg.lv_mask = sp - 1;       // s_{m-1} = N / a_{m-1}
+        } else {
+          dp.gg.lv_mul = sp;
+          dp.gg.lv_lmask = sp - 1;
+          dp.gg.lv_mask = 0xffffffffu;
+        }
+        dp.gg.log_a = g.log_a;
+      }
+    }
+  }
   pl.cap = (pl.cap + 3) / 4 * 4;
   pl.smem = (size_t)(d + 1) * pl.cap * 4 + (size_t)pl.cap * (pl.wide ? 8 : 4);
   pl.record = opts && (opts->flags & PF_RECORD_ANCESTORS);
@@ -259,8 +308,25 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pl.ks.step, kBlock, pl.smem);
   if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
   if (nb < 1) { msg = "tile does not fit in shared memory; choose a smaller tile"; return PF_EINVAL; }
-  int grid = (opts && opts->grid > 0) ? opts->grid : nb * sms;
-  grid = std::max(1, std::min<int>(grid, (int)pl.max_tiles));
+  pl.max_grid = 0;
+  for (int k = 0; k < pl.m; ++k) {
+    DigitPlan& dp = pl.dp[k];
+    int units = 0, per_sm = 0;
+    if (dp.group) {
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, dp.kernel, kBlock, 0);
+      if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
+      units = (int)dp.gg.nbatch;
+    } else {
+      dp.kernel = pl.ks.step;
+      dp.smem = pl.smem;
+      per_sm = nb;
+      units = (int)pl.geom[k].ntiles;
+    }
+    int grid = (opts && opts->grid > 0) ? opts->grid : std::max(1, per_sm) * sms;
+    dp.grid = std::max(1, std::min(grid, units));
+    pl.max_grid = std::max(pl.max_grid, dp.grid);
+  }
+  const int grid = pl.max_grid;
   pl.grid = grid;
   Layout& L = pl.lay;
   size_t off = 0;
@@ -279,9 +345,15 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   return PF_OK;
 }
 
-cudaError_t launch_step(pf_handle* h, cudaStream_t stream) {
+// Launch the step kernel for time step n (digit n mod m).
+cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t n) {
+  DigitPlan& dp = h->plan.dp[n % (uint64_t)h->plan.m];
+  if (dp.group) {
+    void* args[] = {&h->P, &dp.gg};
+    return cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, 0, stream);
+  }
   void* args[] = {&h->P};
-  return cudaLaunchKernel(h->plan.ks.step, dim3(h->plan.grid), dim3(kBlock), args, h->plan.smem, stream);
+  return cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, dp.smem, stream);
 }
 
 }  // namespace
@@ -358,6 +430,7 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   P.m = pl.m;
   P.seed_lo = (uint32_t)seed;
   P.seed_hi = (uint32_t)(seed >> 32);
+  P.rk = make_round_keys(seed);
   P.tile_cap = pl.cap;
   P.inv_N = (float)(1.0 / pl.N);
   P.model = pl.mp;
@@ -414,29 +487,33 @@ pf_status pf_push_observations(pf_handle* h, const float* y, int32_t T) {
 
 namespace {
 
-// L steps on pushed observations: a captured graph when L is the chunk length.
+// L steps on pushed observations, starting at step h->n_host: a captured graph
+// (one per radix phase n mod m, since the kernel depends on the digit) when L
+// is the chunk length, else individual launches.
 pf_status enqueue_steps(pf_handle* h, int32_t L) {
   const Plan& pl = h->plan;
+  const uint64_t n0 = h->n_host;
   if (L == pl.chunk_len && L > 1) {
-    if (!h->graph) {
+    if (h->graphs.empty()) h->graphs.assign(pl.m, nullptr);
+    cudaGraphExec_t& exec = h->graphs[n0 % (uint64_t)pl.m];
+    if (!exec) {
       cudaGraph_t graph = nullptr;
       PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t le = cudaSuccess;
-      for (int j = 0; j < L && le == cudaSuccess; ++j) le = launch_step(h, h->cap_stream);
+      for (int j = 0; j < L && le == cudaSuccess; ++j) le = launch_step(h, h->cap_stream, n0 + j);
       cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
       if (le != cudaSuccess) return fail(h, PF_ECUDA, std::string("capture launch: ") + cudaGetErrorString(le));
       if (ce != cudaSuccess) return fail(h, PF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
-      cudaError_t ie = cudaGraphInstantiate(&h->graph, graph, 0);
+      cudaError_t ie = cudaGraphInstantiate(&exec, graph, 0);
       cudaGraphDestroy(graph);
       if (ie != cudaSuccess) {
-        h->graph = nullptr;
+        exec = nullptr;
         return fail(h, PF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
       }
-      h->graph_len = L;
     }
-    PF_CUDA(h, cudaGraphLaunch(h->graph, h->stream));
+    PF_CUDA(h, cudaGraphLaunch(exec, h->stream));
   } else {
-    for (int j = 0; j < L; ++j) PF_CUDA(h, launch_step(h, h->stream));
+    for (int j = 0; j < L; ++j) PF_CUDA(h, launch_step(h, h->stream, n0 + j));
   }
   return PF_OK;
 }
@@ -537,10 +614,32 @@ pf_status pf_get_status(const pf_handle* h, uint32_t* bits) {
   return PF_OK;
 }
 
+pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
+  if (!h || !buf || len == 0) return fail(h, PF_EINVAL, "NULL argument");
+  const Plan& pl = h->plan;
+  std::string o = "{\"N\": " + std::to_string(pl.N) + ", \"d\": " + std::to_string(pl.d) +
+                  ", \"digits\": [";
+  for (int k = 0; k < pl.m; ++k) {
+    const DigitPlan& dp = pl.dp[k];
+    const DigitGeom& g = pl.geom[k];
+    if (k) o += ", ";
+    o += "{\"a\": " + std::to_string(g.a) + ", \"s\": " + std::to_string(g.s) + ", \"kernel\": \"" +
+         (dp.group ? "group" : "tile") + "\", " +
+         (dp.group ? "\"lanes\": " + std::to_string(dp.lanes) : "\"tile\": " + std::to_string(g.tile_n)) +
+         ", \"grid\": " + std::to_string(dp.grid) + "}";
+  }
+  o += "]}";
+  const size_t nb = std::min(len - 1, o.size());
+  std::memcpy(buf, o.data(), nb);
+  buf[nb] = 0;
+  return PF_OK;
+}
+
 pf_status pf_destroy(pf_handle* h) {
   if (!h) return PF_OK;
   cudaError_t e = cudaStreamSynchronize(h->stream);
-  if (h->graph) cudaGraphExecDestroy(h->graph);
+  for (cudaGraphExec_t g : h->graphs)
+    if (g) cudaGraphExecDestroy(g);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
   if (h->own_ws && h->ws) cudaFree(h->ws);
   delete h;

@@ -15,125 +15,26 @@
 // digits below k.  Tile position p = row*nl + col, row = hh*a_k + r; global
 // index i = base + row*s_k + col.  Each row is a contiguous run of nl states.
 //
+// This is the general kernel (any radix up to 1024, mixed radices that are
+// not powers of two); step_group.cuh holds the faster register-resident
+// kernel used for power-of-two radices up to 32.
+//
 // Integer resampling rule (shared specification with the oracle):
 //   delta = fp32(lw - max_G lw), e = exp(delta) (FP32), q = floor(e 2^B)
 //   (B = 24, or 32 for groups > 256), P = inclusive prefix over the group,
 //   u = floor(r Q / 2^32) (or r Q / 2^64), ancestor = #{j : P_j <= u}.
+// Random words are numbered group-major (pi = g a + r, see bfpf_device.cuh).
 #include <cfloat>
 #include <type_traits>
 
 #include "bfpf_device.cuh"
+#include "bfpf_epilogue.cuh"
 #include "bfpf_kernels.h"
+#include "bfpf_model.cuh"
 
 namespace bfpf {
 
 namespace {
-
-template <int D, int KIND>
-__device__ __forceinline__ float obs_log_term(const ModelParams& mp, const float* y, const float* x) {
-  if constexpr (KIND == kStochVol) {
-    // log g - c = -x/2 - y^2 exp(-x) / (2 beta^2)
-    return fmaf(-0.5f, x[0], -(y[0] * y[0]) * __expf(-x[0]) * mp.inv2b2);
-  } else {
-    // log g - c = -1/2 || Lr^{-1} (y - H x) ||^2
-    float r[kMaxDim];
-#pragma unroll
-    for (int j = 0; j < kMaxDim; ++j) {
-      if (j < mp.dy) {
-        float acc = y[j];
-        if (mp.flags & kHIdentity) {          // H is the identity
-          acc -= (j < D) ? x[j] : 0.0f;
-        } else {
-#pragma unroll
-          for (int t = 0; t < D; ++t) acc = fmaf(-mp.H[j * kMaxDim + t], x[t], acc);
-        }
-        r[j] = acc;
-      }
-    }
-    float ss = 0.0f;
-    if (mp.flags & kLrDiagonal) {              // Lr diagonal
-#pragma unroll
-      for (int j = 0; j < kMaxDim; ++j)
-        if (j < mp.dy) {
-          const float z = mp.Lri[j * kMaxDim + j] * r[j];
-          ss = fmaf(z, z, ss);
-        }
-    } else {
-#pragma unroll
-      for (int j = 0; j < kMaxDim; ++j)
-        if (j < mp.dy) {
-          float z = 0.0f;
-#pragma unroll
-          for (int u = 0; u <= j; ++u) z = fmaf(mp.Lri[j * kMaxDim + u], r[u], z);
-          ss = fmaf(z, z, ss);
-        }
-    }
-    return -0.5f * ss;
-  }
-}
-
-// zeta' = A xhat + Lq z  (linear-Gaussian)  or  phi xhat + sigma z  (SV)
-template <int D, int KIND>
-__device__ __forceinline__ void mutate(const ModelParams& mp, const float* xh, const float* z, float* out) {
-  if constexpr (KIND == kStochVol) {
-    out[0] = fmaf(mp.phi, xh[0], mp.sigma * z[0]);
-  } else {
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-      float acc = 0.0f;
-      if (mp.flags & kADiagonal) {            // A diagonal
-        acc = mp.A[t * kMaxDim + t] * xh[t];
-      } else {
-#pragma unroll
-        for (int u = 0; u < D; ++u) acc = fmaf(mp.A[t * kMaxDim + u], xh[u], acc);
-      }
-      if (mp.flags & kLqDiagonal) {            // Lq diagonal
-        acc = fmaf(mp.Lq[t * kMaxDim + t], z[t], acc);
-      } else {
-#pragma unroll
-        for (int u = 0; u <= t; ++u) acc = fmaf(mp.Lq[t * kMaxDim + u], z[u], acc);
-      }
-      out[t] = acc;
-    }
-  }
-}
-
-struct Partial {
-  float m, s1, s2;
-};
-
-// Merge a group's (max, sums) into the running block partial, rescaling to the larger max.
-template <int D>
-__device__ __forceinline__ void merge_partial(Partial& acc, float* accx, float m, float s1, float s2,
-                                              const float* sx) {
-  if (m == -INFINITY) return;
-  if (m > acc.m) {
-    const float sc = expf(acc.m - m);
-    acc.s1 = fmaf(acc.s1, sc, s1);
-    acc.s2 = fmaf(acc.s2, sc * sc, s2);
-#pragma unroll
-    for (int t = 0; t < D; ++t) accx[t] = fmaf(accx[t], sc, sx[t]);
-    acc.m = m;
-  } else {
-    const float sc = expf(m - acc.m);
-    acc.s1 = fmaf(s1, sc, acc.s1);
-    acc.s2 = fmaf(s2, sc * sc, acc.s2);
-#pragma unroll
-    for (int t = 0; t < D; ++t) accx[t] = fmaf(sx[t], sc, accx[t]);
-  }
-}
-
-template <int D>
-__device__ __forceinline__ void shfl_merge(Partial& acc, float* accx, int off) {
-  Partial o;
-  o.m = __shfl_down_sync(0xffffffffu, acc.m, off);
-  o.s1 = __shfl_down_sync(0xffffffffu, acc.s1, off);
-  o.s2 = __shfl_down_sync(0xffffffffu, acc.s2, off);
-  float ox[D];
-#pragma unroll
-  for (int t = 0; t < D; ++t) ox[t] = __shfl_down_sync(0xffffffffu, accx[t], off);
-  merge_partial<D>(acc, accx, o.m, o.s1, o.s2, ox);
-}
 
 __device__ __forceinline__ unsigned long long mulhi64(unsigned long long a, unsigned long long b) {
   return __umul64hi(a, b);
@@ -144,11 +45,7 @@ __device__ __forceinline__ unsigned long long mulhi64(unsigned long long a, unsi
 template <int D, int KIND, bool WIDE>
 __global__ void __launch_bounds__(kBlock) step_butterfly_kernel(const __grid_constant__ StepParams p) {
   using PT = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
-  constexpr int NP = 3 + D;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ float s_red[kBlock / 32][NP];
-  __shared__ float s_redlo[kBlock / 32][NP];
-  __shared__ uint32_t s_last;
 
   const uint32_t tid = threadIdx.x;
   const uint32_t cap = p.tile_cap;
@@ -171,6 +68,7 @@ __global__ void __launch_bounds__(kBlock) step_butterfly_kernel(const __grid_con
 #pragma unroll
   for (int j = 0; j < kMaxDim; ++j) y[j] = (j < mp.dy) ? p.y_ring[(n % kRing) * mp.dy + j] : 0.0f;
   uint32_t status = 0;
+  const uint32_t ngroups = g.nh * nl;   // groups per tile
 
   // lifting steps of the ancestor search: largest power of two < a (0 if a == 1)
   uint32_t step0 = 1;
@@ -222,17 +120,11 @@ __global__ void __launch_bounds__(kBlock) step_butterfly_kernel(const __grid_con
       float xv[D];
 #pragma unroll
       for (int t = 0; t < D; ++t) xv[t] = s_x[t * cap + pos];
-      float lw = lv + obs_log_term<D, KIND>(mp, y, xv) - muf;
-      if (lw != lw || lw == INFINITY) {
-        lw = -INFINITY;
-        status |= kStatusNonFinite;
-      }
-      s_lw[pos] = lw;
+      s_lw[pos] = sanitize_logweight(lv + obs_log_term<D, KIND>(mp, y, xv) - muf, status);
     }
     __syncthreads();
 
     // ---- per group: max, log-sum-exp, integer weights and prefix sums ----
-    const uint32_t ngroups = g.nh * nl;
     for (uint32_t gid = tid; gid < ngroups; gid += kBlock) {
       const uint32_t hh = fdiv(gid, g.div_nl);
       const uint32_t col = gid - hh * nl;
@@ -270,87 +162,72 @@ __global__ void __launch_bounds__(kBlock) step_butterfly_kernel(const __grid_con
     }
     __syncthreads();
 
-    // ---- draw ancestors, gather from shared memory, mutate, store ----
-    const uint32_t key0 = p.seed_lo, key1 = p.seed_hi;
-    if (g.quad) {
-      for (uint32_t q = tid; q < (tn >> 2); q += kBlock) {
-        const uint32_t pos0 = q << 2;
-        const uint32_t row0 = fdiv(pos0, g.div_nl);
-        const uint32_t i0 = base + row0 * s + (pos0 - row0 * nl);
-        uint32_t rw[4] = {0u, 0u, 0u, 0u};
-        unsigned long long rw64[4] = {0ull, 0ull, 0ull, 0ull};
+    // ---- draw ancestors (group-major counters), gather, mutate, store ----
+    // Work item = (member quad rq, group gid of the tile); consecutive threads
+    // take consecutive groups, i.e. consecutive columns of a row.
+    const uint32_t nq = (a + 3) >> 2;
+    const bool a4 = (a & 3u) == 0;
+    for (uint32_t it = tid; it < ngroups * nq; it += kBlock) {
+      const uint32_t rq = fdiv(it, g.div_tgroups);
+      const uint32_t gid = it - rq * ngroups;
+      const uint32_t hh = fdiv(gid, g.div_nl);
+      const uint32_t col = gid - hh * nl;
+      const uint32_t gb = hh * a * nl + col;                 // tile position of member 0
+      const uint32_t gc = (h0 + hh) * s + l0 + col;          // group index h*s + l
+      const uint32_t ib = base + hh * a * s + col;           // global index of member 0
+      const PT Q = s_P[gb + (a - 1) * nl];
+      const uint32_t r0 = rq << 2;
+      const uint32_t pi0 = gc * a + r0;
+      uint32_t rw[4] = {0u, 0u, 0u, 0u};
+      unsigned long long rw64[4] = {0ull, 0ull, 0ull, 0ull};
+      float z[4 * D];
+      if (a4) {   // pi0 % 4 == 0: whole counter blocks
         if (WIDE && wide_digit) {
-          const uint4 w0 = philox4x32_10(make_uint4(i0 >> 1, n, kPurposeResampleWide, 0), key0, key1);
-          const uint4 w1 = philox4x32_10(make_uint4((i0 >> 1) + 1, n, kPurposeResampleWide, 0), key0, key1);
+          const uint4 w0 = philox4x32_10(make_uint4(pi0 >> 1, n, kPurposeResampleWide, 0), p.rk);
+          const uint4 w1 = philox4x32_10(make_uint4((pi0 >> 1) + 1, n, kPurposeResampleWide, 0), p.rk);
           rw64[0] = ((unsigned long long)w0.y << 32) | w0.x;
           rw64[1] = ((unsigned long long)w0.w << 32) | w0.z;
           rw64[2] = ((unsigned long long)w1.y << 32) | w1.x;
           rw64[3] = ((unsigned long long)w1.w << 32) | w1.z;
         } else {
-          const uint4 w = philox4x32_10(make_uint4(i0 >> 2, n, kPurposeResample, 0), key0, key1);
+          const uint4 w = philox4x32_10(make_uint4(pi0 >> 2, n, kPurposeResample, 0), p.rk);
           rw[0] = w.x; rw[1] = w.y; rw[2] = w.z; rw[3] = w.w;
         }
-        float z[4 * D];
 #pragma unroll
         for (int b = 0; b < D; ++b) {
-          const uint4 w = philox4x32_10(make_uint4((i0 >> 2) * D + b, n, kPurposePropagate, 0), key0, key1);
+          const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), p.rk);
           normals4(w, z + 4 * b);
         }
-        float outv[D][4];
+      } else {    // members straddle counter blocks: one block per draw / normal
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const uint32_t pos = pos0 + j;
-          const uint32_t row = fdiv(pos, g.div_nl);
-          const uint32_t col = pos - row * nl;
-          const uint32_t hh = fdiv(row, g.div_a);
-          const uint32_t r = row - hh * a;
-          const uint32_t gb = hh * a * nl + col;
-          const PT Q = s_P[gb + (a - 1) * nl];
-          PT u;
-          if (WIDE && wide_digit) u = (PT)mulhi64(rw64[j], (unsigned long long)Q);
-          else u = (PT)(((unsigned long long)rw[j] * Q) >> 32);
-          uint32_t c = 0;
-          for (uint32_t stp = step0; stp; stp >>= 1) {
-            const uint32_t cand = c + stp;
-            if (cand <= a - 1 && s_P[gb + (cand - 1) * nl] <= u) c = cand;
+        for (int jj = 0; jj < 4; ++jj) {
+          const uint32_t pi = pi0 + jj;
+          if (r0 + jj >= a) break;
+          if (WIDE && wide_digit) {
+            const uint4 w = philox4x32_10(make_uint4(pi >> 1, n, kPurposeResampleWide, 0), p.rk);
+            rw64[jj] = (pi & 1u) ? (((unsigned long long)w.w << 32) | w.z) : (((unsigned long long)w.y << 32) | w.x);
+          } else {
+            const uint4 w = philox4x32_10(make_uint4(pi >> 2, n, kPurposeResample, 0), p.rk);
+            const uint32_t sel = pi & 3u;
+            rw[jj] = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
           }
-          if (Q == 0) c = r;
-          const uint32_t pa = gb + c * nl;
-          float xh[D];
 #pragma unroll
-          for (int t = 0; t < D; ++t) xh[t] = s_x[t * cap + pa];
-          float xo[D];
-          mutate<D, KIND>(mp, xh, z + j * D, xo);
-#pragma unroll
-          for (int t = 0; t < D; ++t) outv[t][j] = xo[t];
-          if (p.anc) p.anc[i0 + j] = (int32_t)(i0 + j + (c - r) * s);
+          for (int t = 0; t < D; ++t) {
+            const uint32_t nu = pi * D + t;
+            const uint4 w = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
+            float zz[4];
+            normals4(w, zz);
+            z[jj * D + t] = zz[nu & 3u];
+          }
         }
-#pragma unroll
-        for (int t = 0; t < D; ++t)
-          __stcs(reinterpret_cast<float4*>(p.x + (size_t)t * N + i0),
-                 make_float4(outv[t][0], outv[t][1], outv[t][2], outv[t][3]));
       }
-    } else {
-      for (uint32_t pos = tid; pos < tn; pos += kBlock) {
-        const uint32_t row = fdiv(pos, g.div_nl);
-        const uint32_t col = pos - row * nl;
-        const uint32_t i = base + row * s + col;
-        const uint32_t hh = fdiv(row, g.div_a);
-        const uint32_t r = row - hh * a;
-        const uint32_t gb = hh * a * nl + col;
-        const PT Q = s_P[gb + (a - 1) * nl];
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const uint32_t r = r0 + jj;
+        if (r >= a) break;
         PT u;
-        if (WIDE && wide_digit) {
-          const uint4 w = philox4x32_10(make_uint4(i >> 1, n, kPurposeResampleWide, 0), key0, key1);
-          const unsigned long long r64 = (i & 1u) ? (((unsigned long long)w.w << 32) | w.z)
-                                                  : (((unsigned long long)w.y << 32) | w.x);
-          u = (PT)mulhi64(r64, (unsigned long long)Q);
-        } else {
-          const uint4 w = philox4x32_10(make_uint4(i >> 2, n, kPurposeResample, 0), key0, key1);
-          const uint32_t sel = i & 3u;
-          const uint32_t rr = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
-          u = (PT)(((unsigned long long)rr * Q) >> 32);
-        }
+        if (WIDE && wide_digit) u = (PT)mulhi64(rw64[jj], (unsigned long long)Q);
+        else u = (PT)(((unsigned long long)rw[jj] * Q) >> 32);
         uint32_t c = 0;
         for (uint32_t stp = step0; stp; stp >>= 1) {
           const uint32_t cand = c + stp;
@@ -358,134 +235,19 @@ __global__ void __launch_bounds__(kBlock) step_butterfly_kernel(const __grid_con
         }
         if (Q == 0) c = r;
         const uint32_t pa = gb + c * nl;
-        float xh[D], z[D], xo[D];
+        float xh[D], xo[D];
 #pragma unroll
-        for (int t = 0; t < D; ++t) {
-          xh[t] = s_x[t * cap + pa];
-          const uint32_t nu = i * D + t;
-          const uint4 w = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), key0, key1);
-          float zz[4];
-          normals4(w, zz);
-          z[t] = zz[nu & 3u];
-        }
-        mutate<D, KIND>(mp, xh, z, xo);
+        for (int t = 0; t < D; ++t) xh[t] = s_x[t * cap + pa];
+        mutate<D, KIND>(mp, xh, z + jj * D, xo);
+        const uint32_t i = ib + r * s;
 #pragma unroll
         for (int t = 0; t < D; ++t) __stcs(p.x + (size_t)t * N + i, xo[t]);
-        if (p.anc) p.anc[i] = (int32_t)(i + (c - r) * s);
+        if (p.anc) p.anc[i] = (int32_t)(ib + c * s);
       }
     }
   }
 
-  // ---- block partial -> global; the last block finishes the step ----
-  if (status) atomicOr(&st->status, status);
-  const uint32_t lane = tid & 31u, warp = tid >> 5;
-#pragma unroll
-  for (int off = 16; off; off >>= 1) shfl_merge<D>(acc, accx, off);
-  if (lane == 0) {
-    s_red[warp][0] = acc.m;
-    s_red[warp][1] = acc.s1;
-    s_red[warp][2] = acc.s2;
-#pragma unroll
-    for (int t = 0; t < D; ++t) s_red[warp][3 + t] = accx[t];
-  }
-  __syncthreads();
-  if (tid == 0) {
-    Partial b{-INFINITY, 0.0f, 0.0f};
-    float bx[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t) bx[t] = 0.0f;
-    for (int w = 0; w < kBlock / 32; ++w) merge_partial<D>(b, bx, s_red[w][0], s_red[w][1], s_red[w][2], &s_red[w][3]);
-    float* out = p.partials + (size_t)blockIdx.x * NP;
-    out[0] = b.m;
-    out[1] = b.s1;
-    out[2] = b.s2;
-#pragma unroll
-    for (int t = 0; t < D; ++t) out[3 + t] = bx[t];
-    __threadfence();
-    const uint32_t prev = atomicAdd(&st->done, 1u);
-    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  if (!s_last) return;
-  __threadfence();
-
-  // Last block: combine all block partials in a fixed order with compensated
-  // FP32 sums, then finish in FP64.
-  const uint32_t G = gridDim.x;
-  float Mx = -INFINITY;
-  for (uint32_t b = tid; b < G; b += kBlock) Mx = fmaxf(Mx, __ldcg(p.partials + (size_t)b * NP));
-#pragma unroll
-  for (int off = 16; off; off >>= 1) Mx = fmaxf(Mx, __shfl_xor_sync(0xffffffffu, Mx, off));
-  if (lane == 0) s_red[warp][0] = Mx;
-  __syncthreads();
-  Mx = s_red[0][0];
-  for (int w = 1; w < kBlock / 32; ++w) Mx = fmaxf(Mx, s_red[w][0]);
-  __syncthreads();
-
-  float hi[NP - 1], lo[NP - 1];
-#pragma unroll
-  for (int v = 0; v < NP - 1; ++v) hi[v] = lo[v] = 0.0f;
-  if (Mx != -INFINITY) {
-    for (uint32_t b = tid; b < G; b += kBlock) {
-      const float* pb = p.partials + (size_t)b * NP;
-      const float mb = __ldcg(pb);
-      if (mb == -INFINITY) continue;
-      const float w = expf(mb - Mx);
-      ff_add(hi[0], lo[0], __ldcg(pb + 1) * w);
-      ff_add(hi[1], lo[1], __ldcg(pb + 2) * (w * w));
-#pragma unroll
-      for (int t = 0; t < D; ++t) ff_add(hi[2 + t], lo[2 + t], __ldcg(pb + 3 + t) * w);
-    }
-  }
-#pragma unroll
-  for (int off = 16; off; off >>= 1) {
-#pragma unroll
-    for (int v = 0; v < NP - 1; ++v) {
-      const float oh = __shfl_down_sync(0xffffffffu, hi[v], off);
-      const float ol = __shfl_down_sync(0xffffffffu, lo[v], off);
-      ff_add(hi[v], lo[v], oh);
-      lo[v] += ol;
-    }
-  }
-  if (lane == 0) {
-#pragma unroll
-    for (int v = 0; v < NP - 1; ++v) {
-      s_red[warp][v] = hi[v];
-      s_redlo[warp][v] = lo[v];
-    }
-  }
-  __syncthreads();
-  if (tid == 0) {
-    double S[NP - 1];
-    for (int v = 0; v < NP - 1; ++v) {
-      float h = 0.0f, l = 0.0f;
-      for (int w = 0; w < kBlock / 32; ++w) {
-        ff_add(h, l, s_red[w][v]);
-        l += s_redlo[w][v];
-      }
-      S[v] = (double)h + (double)l;
-    }
-    const uint32_t slot = n % kRing;
-    double lme, inc, ess;
-    if (Mx == -INFINITY || !(S[0] > 0.0)) {
-      lme = -INFINITY;
-      inc = -INFINITY;
-      ess = 0.0;
-    } else {
-      lme = (double)Mx + log(S[0] * (double)p.inv_N);
-      inc = lme + ((double)muf - st->mu) + mp.c_obs;
-      ess = S[0] * S[0] / ((double)N * S[1]);
-    }
-    p.inc_ring[slot] = inc;
-    p.ess_ring[slot] = (float)ess;
-    for (int t = 0; t < D; ++t) p.mean_ring[slot * mp.d + t] = (float)(S[2 + t] / S[0]);
-    st->loglik += inc;
-    st->mu = lme;
-    st->mu_f = (float)lme;
-    st->done = 0;
-    __threadfence();
-    st->n = n + 1;
-  }
+  finish_step<D>(p, acc, accx, n, status, muf);
 }
 
 // Initial particles zeta_0 ~ pi_0 (Algorithm 1, first loop).
@@ -497,7 +259,7 @@ __global__ void __launch_bounds__(kBlock) init_particles_kernel(const __grid_con
 #pragma unroll
     for (int t = 0; t < D; ++t) {
       const uint32_t nu = i * D + t;
-      const uint4 w = philox4x32_10(make_uint4(nu >> 2, 0, kPurposeInit, 0), p.seed_lo, p.seed_hi);
+      const uint4 w = philox4x32_10(make_uint4(nu >> 2, 0, kPurposeInit, 0), p.rk);
       float zz[4];
       normals4(w, zz);
       z[t] = zz[nu & 3u];
@@ -558,6 +320,20 @@ bool select_kernels(int d, int kind, bool wide, KernelSet& ks) {
       return false;
   }
 #undef BFPF_CASE
+}
+
+const void* select_group_kernel(int d, int kind, int a, int* G) {
+  switch (d) {
+    case 1: return group_kernel_d1(kind, a, G);
+    case 2: return group_kernel_d2(kind, a, G);
+    case 3: return group_kernel_d3(kind, a, G);
+    case 4: return group_kernel_d4(kind, a, G);
+    case 5: return group_kernel_d5(kind, a, G);
+    case 6: return group_kernel_d6(kind, a, G);
+    case 7: return group_kernel_d7(kind, a, G);
+    case 8: return group_kernel_d8(kind, a, G);
+    default: return nullptr;
+  }
 }
 
 cudaError_t launch_philox_blocks(uint64_t seed, uint4 c, uint32_t count, uint32_t* out, cudaStream_t stream) {

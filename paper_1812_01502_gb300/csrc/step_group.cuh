@@ -1,0 +1,302 @@
+// step_group.cuh - one time step of the butterfly particle filter with the
+// interaction groups held in registers (power-of-two radix A <= 32).
+//
+// Paper: Heine, Whiteley & Cemgil, arXiv 1812.01502.  Time step n is the loop
+// body of Algorithm 1 with ONE stage of Algorithm 3 on digit k = n mod m:
+//   weight     lw_i = log V_i + log g_n(zeta_i) - mu           (V_0 = g)
+//   stage      V'_G = A^-1 sum_{j in G} V_j                     (eq. (V_defn_proofs))
+//   resample   xi_i ~ sum_{j in G(i)} V_j delta_{zeta_j} / sum V_j   (integer rule)
+//   mutate     zeta'_i ~ f(xi_i, .)                             (Algorithm 1)
+//
+// Work mapping: a group of A members (the A particles sharing every digit
+// but k) is owned by G consecutive lanes of one warp, each holding M = A/G
+// members in registers: group max / sums by xor-shuffles, the integer prefix
+// sum by an in-thread scan plus a shuffle scan over the G lanes.  Prefix sums
+// and states are staged in shared memory in a [member][group] layout so that
+// the ancestor search and the gather read different banks across a warp.
+// Only warp-level synchronisation is needed inside the loop.  Loads and
+// stores go straight to global memory: for a fixed member, consecutive lanes
+// own consecutive groups, i.e. consecutive addresses when s_k >= 32.
+//
+// Integer resampling rule (shared with the oracle): delta = fp32(lw - max),
+// e = exp(delta), q = floor(e 2^24), P = inclusive prefix, Q = P_{A-1},
+// u = floor(r Q / 2^32), ancestor = #{j : P_j <= u} (binary lifting).
+#pragma once
+
+#include "bfpf_device.cuh"
+#include "bfpf_epilogue.cuh"
+#include "bfpf_model.cuh"
+
+namespace bfpf {
+
+template <int D, int KIND, int A, int G>
+__global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constant__ StepParams p,
+                                                           const __grid_constant__ GroupGeom gg) {
+  static_assert(A >= 2 && A <= 32 && (A & (A - 1)) == 0, "radix must be a power of two <= 32");
+  static_assert(G >= 1 && G <= A && A % G == 0, "bad lanes per group");
+  constexpr int M = A / G;                 // members per lane
+  constexpr int GPB = kBlock / G;          // groups per block iteration
+  constexpr int LD = GPB + (G > 1 ? 1 : 0);
+  constexpr unsigned FULL = 0xffffffffu;
+  // s_tab[r * LD + tg]: prefix sums of group tg; s_tab[(A + t * A + r) * LD + tg]: states
+  __shared__ uint32_t s_tab[(1 + D) * A * LD];
+
+  const uint32_t tid = threadIdx.x;
+  const uint32_t tg = tid / G, j = tid % G;
+  const ModelParams& mp = p.model;
+  DevState* st = p.st;
+  const uint32_t n = st->n;
+  const float* __restrict__ lV_in = p.lV[n & 1u];
+  float* __restrict__ lV_out = p.lV[(n & 1u) ^ 1u];
+  float* __restrict__ X = p.x;
+  const float muf = st->mu_f;
+  const uint32_t N = p.N;
+  float y[kMaxDim];
+#pragma unroll
+  for (int q = 0; q < kMaxDim; ++q) y[q] = (q < mp.dy) ? p.y_ring[(n % kRing) * mp.dy + q] : 0.0f;
+  uint32_t status = 0;
+  const uint32_t log2s = gg.log2s, log2as = gg.log2as;
+  const uint32_t smask = (1u << log2s) - 1u;
+  const bool contiguous = (log2s == 0) && (M % 4 == 0);   // digit 0: members are adjacent
+  uint32_t* const col = s_tab + tg;                        // my group's column of the tables
+
+  Partial acc{-INFINITY, 0.0f, 0.0f};
+  float accx[D];
+#pragma unroll
+  for (int t = 0; t < D; ++t) accx[t] = 0.0f;
+
+  for (uint32_t batch = blockIdx.x; batch < gg.nbatch; batch += gridDim.x) {
+    const uint32_t g = batch * GPB + tg;              // group index h*s + l
+    const uint32_t h = g >> log2s;
+    const uint32_t l = g & smask;
+    const uint32_t ig = (h << log2as) + l;            // global index of member 0
+    const uint32_t i0 = ig + ((j * M) << log2s);      // my first member
+    const float* lvp = lV_in + ((((h * A + j * M) * gg.lv_mul) + (l & gg.lv_lmask)) & gg.lv_mask);
+
+    // ---- load my members, weight them (lw = log V + log g_n - mu) ----
+    float xv[M][D];
+    float lw[M];
+    if (contiguous) {
+#pragma unroll
+      for (int q = 0; q < M / 4; ++q) {
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(X + (size_t)t * N + i0) + q);
+          xv[4 * q][t] = v.x; xv[4 * q + 1][t] = v.y; xv[4 * q + 2][t] = v.z; xv[4 * q + 3][t] = v.w;
+        }
+        const float4 v = __ldg(reinterpret_cast<const float4*>(lvp) + q);
+        lw[4 * q] = v.x; lw[4 * q + 1] = v.y; lw[4 * q + 2] = v.z; lw[4 * q + 3] = v.w;
+      }
+    } else {
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm) {
+        const uint32_t i = i0 + (mm << log2s);
+#pragma unroll
+        for (int t = 0; t < D; ++t) xv[mm][t] = __ldcs(X + (size_t)t * N + i);
+        lw[mm] = __ldg(lvp + mm * gg.lv_mul);
+      }
+    }
+#pragma unroll
+    for (int mm = 0; mm < M; ++mm) lw[mm] += obs_log_term<D, KIND>(mp, y, xv[mm]) - muf;
+
+    // ---- group max, weights, integer prefix sums ----
+    float mx = lw[0];
+#pragma unroll
+    for (int mm = 1; mm < M; ++mm) mx = fmaxf(mx, lw[mm]);
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
+    float s1 = 0.0f, s2 = 0.0f, sx[D];
+    uint32_t P[M];
+    uint32_t run = 0;
+#pragma unroll
+    for (int t = 0; t < D; ++t) sx[t] = 0.0f;
+#pragma unroll
+    for (int mm = 0; mm < M; ++mm) {
+      const float dl = lw[mm] - mx;
+      float e = __expf(dl);
+      e = (dl == 0.0f) ? 1.0f : e;                      // the group maximum weighs exactly 2^24
+      s1 += e;
+      s2 = fmaf(e, e, s2);
+#pragma unroll
+      for (int t = 0; t < D; ++t) sx[t] = fmaf(e, xv[mm][t], sx[t]);
+      run += __float2uint_rz(e * 16777216.0f);
+      P[mm] = run;
+    }
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) s1 += __shfl_xor_sync(FULL, s1, off);
+    if (!(s1 >= 1.0f && s1 <= (float)A)) {
+      // Rare path: a non-finite log-weight (NaN / +inf -> weight zero) or a group
+      // whose weights are all zero.  Recompute the group with sanitised weights.
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm) lw[mm] = sanitize_logweight(lw[mm], status);
+      mx = -INFINITY;
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm) mx = fmaxf(mx, lw[mm]);
+#pragma unroll
+      for (int off = 1; off < G; off <<= 1) mx = fmaxf(mx, __shfl_xor_sync(FULL, mx, off));
+      const bool live = mx != -INFINITY;
+      s1 = 0.0f;
+      s2 = 0.0f;
+      run = 0;
+#pragma unroll
+      for (int t = 0; t < D; ++t) sx[t] = 0.0f;
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm) {
+        const float dl = lw[mm] - mx;
+        const float e = live ? ((dl == 0.0f) ? 1.0f : __expf(dl)) : 0.0f;
+        s1 += e;
+        s2 = fmaf(e, e, s2);
+#pragma unroll
+        for (int t = 0; t < D; ++t) sx[t] = fmaf(e, xv[mm][t], sx[t]);
+        run += __float2uint_rz(e * 16777216.0f);
+        P[mm] = run;
+      }
+#pragma unroll
+      for (int off = 1; off < G; off <<= 1) s1 += __shfl_xor_sync(FULL, s1, off);
+      if (!live && j == 0) status |= kStatusZeroGroup;
+    }
+    uint32_t incl = run;
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) {
+      const uint32_t v = __shfl_up_sync(FULL, incl, off, G);
+      if ((int)j >= off) incl += v;
+    }
+    const uint32_t Q = (G > 1) ? __shfl_sync(FULL, incl, G - 1, G) : incl;
+    const uint32_t excl = incl - run;
+#pragma unroll
+    for (int off = 1; off < G; off <<= 1) {
+      s2 += __shfl_xor_sync(FULL, s2, off);
+#pragma unroll
+      for (int t = 0; t < D; ++t) sx[t] += __shfl_xor_sync(FULL, sx[t], off);
+    }
+#pragma unroll
+    for (int mm = 0; mm < M; ++mm) {
+      const uint32_t r = j * M + mm;
+      col[r * LD] = P[mm] + excl;
+#pragma unroll
+      for (int t = 0; t < D; ++t) col[(A + t * A + r) * LD] = __float_as_uint(xv[mm][t]);
+    }
+    if (j == 0) {
+      lV_out[g] = (Q != 0) ? (mx + logf(s1) - gg.log_a) : -INFINITY;
+      merge_partial<D>(acc, accx, mx, s1, s2, sx);
+    }
+    __syncwarp();
+
+    // ---- per 4 members: random words (group-major counters), draws, gather, mutate, store ----
+    const uint32_t pi0 = g * A + j * M;
+    float xo[M][D];
+    uint32_t coff[M];          // word offset of the ancestor's row in the tables
+#pragma unroll
+    for (int q4 = 0; q4 < (M + 3) / 4; ++q4) {
+      constexpr int MQ = (M < 4) ? M : 4;             // members handled in this round
+      uint32_t rw[MQ];
+      {
+        const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) + q4, n, kPurposeResample, 0), p.rk);
+        if constexpr (M >= 4) {
+          rw[0] = w.x; rw[1] = w.y; rw[2] = w.z; rw[3] = w.w;
+        } else {
+#pragma unroll
+          for (int mm = 0; mm < MQ; ++mm) {
+            const uint32_t o = ((pi0 & 3u) + mm) & 3u;
+            rw[mm] = o == 0 ? w.x : o == 1 ? w.y : o == 2 ? w.z : w.w;
+          }
+        }
+      }
+      float z[MQ * D];
+      if constexpr ((MQ * D) % 4 == 0) {              // then the first normal number is a multiple of 4
+        const uint32_t c0 = ((pi0 + 4 * q4) * D) >> 2;
+#pragma unroll
+        for (int b = 0; b < MQ * D / 4; ++b) {
+          const uint4 w = philox4x32_10(make_uint4(c0 + b, n, kPurposePropagate, 0), p.rk);
+          normals4_fast(w, z + 4 * b);
+        }
+      } else if constexpr (4 % (MQ * D) == 0) {       // 1 or 2 normals inside one block
+        const uint32_t nu0 = pi0 * D;
+        const uint4 w = philox4x32_10(make_uint4(nu0 >> 2, n, kPurposePropagate, 0), p.rk);
+        float zz[4];
+        normals4_fast(w, zz);
+        const uint32_t off = nu0 & 3u;
+#pragma unroll
+        for (int q = 0; q < MQ * D; ++q) {
+          const uint32_t o = off + q;
+          z[q] = o == 0 ? zz[0] : o == 1 ? zz[1] : o == 2 ? zz[2] : zz[3];
+        }
+      } else {
+        constexpr int NB = (MQ * D + 6) / 4;
+        const uint32_t nu0 = (pi0 + 4 * q4) * D;
+        float zz[4 * NB];
+#pragma unroll
+        for (int b = 0; b < NB; ++b) {
+          const uint4 w = philox4x32_10(make_uint4((nu0 >> 2) + b, n, kPurposePropagate, 0), p.rk);
+          normals4_fast(w, zz + 4 * b);
+        }
+        const uint32_t off = nu0 & 3u;
+#pragma unroll
+        for (int q = 0; q < MQ * D; ++q) z[q] = zz[off + q];
+      }
+#pragma unroll
+      for (int mq = 0; mq < MQ; ++mq) {
+        const int mm = 4 * q4 + mq;
+        const uint32_t u = __umulhi(rw[mq], Q);       // floor(r Q / 2^32)
+        const uint32_t* cp = col;                      // binary lifting over the prefix sums
+#pragma unroll
+        for (int stp = A / 2; stp >= 1; stp >>= 1)
+          if (cp[(stp - 1) * LD] <= u) cp += stp * LD;
+        if (Q == 0) cp = col + (j * M + mm) * LD;     // an all-zero group keeps its particles
+        float xh[D];
+#pragma unroll
+        for (int t = 0; t < D; ++t) xh[t] = __uint_as_float(cp[(A + t * A) * LD]);
+        mutate<D, KIND>(mp, xh, z + mq * D, xo[mm]);
+        coff[mm] = (uint32_t)(cp - col);
+      }
+    }
+    if (contiguous) {
+#pragma unroll
+      for (int q = 0; q < M / 4; ++q)
+#pragma unroll
+        for (int t = 0; t < D; ++t)
+          __stcs(reinterpret_cast<float4*>(X + (size_t)t * N + i0) + q,
+                 make_float4(xo[4 * q][t], xo[4 * q + 1][t], xo[4 * q + 2][t], xo[4 * q + 3][t]));
+    } else {
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm)
+#pragma unroll
+        for (int t = 0; t < D; ++t) __stcs(X + (size_t)t * N + i0 + (mm << log2s), xo[mm][t]);
+    }
+    if (p.anc) {
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm) p.anc[i0 + (mm << log2s)] = (int32_t)(ig + ((coff[mm] / LD) << log2s));
+    }
+    __syncwarp();
+  }
+  finish_step<D>(p, acc, accx, n, status, muf);
+}
+
+// Lanes per group: each lane keeps M = A / G members, M * D <= 16 state values.
+constexpr int group_members_per_lane(int A, int D) {
+  int m = 1;
+  while (m * 2 <= A && m * 2 * D <= 16) m *= 2;
+  return m;
+}
+
+template <int D, int KIND, int A>
+inline const void* group_kernel_pick(int& G) {
+  constexpr int M = group_members_per_lane(A, D);
+  constexpr int GG = A / M;
+  G = GG;
+  return reinterpret_cast<const void*>(&step_group_kernel<D, KIND, A, GG>);
+}
+
+template <int D, int KIND>
+inline const void* group_kernel_for(int a, int& G) {
+  switch (a) {
+    case 2: return group_kernel_pick<D, KIND, 2>(G);
+    case 4: return group_kernel_pick<D, KIND, 4>(G);
+    case 8: return group_kernel_pick<D, KIND, 8>(G);
+    case 16: return group_kernel_pick<D, KIND, 16>(G);
+    case 32: return group_kernel_pick<D, KIND, 32>(G);
+    default: return nullptr;
+  }
+}
+
+}  // namespace bfpf

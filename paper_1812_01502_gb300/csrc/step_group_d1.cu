@@ -1,0 +1,13 @@
+// step_group_d1.cu - register-resident group kernels for state dimension 1.
+#include "bfpf_kernels.h"
+#include "step_group.cuh"
+
+namespace bfpf {
+
+const void* group_kernel_d1(int kind, int a, int* G) {
+  if (kind == kStochVol) return group_kernel_for<1, kStochVol>(a, *G);
+  if (kind != kLinearGaussian) return nullptr;
+  return group_kernel_for<1, kLinearGaussian>(a, *G);
+}
+
+}  // namespace bfpf

@@ -1,0 +1,13 @@
+// step_group_d2.cu - register-resident group kernels for state dimension 2.
+#include "bfpf_kernels.h"
+#include "step_group.cuh"
+
+namespace bfpf {
+
+const void* group_kernel_d2(int kind, int a, int* G) {
+
+  if (kind != kLinearGaussian) return nullptr;
+  return group_kernel_for<2, kLinearGaussian>(a, *G);
+}
+
+}  // namespace bfpf

@@ -1,0 +1,13 @@
+// step_group_d3.cu - register-resident group kernels for state dimension 3.
+#include "bfpf_kernels.h"
+#include "step_group.cuh"
+
+namespace bfpf {
+
+const void* group_kernel_d3(int kind, int a, int* G) {
+
+  if (kind != kLinearGaussian) return nullptr;
+  return group_kernel_for<3, kLinearGaussian>(a, *G);
+}
+
+}  // namespace bfpf

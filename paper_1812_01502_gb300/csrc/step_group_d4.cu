@@ -1,0 +1,13 @@
+// step_group_d4.cu - register-resident group kernels for state dimension 4.
+#include "bfpf_kernels.h"
+#include "step_group.cuh"
+
+namespace bfpf {
+
+const void* group_kernel_d4(int kind, int a, int* G) {
+
+  if (kind != kLinearGaussian) return nullptr;
+  return group_kernel_for<4, kLinearGaussian>(a, *G);
+}
+
+}  // namespace bfpf

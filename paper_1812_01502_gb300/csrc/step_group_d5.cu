@@ -1,0 +1,13 @@
+// step_group_d5.cu - register-resident group kernels for state dimension 5.
+#include "bfpf_kernels.h"
+#include "step_group.cuh"
+
+namespace bfpf {
+
+const void* group_kernel_d5(int kind, int a, int* G) {
+
+  if (kind != kLinearGaussian) return nullptr;
+  return group_kernel_for<5, kLinearGaussian>(a, *G);
+}
+
+}  // namespace bfpf

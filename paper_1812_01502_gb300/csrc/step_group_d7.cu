@@ -1,0 +1,13 @@
+// step_group_d7.cu - register-resident group kernels for state dimension 7.
+#include "bfpf_kernels.h"
+#include "step_group.cuh"
+
+namespace bfpf {
+
+const void* group_kernel_d7(int kind, int a, int* G) {
+
+  if (kind != kLinearGaussian) return nullptr;
+  return group_kernel_for<7, kLinearGaussian>(a, *G);
+}
+
+}  // namespace bfpf

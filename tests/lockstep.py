@@ -99,7 +99,7 @@ def check_step_full(filt, model, radices, seed, y_n, n):
     grp = (anc // (a * s)) * s + anc % s
     assert np.all(np.bincount(grp, minlength=N // a) == a)
     # states: oracle mutation of the GPU's own ancestors
-    x_chk = bpf.mutate(model, x0.astype(np.float64)[anc], n, seed)
+    x_chk = bpf.mutate(model, x0.astype(np.float64)[anc], n, seed, idx=butterfly.group_major(N, radices, k))
     e_x = rel_err(x1, x_chk)
     lv_chk = o["lV_new"].reshape(H, a, s)[:, 0, :].reshape(-1)
     e_lv = rel_err(lv1, lv_chk)
@@ -151,8 +151,9 @@ def check_step_sampled(filt, model, radices, seed, y_n, n, n_groups, rng):
     assert np.all(anc[idx] // (a * s) == idx // (a * s)) and np.all(anc[idx] % s == idx % s)
     assert not np.any((member_gpu != member_o) & dec), f"step {n}: decidable ancestors differ"
     assert np.all((member_gpu >= lo) & (member_gpu <= hi))
+    pi = ((groups[:, :1] * s + groups[:, 1:2]) * a + np.arange(a)[None, :]).reshape(-1)
     x_chk = bpf.mutate(model, x0[anc[idx].reshape(-1)].astype(np.float64), n, seed,
-                       idx=idx.reshape(-1)).reshape(idx.shape + (x0.shape[1],))
+                       idx=pi).reshape(idx.shape + (x0.shape[1],))
     e_x = rel_err(x1[idx], x_chk)
     e_lv = rel_err(lv1[groups[:, 0] * s + groups[:, 1]], o["lV_new"])
     assert e_x <= TOL_STATE, f"step {n}: state error {e_x}"

@@ -63,6 +63,37 @@ def test_lockstep_small(bfpf, case):
     assert rep["undecidable"] <= max(8, 4 * 2 * LS.ETA * a_max * rep["draws"])
 
 
+@pytest.mark.parametrize("d,radices", [
+    (1, (2,) * 12), (1, (4, 8, 2, 16, 8)), (1, (32, 32, 4)), (2, (8, 8, 8, 8)), (3, (16, 2, 32)),
+    (4, (32, 32)), (5, (4, 16, 8)), (7, (16, 16, 2)), (8, (32, 32)), (8, (2, 4, 8, 16))])
+def test_lockstep_group_kernels(bfpf, d, radices):
+    """Sizes at which the register-resident group kernel runs every digit."""
+    model = S.lg_scalar() if d == 1 else S.lg_dense(d, seed=d)
+    y = S.simulate(model, len(radices) + 2, seed=19)[1]
+    f = _filter(bfpf, model, radices, 99)
+    plan = f.describe()
+    assert all(dg["kernel"] == "group" for dg in plan["digits"]), plan
+    rep = LS.Report()
+    for n in range(len(y)):
+        rep.merge(LS.check_step_full(f, model, radices, 99, y[n], n))
+    f.close()
+    print("group", d, radices, dict(rep))
+    assert rep["undecidable"] <= max(8, 4 * 2 * LS.ETA * max(radices) * rep["draws"])
+
+
+def test_lockstep_sv_group_kernel(bfpf):
+    model = S.sv_model()
+    radices = (16, 16, 16, 4)
+    y = S.simulate(model, 6, seed=23)[1]
+    f = _filter(bfpf, model, radices, 7)
+    assert all(dg["kernel"] == "group" for dg in f.describe()["digits"])
+    rep = LS.Report()
+    for n in range(len(y)):
+        rep.merge(LS.check_step_full(f, model, radices, 7, y[n], n))
+    f.close()
+    print("sv group", dict(rep))
+
+
 def test_config1_lockstep_all_steps(bfpf):
     """1-D LG, N = 2^10 radix 2, T = 100: every step checked from the GPU's state."""
     w = S.workload("lg1d_n1024")

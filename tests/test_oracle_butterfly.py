@@ -94,3 +94,16 @@ def test_paper_stage_is_product_of_two_digit_stages(S, M):
         # the paper's Kronecker order puts the within-PE factor innermost (least significant)
         got = bf.mixed_radix_A(radices, s) @ bf.mixed_radix_A(radices, 0)
         np.testing.assert_allclose(got, want, atol=1e-15)
+
+
+@pytest.mark.parametrize("radices", [(2, 2), (3, 4, 2), (4, 8, 2), (5,)])
+def test_group_major_numbering_is_a_permutation(radices):
+    """Draw numbering at each digit: a permutation in which each group's members are
+    consecutive, in digit order."""
+    N = int(np.prod(radices))
+    for k in range(len(radices)):
+        pi = bf.group_major(N, radices, k)
+        assert np.array_equal(np.sort(pi), np.arange(N))
+        for i in range(N):
+            mem = bf.group_members(i, radices, k)
+            assert [int(pi[j]) for j in mem] == list(range(int(pi[mem[0]]), int(pi[mem[0]]) + radices[k]))
