@@ -209,6 +209,43 @@ const char* pf_last_error(const pf_handle* h);
 pf_status pf_philox_blocks(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
                            int64_t count, uint32_t* out, void* stream);
 
+/*
+ * pf_step_noalloc - one time step on buffers the caller already owns, with no
+ * device allocation of any kind.  (The paper has no counterpart: this entry
+ * point exists for callers whose device memory is managed by someone else -
+ * an engine or framework that owns every allocation, or a real-time loop with
+ * a fixed memory budget - and who therefore may not call cudaMalloc, nor keep
+ * a pf_create workspace alive.)
+ *
+ * The step's temporary data (the device state block, per-block partial sums
+ * and the per-step outputs) lives in a fixed scratch area compiled into the
+ * library: 192 KiB of device memory per GPU that loads the library, held until
+ * the process exits.  The step runs at most 2048 thread blocks; pf_step_noalloc
+ * caps its grid there, so N and d stay limited only as for pf_create.
+ *
+ * Arguments: model, N, radices, m, seed as for pf_create; n = index of this
+ * time step (digit n mod m interacts; it keys the random draws); mu = carried
+ * normaliser: 0 at n = 0, then out[1] of the previous step.  Device buffers:
+ * x (N*d floats, state-major, x[t*N + i]) holds the prediction particles
+ * zeta_n and is overwritten with zeta_{n+1}; lV_in (N / a_{(n-1) mod m}
+ * floats, all zero at n = 0) the carried log stage weights; lV_out
+ * (N / a_{n mod m} floats) receives the new ones.  y_n: dy floats, host.
+ * Host outputs: out[3] = { log-likelihood increment, mu for step n + 1, ESS };
+ * mean_out (d floats, may be NULL) = the filtering mean.  Synchronises `stream`.
+ *
+ * The first call on a device resolves the scratch area's device address
+ * (cudaGetSymbolAddress) with that device current, so make that first call
+ * outside any CUDA stream capture.  Every call on a device shares the one
+ * scratch area and the call clears what must start at zero; calls that can
+ * overlap on the GPU (different streams, or threads without ordering) race on
+ * it and must be serialised by the caller.
+ * Errors: PF_EINVAL as pf_create; PF_ECUDA.
+ */
+pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int32_t* radices, int32_t m,
+                          uint64_t seed, uint32_t n, double mu, float* x, const float* lV_in,
+                          float* lV_out, const float* y_n, double* out, float* mean_out,
+                          void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -663,3 +664,138 @@ pf_status pf_philox_blocks(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// pf_step_noalloc: one step with the temporaries in a fixed, library-owned
+// scratch area instead of an allocated workspace.
+// ---------------------------------------------------------------------------
+namespace {
+
+constexpr int kNoAllocMaxBlocks = 2048;
+constexpr size_t kNoAllocStateOff = 0;
+constexpr size_t kNoAllocPartialsOff = 256;
+constexpr size_t kNoAllocPartialsBytes = (size_t)4 * (3 + kMaxDim) * kNoAllocMaxBlocks;   // 90,112
+constexpr size_t kNoAllocYOff = kNoAllocPartialsOff + kNoAllocPartialsBytes;
+constexpr size_t kNoAllocIncOff = kNoAllocYOff + (size_t)4 * kRing * kMaxDim;
+constexpr size_t kNoAllocMeanOff = kNoAllocIncOff + (size_t)8 * kRing;
+constexpr size_t kNoAllocEssOff = kNoAllocMeanOff + (size_t)4 * kRing * kMaxDim;
+constexpr size_t kNoAllocBytes = 192 * 1024;
+static_assert(kNoAllocEssOff + 4 * kRing <= kNoAllocBytes, "scratch layout exceeds its size");
+constexpr int kNoAllocMaxDevices = 64;
+
+// The scratch area.  In host code this name is only a stand-in for the
+// symbol; its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+std::mutex g_noalloc_mutex;
+unsigned char* g_noalloc_addr[kNoAllocMaxDevices] = {};
+
+// Device address of the scratch area on the current device, resolved once per device.
+cudaError_t noalloc_scratch(unsigned char** out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+  if (!g_noalloc_addr[dev]) {
+    void* ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+    if (e != cudaSuccess) return e;
+    g_noalloc_addr[dev] = static_cast<unsigned char*>(ptr);
+  }
+  *out = g_noalloc_addr[dev];
+  return cudaSuccess;
+}
+
+struct NoAllocStart {
+  double mu;
+  uint32_t n;
+  uint32_t dy;
+  float y[kMaxDim];
+};
+
+// Clears the device state block (block counter, status, likelihood) and puts
+// this step's observation and normaliser in place.
+__global__ void noalloc_start_kernel(DevState* st, float* y_ring, NoAllocStart s) {
+  if (threadIdx.x == 0) {
+    st->n = s.n;
+    st->done = 0;
+    st->status = 0;
+    st->mu = s.mu;
+    st->mu_f = (float)s.mu;
+    st->loglik = 0.0;
+    for (uint32_t j = 0; j < s.dy; ++j) y_ring[(s.n % kRing) * s.dy + j] = s.y[j];
+  }
+}
+
+}  // namespace
+
+extern "C" pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int32_t* radices, int32_t m,
+                                     uint64_t seed, uint32_t n, double mu, float* x, const float* lV_in,
+                                     float* lV_out, const float* y_n, double* out, float* mean_out,
+                                     void* stream) {
+  if (!x || !lV_in || !lV_out || !y_n || !out) return fail(nullptr, PF_EINVAL, "NULL argument");
+  Plan pl;
+  std::string msg;
+  pf_status s = make_plan(model, N, radices, m, nullptr, pl, msg);
+  if (s == PF_OK) s = finish_plan(pl, nullptr, msg);
+  if (s != PF_OK) return fail(nullptr, s, msg);
+  if (pl.max_grid > kNoAllocMaxBlocks)
+    return fail(nullptr, PF_EINVAL, "this device would run more than 2048 thread blocks, the scratch area's limit");
+  unsigned char* scratch = nullptr;
+  cudaError_t e = noalloc_scratch(&scratch);
+  if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+
+  StepParams P{};
+  P.rk = make_round_keys(seed);
+  P.x = x;
+  P.lV[n & 1u] = const_cast<float*>(lV_in);
+  P.lV[(n & 1u) ^ 1u] = lV_out;
+  P.anc = nullptr;
+  P.st = reinterpret_cast<DevState*>(scratch + kNoAllocStateOff);
+  P.partials = reinterpret_cast<float*>(scratch + kNoAllocPartialsOff);
+  P.y_ring = reinterpret_cast<const float*>(scratch + kNoAllocYOff);
+  P.inc_ring = reinterpret_cast<double*>(scratch + kNoAllocIncOff);
+  P.mean_ring = reinterpret_cast<float*>(scratch + kNoAllocMeanOff);
+  P.ess_ring = reinterpret_cast<float*>(scratch + kNoAllocEssOff);
+  P.N = pl.N;
+  P.m = pl.m;
+  P.seed_lo = (uint32_t)seed;
+  P.seed_hi = (uint32_t)(seed >> 32);
+  P.tile_cap = pl.cap;
+  P.inv_N = (float)(1.0 / pl.N);
+  P.model = pl.mp;
+  std::memcpy(P.geom, pl.geom, sizeof(P.geom));
+
+  NoAllocStart start{};
+  start.mu = mu;
+  start.n = n;
+  start.dy = (uint32_t)pl.dy;
+  for (int j = 0; j < pl.dy; ++j) start.y[j] = y_n[j];
+  noalloc_start_kernel<<<1, 32, 0, st>>>(P.st, const_cast<float*>(P.y_ring), start);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("start kernel: ") + cudaGetErrorString(e));
+  DigitPlan& dp = pl.dp[n % (uint32_t)pl.m];
+  if (dp.group) {
+    void* args[] = {&P, &dp.gg};
+    e = cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, 0, st);
+  } else {
+    void* args[] = {&P};
+    e = cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, dp.smem, st);
+  }
+  if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("step kernel: ") + cudaGetErrorString(e));
+  const uint32_t slot = n % kRing;
+  DevState dst;
+  float ess = 0.0f;
+  e = cudaMemcpyAsync(&dst, P.st, sizeof(dst), cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&out[0], P.inc_ring + slot, 8, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(&ess, P.ess_ring + slot, 4, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess && mean_out)
+    e = cudaMemcpyAsync(mean_out, P.mean_ring + (size_t)slot * pl.d, (size_t)4 * pl.d, cudaMemcpyDeviceToHost, st);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("copy back: ") + cudaGetErrorString(e));
+  out[1] = dst.mu;
+  out[2] = (double)ess;
+  return PF_OK;
+}
