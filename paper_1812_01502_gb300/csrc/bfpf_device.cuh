@@ -38,6 +38,7 @@ constexpr uint32_t kPurposeResampleWide = 3;
 
 constexpr uint32_t kStatusNonFinite = 1u;
 constexpr uint32_t kStatusZeroGroup = 2u;
+constexpr uint32_t kStatusTimeout = 4u;    // a bounded wait gave up (global scan)
 
 enum ModelKind : int { kLinearGaussian = 1, kStochVol = 2 };
 
@@ -220,6 +221,9 @@ struct DevState {
   float mu_f;          // FP32 copy of mu, subtracted by the kernels
   double mu;           // carried normaliser (log-mean carried weight)
   double loglik;       // cumulative log-likelihood (FP64)
+  float gmax;          // global resampling: maximum log-weight of the step
+  uint32_t done2;      // global resampling: blocks finished with the draw kernel
+  unsigned long long ticket;   // global resampling: scan tiles handed out so far
 };
 
 struct StepParams {
@@ -241,5 +245,22 @@ struct StepParams {
   ModelParams model;
   DigitGeom geom[kMaxDigits];
 };
+
+// Buffers of the global-resampling path (m = 1, N > kMaxCtaRadix).
+struct GlobalParams {
+  float* xbuf[2];                 // states, ping-pong by time-step parity (gather is random)
+  float* lw;                      // [N] log-weights of the step
+  unsigned long long* P;          // [N] inclusive prefix sums of the integer weights
+  unsigned long long* top;        // [ntop] P at the end of every 2^top_shift-th segment
+  unsigned long long* agg;        // [nscan] scan tile aggregates
+  unsigned long long* incl;       // [nscan] scan tile inclusive prefixes
+  uint32_t* flag;                 // [nscan] 2n+1: aggregate ready, 2n+2: prefix ready (step n)
+  uint32_t nscan;                 // scan tiles of kScanTile particles
+  uint32_t ntop, top_shift;
+};
+
+constexpr int kScanItems = 16;
+constexpr uint32_t kScanTile = kBlock * kScanItems;   // 4096 particles
+constexpr uint32_t kTopMax = 4096;
 
 }  // namespace bfpf

@@ -54,9 +54,12 @@ __device__ __forceinline__ void shfl_merge(Partial& acc, float* accx, int off) {
 }
 
 // Called by every thread of every block exactly once, after its last tile.
-template <int D>
+// ADVANCE = false (global resampling, which finishes the step in a later
+// kernel): the last block leaves n alone and instead writes the global
+// maximum log-weight and the single group's new log weight.
+template <int D, bool ADVANCE = true>
 __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, float* accx, uint32_t n,
-                                            uint32_t status, float muf) {
+                                            uint32_t status, float muf, float* lv_single_out = nullptr) {
   constexpr int NP = 3 + D;
   constexpr int NW = kBlock / 32;
   __shared__ float s_red[NW][NP];
@@ -171,8 +174,13 @@ __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, fl
     st->mu = lme;
     st->mu_f = (float)lme;
     st->done = 0;
-    __threadfence();
-    st->n = n + 1;
+    if constexpr (ADVANCE) {
+      __threadfence();
+      st->n = n + 1;
+    } else {
+      st->gmax = Mx;
+      if (lv_single_out) *lv_single_out = (float)lme;   // log of the one group's mean weight
+    }
   }
 }
 

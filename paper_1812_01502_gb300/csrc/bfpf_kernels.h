@@ -27,6 +27,15 @@ const void* group_kernel_d6(int kind, int a, int* G);
 const void* group_kernel_d7(int kind, int a, int* G);
 const void* group_kernel_d8(int kind, int a, int* G);
 
+// Global-resampling comparator (radices = {N}, N > 1024): three kernels per step,
+// each taking (StepParams, GlobalParams).
+struct GlobalKernels {
+  const void* weight;
+  const void* scan;
+  const void* draw;
+};
+bool select_global_kernels(int d, int kind, GlobalKernels& gk);
+
 cudaError_t launch_philox_blocks(uint64_t seed, uint4 c, uint32_t count, uint32_t* out,
                                  cudaStream_t stream);
 

@@ -30,6 +30,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t st, x, lv0, lv1, anc, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
+  size_t x2, lw, P, top, agg, incl, flag;   // global resampling only
 };
 
 // The kernel that runs the steps on one digit.
@@ -58,6 +59,10 @@ struct Plan {
   DigitGeom geom[kMaxDigits]{};
   DigitPlan dp[kMaxDigits]{};
   int max_grid = 0;
+  bool global = false;        // radices = {N} with N > kMaxCtaRadix: global resampling kernels
+  GlobalKernels gk{};
+  int grid_weight = 0, grid_draw = 0;
+  uint32_t nscan = 0, ntop = 0, top_shift = 0;
   Layout lay{};
 };
 
@@ -72,6 +77,7 @@ struct pf_handle {
   size_t ws_bytes = 0;
   Plan plan;
   StepParams P{};
+  GlobalParams GP{};
   uint64_t n_host = 0;     // time steps enqueued
   uint64_t n_pushed = 0;   // observations copied into the ring
   std::vector<cudaGraphExec_t> graphs;   // chunk graphs, one per radix phase (n mod m)
@@ -208,13 +214,30 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     if (a > (int64_t)kNarrowMaxRadix) pl.wide = true;
   }
   if (prod != N64) { msg = "the product of the radices must equal N"; return PF_EINVAL; }
-  if (m == 1 && N64 > (int64_t)kMaxCtaRadix) {
-    msg = "global resampling (m = 1) with N > 1024 is not available in this build";
-    return PF_EINVAL;
-  }
   pl.N = (uint32_t)N64;
   pl.m = m;
   const int d = pl.d;
+  if (m == 1 && N64 > (int64_t)kMaxCtaRadix) {
+    // Global multinomial resampling (Algorithm 2) across thread blocks.
+    pl.global = true;
+    pl.wide = true;
+    if (!select_global_kernels(d, pl.kind, pl.gk)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
+    if (!select_kernels(d, pl.kind, true, pl.ks)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
+    pl.nscan = (pl.N + kScanTile - 1) / kScanTile;
+    uint32_t lg = 0;
+    while ((1ull << lg) < pl.N) ++lg;
+    pl.top_shift = lg > 12 ? lg - 12 : 0;
+    pl.ntop = (pl.N + (1u << pl.top_shift) - 1) >> pl.top_shift;
+    DigitGeom& g = pl.geom[0];
+    g.a = pl.N;
+    g.s = 1;
+    g.H = 1;
+    g.log_a = (float)std::log((double)pl.N);
+    g.wide = 1;
+    pl.record = opts && (opts->flags & PF_RECORD_ANCESTORS);
+    pl.chunk_len = (opts && opts->chunk_len > 0) ? std::min<int>(opts->chunk_len, (int)kRing) : 64;
+    return PF_OK;
+  }
   uint32_t target = (opts && opts->tile > 0) ? (uint32_t)opts->tile : (d == 1 ? 4096u : d <= 4 ? 2048u : 1024u);
   target = std::max<uint32_t>(target, 4);
   uint32_t s = 1;
@@ -300,10 +323,47 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
 }
 
 // Needs a CUDA device: occupancy decides the persistent grid size.
+pf_status finish_plan_global(Plan& pl, const pf_options* opts, int sms, std::string& msg) {
+  int nw = 0, nd = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nw, pl.gk.weight, kBlock, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd, pl.gk.draw, kBlock, 0);
+  if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
+  const int units = (int)((pl.N + kBlock - 1) / kBlock);
+  int gw = (opts && opts->grid > 0) ? opts->grid : std::max(1, nw) * sms;
+  int gd = (opts && opts->grid > 0) ? opts->grid : std::max(1, nd) * sms;
+  pl.grid_weight = std::max(1, std::min(gw, units));
+  pl.grid_draw = std::max(1, std::min(gd, units));
+  pl.max_grid = pl.grid_weight;
+  pl.grid = pl.grid_weight;
+  Layout& L = pl.lay;
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  L.st = take(sizeof(DevState));
+  L.x = take((size_t)4 * pl.d * pl.N);
+  L.x2 = take((size_t)4 * pl.d * pl.N);
+  L.lv0 = take(4);
+  L.lv1 = take(4);
+  L.anc = pl.record ? take((size_t)4 * pl.N) : 0;
+  L.partials = take((size_t)4 * (3 + pl.d) * pl.grid_weight);
+  L.y_ring = take((size_t)4 * kRing * pl.dy);
+  L.inc_ring = take((size_t)8 * kRing);
+  L.mean_ring = take((size_t)4 * kRing * pl.d);
+  L.ess_ring = take((size_t)4 * kRing);
+  L.lw = take((size_t)4 * pl.N);
+  L.P = take((size_t)8 * pl.N);
+  L.top = take((size_t)8 * kTopMax);
+  L.agg = take((size_t)8 * pl.nscan);
+  L.incl = take((size_t)8 * pl.nscan);
+  L.flag = take((size_t)4 * pl.nscan);
+  L.total = off;
+  return PF_OK;
+}
+
 pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   int dev = 0, sms = 0, nb = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess && pl.global) return finish_plan_global(pl, opts, sms, msg);
   if (e == cudaSuccess)   // opt in beyond the 48 KB default whatever the size
     e = cudaFuncSetAttribute(pl.ks.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pl.ks.step, kBlock, pl.smem);
@@ -346,8 +406,15 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   return PF_OK;
 }
 
-// Launch the step kernel for time step n (digit n mod m).
+// Launch the step kernel(s) for time step n (digit n mod m).
 cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t n) {
+  if (h->plan.global) {
+    void* args[] = {&h->P, &h->GP};
+    cudaError_t e = cudaLaunchKernel(h->plan.gk.weight, dim3(h->plan.grid_weight), dim3(kBlock), args, 0, stream);
+    if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.scan, dim3(h->plan.nscan), dim3(kBlock), args, 0, stream);
+    if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.draw, dim3(h->plan.grid_draw), dim3(kBlock), args, 0, stream);
+    return e;
+  }
   DigitPlan& dp = h->plan.dp[n % (uint64_t)h->plan.m];
   if (dp.group) {
     void* args[] = {&h->P, &dp.gg};
@@ -436,6 +503,20 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   P.inv_N = (float)(1.0 / pl.N);
   P.model = pl.mp;
   std::memcpy(P.geom, pl.geom, sizeof(P.geom));
+  if (pl.global) {
+    GlobalParams& G = h->GP;
+    G.xbuf[0] = P.x;
+    G.xbuf[1] = reinterpret_cast<float*>(h->ws + L.x2);
+    G.lw = reinterpret_cast<float*>(h->ws + L.lw);
+    G.P = reinterpret_cast<unsigned long long*>(h->ws + L.P);
+    G.top = reinterpret_cast<unsigned long long*>(h->ws + L.top);
+    G.agg = reinterpret_cast<unsigned long long*>(h->ws + L.agg);
+    G.incl = reinterpret_cast<unsigned long long*>(h->ws + L.incl);
+    G.flag = reinterpret_cast<uint32_t*>(h->ws + L.flag);
+    G.nscan = pl.nscan;
+    G.ntop = pl.ntop;
+    G.top_shift = pl.top_shift;
+  }
 
   // Algorithm 1, first loop: zeta_0 ~ pi_0; carried weights start at zero.
   auto bail = [&](cudaError_t err, const char* what) {
@@ -447,8 +528,12 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   };
   e = cudaMemsetAsync(h->ws + L.st, 0, sizeof(DevState), h->stream);
   if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
-  e = cudaMemsetAsync(h->ws + L.lv0, 0, (size_t)4 * (pl.N / pl.min_a), h->stream);
+  e = cudaMemsetAsync(h->ws + L.lv0, 0, pl.global ? 4 : (size_t)4 * (pl.N / pl.min_a), h->stream);
   if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
+  if (pl.global) {
+    e = cudaMemsetAsync(h->ws + L.flag, 0, (size_t)4 * pl.nscan, h->stream);
+    if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
+  }
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, h->device);
   const uint32_t blocks = std::min<uint32_t>((pl.N + kBlock - 1) / kBlock, (uint32_t)std::max(1, sms) * 8);
@@ -580,12 +665,14 @@ pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars)
   const Plan& pl = h->plan;
   DevState st;
   PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
-  if (x) PF_CUDA(h, cudaMemcpyAsync(x, h->P.x, (size_t)4 * pl.d * pl.N, cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  const float* xcur = pl.global ? h->GP.xbuf[st.n & 1u] : h->P.x;
+  if (x) PF_CUDA(h, cudaMemcpyAsync(x, xcur, (size_t)4 * pl.d * pl.N, cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   if (lV) {
     const uint32_t n = st.n;
     const int kp = (int)((n + pl.m - 1) % pl.m);
-    const size_t cnt = pl.N / pl.geom[kp].a;
+    const size_t cnt = pl.global ? 1 : pl.N / pl.geom[kp].a;
     PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[n & 1u], 4 * cnt, cudaMemcpyDeviceToHost, h->stream));
     PF_CUDA(h, cudaStreamSynchronize(h->stream));
   }
@@ -620,6 +707,10 @@ pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
   const Plan& pl = h->plan;
   std::string o = "{\"N\": " + std::to_string(pl.N) + ", \"d\": " + std::to_string(pl.d) +
                   ", \"digits\": [";
+  if (pl.global)
+    o += "{\"a\": " + std::to_string(pl.N) + ", \"s\": 1, \"kernel\": \"global\", \"scan_tiles\": " +
+         std::to_string(pl.nscan) + ", \"grid\": " + std::to_string(pl.grid_draw) + "}";
+  else
   for (int k = 0; k < pl.m; ++k) {
     const DigitPlan& dp = pl.dp[k];
     const DigitGeom& g = pl.geom[k];
@@ -738,6 +829,10 @@ extern "C" pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int
   Plan pl;
   std::string msg;
   pf_status s = make_plan(model, N, radices, m, nullptr, pl, msg);
+  if (s == PF_OK && pl.global) {
+    s = PF_EINVAL;
+    msg = "global resampling (radices = {N}, N > 1024) needs a handle from pf_create";
+  }
   if (s == PF_OK) s = finish_plan(pl, nullptr, msg);
   if (s != PF_OK) return fail(nullptr, s, msg);
   if (pl.max_grid > kNoAllocMaxBlocks)

@@ -33,6 +33,17 @@ def plausible_members(q: np.ndarray, u: np.ndarray, axis: int):
     Q = np.take(P, [-1], axis=axis)
     a = q.shape[axis]
     margin = 2 * ETA * np.minimum(P, Q - P) + a + 4
+    if a > 64:   # P +- margin are non-decreasing along the group: binary searches
+        Pm = np.moveaxis(P, axis, -1).reshape(-1, a)
+        Mm = np.moveaxis(margin, axis, -1).reshape(-1, a)
+        um = np.moveaxis(u.astype(np.float64), axis, -1).reshape(-1, a)
+        lo = np.empty(um.shape, dtype=np.int64)
+        hi = np.empty(um.shape, dtype=np.int64)
+        for g in range(Pm.shape[0]):
+            lo[g] = np.searchsorted(Pm[g] + Mm[g], um[g], side="right")
+            hi[g] = np.minimum(np.searchsorted(Pm[g] - Mm[g], um[g], side="right"), a - 1)
+        shape = np.moveaxis(u, axis, -1).shape
+        return np.moveaxis(lo.reshape(shape), -1, axis), np.moveaxis(hi.reshape(shape), -1, axis)
     Pm = np.moveaxis(P, axis, -1)
     um = np.moveaxis(u.astype(np.float64), axis, -1)
     mg = np.moveaxis(margin, axis, -1)

@@ -94,6 +94,25 @@ def test_lockstep_sv_group_kernel(bfpf):
     print("sv group", dict(rep))
 
 
+@pytest.mark.parametrize("d,N,T", [(1, 4096, 5), (1, 1 << 16, 3), (4, 5000, 3), (8, 1 << 14, 2), (0, 1 << 15, 4)])
+def test_lockstep_global_resampling(bfpf, d, N, T):
+    """radices = {N} above one block: the three-kernel global path (d = 0 means SV)."""
+    model = S.sv_model() if d == 0 else (S.lg_scalar() if d == 1 else S.lg_dense(d, seed=d))
+    y = S.simulate(model, T, seed=41)[1]
+    f = _filter(bfpf, model, (N,), 606)
+    assert f.describe()["digits"][0]["kernel"] == "global"
+    rep = LS.Report()
+    for n in range(T):
+        rep.merge(LS.check_step_full(f, model, (N,), 606, y[n], n))
+    assert f.status() == 0
+    f.close()
+    print("global", d, N, dict(rep))
+    # With one group of N members the worst-case margin (ETA times a cumulative sum)
+    # spans several boundary spacings, so most draws count as undecidable; the
+    # actual FP32/FP64 differences are far smaller: nearly all draws agree exactly.
+    assert rep["mismatched_undecidable"] <= 0.001 * rep["draws"]
+
+
 def test_config1_lockstep_all_steps(bfpf):
     """1-D LG, N = 2^10 radix 2, T = 100: every step checked from the GPU's state."""
     w = S.workload("lg1d_n1024")
