@@ -48,6 +48,8 @@ def _args():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--workload", default="sv_n16m")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-global", action="store_true", help="skip the global-resampling comparator legs")
+    p.add_argument("--global-steps", type=int, default=200)
     p.add_argument("--oracle-rate", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--oracle-n", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--oracle-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
@@ -219,6 +221,102 @@ def reference_main(a):
 # ---------------------------------------------------------------------------
 # Our arm
 # ---------------------------------------------------------------------------
+def _radix16(N: int):
+    """Radix-16 digits (plus one smaller digit) whose product is N (a power of two)."""
+    out, rem = [], N
+    while rem >= 16:
+        out.append(16)
+        rem //= 16
+    if rem > 1:
+        out.append(rem)
+    return tuple(out)
+
+
+def _timed_flushed_steps(bf, filt, y_dev, K, W, flush, stream, dev):
+    """Per-step device times (ms) of K steps, L2 flushed before each, after W warm-up steps."""
+    import torch
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    with torch.cuda.stream(stream):
+        filt.push(y_dev[:W])
+        for _ in range(W):
+            flush.zero_()
+            filt.advance(1)
+        for j in range(K):
+            if j % 1000 == 0:
+                filt.push(y_dev[W + j:W + min(K, j + 1000)])
+            flush.zero_()
+            starts[j].record(stream)
+            filt.advance(1)
+            ends[j].record(stream)
+        torch.cuda.synchronize(dev)
+    return [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+
+
+def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
+    """Filter-mean MSE (Section 6.1: sum over steps and components, mean over runs)
+    against the number of particles, for the butterfly (radix 16) and the global-
+    resampling filter on the same observations, and the time per step of each.
+    Reference mean: average of two independent global runs at N = 2^25; the
+    reference's own error (half the squared spread of the two runs, halved again
+    for their average) is subtracted."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    y = S.simulate(w.model, T, w.data_seed)[1].astype(np.float32)
+
+    def run(N, radices, seed):
+        f = bf.ButterflyFilter(w.model, N, radices, seed, device=dev)
+        f.run(y[:4])                                  # graph capture / first touch
+        g = bf.ButterflyFilter(w.model, N, radices, seed, device=dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        yd = torch.tensor(y, device=dev)
+        torch.cuda.synchronize(dev)
+        e0.record(g.stream)
+        r = g.run(yd)
+        e1.record(g.stream)
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / T
+        mean = r["mean"].double().cpu().numpy()
+        f.close()
+        g.close()
+        return mean, ms
+
+    ref = [run(1 << 25, (1 << 25,), seed0 + 1 + j)[0] for j in range(2)]
+    ref_mean = 0.5 * (ref[0] + ref[1])
+    ref_mse = 0.25 * float(np.sum((ref[0] - ref[1]) ** 2))     # error of the averaged reference
+    out = {}
+    for name, Ns, rad in (("butterfly", [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24], _radix16),
+                          ("global", [1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22], lambda N: (N,))):
+        mses, times = [], []
+        for N in Ns:
+            J = 4 if N <= (1 << 20) else 2
+            errs, ts = [], []
+            for j in range(J):
+                mean, ms = run(N, rad(N), seed0 + 100 * j + N % 97)
+                errs.append(float(np.sum((mean - ref_mean) ** 2)) - ref_mse)
+                ts.append(ms)
+            mses.append(max(float(np.mean(errs)), 1e-30))
+            times.append(float(np.median(ts)))
+        out[name] = {"N": Ns, "mse": mses, "ms_per_step": times}
+    # equal error: the global filter's N at the butterfly's MSE at the largest N (log-log fits)
+    bN, bm, bt = out["butterfly"]["N"], out["butterfly"]["mse"], out["butterfly"]["ms_per_step"]
+    gN, gm, gt = out["global"]["N"], out["global"]["mse"], out["global"]["ms_per_step"]
+    fit_g = np.polyfit(np.log(gN), np.log(gm), 1)
+    fit_b = np.polyfit(np.log(bN), np.log(bm), 1)
+    target = float(np.exp(np.polyval(fit_b, np.log(bN[-1]))))
+    logN_eq = (np.log(target) - fit_g[1]) / fit_g[0]
+    t_g = float(np.exp(np.interp(logN_eq, np.log(gN), np.log(gt),
+                                 left=None, right=None))) if logN_eq <= np.log(gN[-1]) else \
+        float(np.exp(np.polyval(np.polyfit(np.log(gN[-3:]), np.log(gt[-3:]), 1), logN_eq)))
+    t_b = bt[-1]
+    return {"T": T, "reference": "mean of 2 global runs at N=2^25, their spread subtracted",
+            "butterfly": out["butterfly"], "global": out["global"],
+            "mse_slope": {"butterfly": float(fit_b[0]), "global": float(fit_g[0])},
+            "butterfly_N": bN[-1], "butterfly_mse": target, "global_N_at_equal_mse": float(np.exp(logN_eq)),
+            "butterfly_ms_per_step": t_b, "global_ms_per_step_at_equal_mse": t_g,
+            "speedup_at_equal_error": t_g / t_b}
+
 def ours_main(a):
     import numpy as np
     import torch
@@ -267,6 +365,13 @@ def ours_main(a):
             ends[j].record(stream)
         torch.cuda.synchronize(dev)
         clk = clocks.stop()
+    step_ms = [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    p50_ms = float(np.percentile(step_ms, 50))
+    p99_ms = float(np.percentile(step_ms, 99))
+    bytes_steps = [algorithmic_bytes(w, n0 + j) for j in range(K)]
+    achieved_gbs = sum(bytes_steps) / (total_ms * 1e-3) / 1e9
+
     # --- L2-resident chunk (consecutive steps, CUDA graph), for reference ----
     KR = min(K, 1000)
     y_dev2 = torch.tensor(y[W + K:W + K + KR], device=dev).contiguous()
@@ -292,6 +397,21 @@ def ours_main(a):
     e2e_s = time.perf_counter() - t0
     ll_e2e = float(np.sum(out["inc"]))
     efilt.close()
+
+    # --- the global-resampling comparator on the same workload -----------------
+    glob = None
+    if not a.no_global and w.N > 1024:
+        KG = max(1, min(a.global_steps, K))
+        gfilt = bf.ButterflyFilter(w.model, w.N, (w.N,), w.filter_seed + rank, device=dev)
+        g_ms = _timed_flushed_steps(bf, gfilt, torch.tensor(y[:W + KG], device=dev).contiguous(), KG, W,
+                                    flush, gfilt.stream, dev)
+        gfilt.close()
+        glob = {"value": world * w.N * KG / (sum(g_ms) * 1e-3), "unit": METRIC, "steps": KG,
+                "ms_per_step": sum(g_ms) / KG, "p99_ms": float(np.percentile(g_ms, 99)),
+                "kernels_per_step": 3}
+    eq = None
+    if not a.no_global and rank == 0 and w.model.kind == "sv" and w.N == (1 << 24):
+        eq = equal_error_leg(bf, w, dev)
 
     if world > 1:
         t = torch.tensor([total_ms, e2e_s, resident_ms], device=dev, dtype=torch.float64)
@@ -323,7 +443,8 @@ def ours_main(a):
             cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": W,
-        "ms_per_step": total_ms / K, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "ms_per_step": total_ms / K, "p50_ms": p50_ms, "p99_ms": p99_ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32", "data": "synthetic",
         "config": {"workload": a.workload, "N": w.N, "radices": list(w.radices), "d": w.model.d,
                    "model": w.model.kind, "l2": "flushed before every timed step (512 MB write)",
@@ -339,6 +460,8 @@ def ours_main(a):
                 "d2h_bytes_per_step": 4 * w.model.d + 8 + 4, "loglik": ll_e2e},
         "gpu_launches": K,
         "clocks": clk,
+        "global_resampling": glob,
+        "equal_error": eq,
     }
     print(json.dumps(line))
     filt.close()
