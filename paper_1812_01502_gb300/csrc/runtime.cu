@@ -14,7 +14,7 @@
 #include <string>
 #include <vector>
 
-#include "../../include/bfpf.h"
+#include "bfpf.h"
 #include "bfpf_device.cuh"
 #include "bfpf_kernels.h"
 

@@ -20,7 +20,8 @@
 //
 // Integer resampling rule (shared with the oracle): delta = fp32(lw - max),
 // e = exp(delta), q = floor(e 2^24), P = inclusive prefix, Q = P_{A-1},
-// u = floor(r Q / 2^32), ancestor = #{j : P_j <= u} (binary lifting).
+// u = floor(r Q / 2^32), ancestor = #{j : P_j <= u}, found with two 16-byte
+// shared-memory loads (bucket pivots P_3, P_7, ..., then the bucket's 4 sums).
 #pragma once
 
 #include "bfpf_device.cuh"
@@ -38,8 +39,15 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
   constexpr int GPB = kBlock / G;          // groups per block iteration
   constexpr int LD = GPB + (G > 1 ? 1 : 0);
   constexpr unsigned FULL = 0xffffffffu;
-  // s_tab[r * LD + tg]: prefix sums of group tg; s_tab[(A + t * A + r) * LD + tg]: states
-  __shared__ uint32_t s_tab[(1 + D) * A * LD];
+  // Prefix-sum rows, one per group: P_0 .. P_{A-1}, then the bucket pivots
+  // P_3, P_7, ... (A >= 8); the row stride RS = 4 mod 8 words puts the 16-byte
+  // loads of 8 lanes (different groups) on distinct banks.
+  constexpr int PIV = (A >= 8) ? A / 4 : 0;
+  constexpr int RS = (A + PIV) + ((12 - (A + PIV) % 8) % 8);
+  static_assert(RS % 8 == 4 && RS >= A + PIV, "row stride");
+  __shared__ __align__(16) uint32_t s_rows[GPB * RS];
+  // states, [t][member][group]: the gather of a warp reads distinct banks
+  __shared__ uint32_t s_tab[D * A * LD];
 
   const uint32_t tid = threadIdx.x;
   const uint32_t tg = tid / G, j = tid % G;
@@ -58,7 +66,8 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
   const uint32_t log2s = gg.log2s, log2as = gg.log2as;
   const uint32_t smask = (1u << log2s) - 1u;
   const bool contiguous = (log2s == 0) && (M % 4 == 0);   // digit 0: members are adjacent
-  uint32_t* const col = s_tab + tg;                        // my group's column of the tables
+  uint32_t* const col = s_tab + tg;                        // my group's column of the state table
+  uint32_t* const row = s_rows + tg * RS;                  // my group's prefix-sum row
 
   Partial acc{-INFINITY, 0.0f, 0.0f};
   float accx[D];
@@ -170,11 +179,25 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
       for (int t = 0; t < D; ++t) sx[t] += __shfl_xor_sync(FULL, sx[t], off);
     }
 #pragma unroll
+    for (int mm = 0; mm < M; ++mm) P[mm] += excl;
+    if constexpr (M % 4 == 0) {
+#pragma unroll
+      for (int q = 0; q < M / 4; ++q)
+        *reinterpret_cast<uint4*>(row + j * M + 4 * q) = make_uint4(P[4 * q], P[4 * q + 1], P[4 * q + 2], P[4 * q + 3]);
+    } else {
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm) row[j * M + mm] = P[mm];
+    }
+    if constexpr (PIV > 0) {
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm)
+        if (((j * M + mm) & 3u) == 3u) row[A + ((j * M + mm) >> 2)] = P[mm];
+    }
+#pragma unroll
     for (int mm = 0; mm < M; ++mm) {
       const uint32_t r = j * M + mm;
-      col[r * LD] = P[mm] + excl;
 #pragma unroll
-      for (int t = 0; t < D; ++t) col[(A + t * A + r) * LD] = __float_as_uint(xv[mm][t]);
+      for (int t = 0; t < D; ++t) col[(t * A + r) * LD] = __float_as_uint(xv[mm][t]);
     }
     if (j == 0) {
       lV_out[g] = (Q != 0) ? (mx + logf(s1) - gg.log_a) : -INFINITY;
@@ -185,7 +208,7 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
     // ---- per 4 members: random words (group-major counters), draws, gather, mutate, store ----
     const uint32_t pi0 = g * A + j * M;
     float xo[M][D];
-    uint32_t coff[M];          // word offset of the ancestor's row in the tables
+    uint32_t coff[M];          // ancestor's digit k
 #pragma unroll
     for (int q4 = 0; q4 < (M + 3) / 4; ++q4) {
       constexpr int MQ = (M < 4) ? M : 4;             // members handled in this round
@@ -238,16 +261,30 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
       for (int mq = 0; mq < MQ; ++mq) {
         const int mm = 4 * q4 + mq;
         const uint32_t u = __umulhi(rw[mq], Q);       // floor(r Q / 2^32)
-        const uint32_t* cp = col;                      // binary lifting over the prefix sums
+        uint32_t c;                                    // #{j : P_j <= u}: 4-ary, two levels
+        if constexpr (A == 2) {
+          c = (u >= row[0]) ? 1u : 0u;
+        } else {
+          uint32_t b = 0;                              // bucket: pivots P_{4b+3} <= u
+          if constexpr (PIV > 0) {
 #pragma unroll
-        for (int stp = A / 2; stp >= 1; stp >>= 1)
-          if (cp[(stp - 1) * LD] <= u) cp += stp * LD;
-        if (Q == 0) cp = col + (j * M + mm) * LD;     // an all-zero group keeps its particles
+            for (int q = 0; q < PIV / 4 + (PIV % 4 ? 1 : 0); ++q) {
+              const uint4 pv = *reinterpret_cast<const uint4*>(row + A + 4 * q);
+              const uint32_t pvs[4] = {pv.x, pv.y, pv.z, pv.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (4 * q + e < PIV - 1) b += (u >= pvs[e]) ? 1u : 0u;
+            }
+          }
+          const uint4 v = *reinterpret_cast<const uint4*>(row + 4 * b);
+          c = 4 * b + ((u >= v.x) ? 1u : 0u) + ((u >= v.y) ? 1u : 0u) + ((u >= v.z) ? 1u : 0u);
+        }
+        if (Q == 0) c = j * M + mm;                    // an all-zero group keeps its particles
         float xh[D];
 #pragma unroll
-        for (int t = 0; t < D; ++t) xh[t] = __uint_as_float(cp[(A + t * A) * LD]);
+        for (int t = 0; t < D; ++t) xh[t] = __uint_as_float(col[(t * A + c) * LD]);
         mutate<D, KIND>(mp, xh, z + mq * D, xo[mm]);
-        coff[mm] = (uint32_t)(cp - col);
+        coff[mm] = c;
       }
     }
     if (contiguous) {
@@ -265,7 +302,7 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
     }
     if (p.anc) {
 #pragma unroll
-      for (int mm = 0; mm < M; ++mm) p.anc[i0 + (mm << log2s)] = (int32_t)(ig + ((coff[mm] / LD) << log2s));
+      for (int mm = 0; mm < M; ++mm) p.anc[i0 + (mm << log2s)] = (int32_t)(ig + (coff[mm] << log2s));
     }
     __syncwarp();
   }
