@@ -210,6 +210,35 @@ pf_status pf_philox_blocks(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
                            int64_t count, uint32_t* out, void* stream);
 
 /*
+ * Batches: F independent filters with their own model, N, radices and seed
+ * (uneven sizes and state dimensions), advanced together, one time step per
+ * kernel launch for the whole batch.  radices is the concatenation of the F
+ * radix lists (m[f] entries each).  Every radix must be <= 256, and m[f] == 1
+ * needs N[f] <= 1024; otherwise the rules of pf_create apply per filter.
+ * Filter f's observation at step n is y[(f*T + n)*dy_max + j] in pf_batch_run,
+ * dy_max = the largest dy of the batch; outputs are [F][T] (increments, ESS)
+ * and [F][T][d_max] (means), d_max = the largest d.  workspace as in pf_create
+ * (NULL: the library allocates).  A filter's results do not depend on the
+ * other filters of the batch.
+ */
+typedef struct pf_batch pf_batch;
+pf_status pf_batch_workspace_size(int32_t F, const pf_model* models, const int64_t* N,
+                                  const int32_t* radices, const int32_t* m,
+                                  const pf_options* opts, size_t* bytes);
+pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, const int32_t* radices,
+                          const int32_t* m, const uint64_t* seeds, const pf_options* opts,
+                          void* workspace, size_t workspace_bytes, pf_batch** out);
+pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_incs, float* means,
+                       float* ess);
+/* Cumulative FP64 log-likelihood of every filter (F doubles, host).  Synchronises. */
+pf_status pf_batch_loglik(const pf_batch* b, double* out);
+/* State of filter f as pf_get_state (x: N[f]*d floats, lV, scalars {n, loglik, mu, mu_used}). */
+pf_status pf_batch_get_state(const pf_batch* b, int32_t f, float* x, float* lV, double* scalars);
+pf_status pf_batch_destroy(pf_batch* b);
+/* Message for the last failed call on `b` (or on this thread when b is NULL). */
+const char* pf_batch_last_error(const pf_batch* b);
+
+/*
  * pf_step_noalloc - one time step on buffers the caller already owns, with no
  * device allocation of any kind.  (The paper has no counterpart: this entry
  * point exists for callers whose device memory is managed by someone else -

@@ -83,6 +83,15 @@ def load_library(path: str = LIB_PATH):
         "pf_describe": (i32, [vp, c.c_char_p, c.c_size_t]),
         "pf_last_error": (c.c_char_p, [vp]),
         "pf_philox_blocks": (i32, [u64, u32, u32, u32, u32, i64, vp, vp]),
+        "pf_batch_workspace_size": (i32, [i32, c.POINTER(PFModel), c.POINTER(i64), c.POINTER(i32), c.POINTER(i32),
+                                          c.POINTER(PFOptions), c.POINTER(c.c_size_t)]),
+        "pf_batch_create": (i32, [i32, c.POINTER(PFModel), c.POINTER(i64), c.POINTER(i32), c.POINTER(i32),
+                                  c.POINTER(u64), c.POINTER(PFOptions), vp, c.c_size_t, c.POINTER(vp)]),
+        "pf_batch_run": (i32, [vp, vp, i32, vp, vp, vp]),
+        "pf_batch_loglik": (i32, [vp, vp]),
+        "pf_batch_get_state": (i32, [vp, i32, vp, vp, vp]),
+        "pf_batch_destroy": (i32, [vp]),
+        "pf_batch_last_error": (c.c_char_p, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -291,6 +300,112 @@ class ButterflyFilter:
         return b.value
 
 
+class FilterBatch:
+    """F independent filters (own model, N, radices, seed) advanced together, one
+    kernel launch per time step for the whole batch (pf_batch_*)."""
+
+    def __init__(self, specs, *, chunk_len: int = 0, device=None, stream=None):
+        """specs: sequence of (model, N, radices, seed)."""
+        torch = _torch()
+        lib = load_library()
+        if not torch.cuda.is_available():
+            raise PFError(PF_ECUDA, "no CUDA device: the butterfly filter runs only on the GPU")
+        self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
+        self.F = len(specs)
+        self._keep = []
+        models = (PFModel * self.F)()
+        for f, (model, N, radices, seed) in enumerate(specs):
+            pm, keep = make_model(model)
+            models[f] = pm
+            self._keep.append(keep)
+        self._models = models
+        self.N = [int(s[1]) for s in specs]
+        self.radices = [tuple(int(a) for a in s[2]) for s in specs]
+        self.d = [models[f].d for f in range(self.F)]
+        self.dy = [models[f].dy for f in range(self.F)]
+        self.d_max, self.dy_max = max(self.d), max(self.dy)
+        self._N = (ctypes.c_int64 * self.F)(*self.N)
+        flat = [a for r in self.radices for a in r]
+        self._rad = (ctypes.c_int32 * len(flat))(*flat)
+        self._m = (ctypes.c_int32 * self.F)(*[len(r) for r in self.radices])
+        self._seeds = (ctypes.c_uint64 * self.F)(*[int(s[3]) for s in specs])
+        self._opts = PFOptions(tile=0, chunk_len=int(chunk_len), flags=0, grid=0,
+                               stream=ctypes.c_void_p(self.stream.cuda_stream))
+        with torch.cuda.device(self.device):
+            nbytes = ctypes.c_size_t(0)
+            _check(lib.pf_batch_workspace_size(self.F, models, self._N, self._rad, self._m, ctypes.byref(self._opts),
+                                               ctypes.byref(nbytes)))
+            self.workspace = torch.empty(int(nbytes.value), dtype=torch.uint8, device=self.device)
+            h = ctypes.c_void_p()
+            st = lib.pf_batch_create(self.F, models, self._N, self._rad, self._m, self._seeds, ctypes.byref(self._opts),
+                                     _cuda_ptr(self.workspace), int(nbytes.value), ctypes.byref(h))
+            if st != PF_OK:
+                raise PFError(st, lib.pf_batch_last_error(None).decode(errors="replace"))
+        self._h = h
+        self.steps = 0
+
+    def _check(self, st):
+        if st != PF_OK:
+            raise PFError(st, _lib.pf_batch_last_error(self._h).decode(errors="replace"))
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._check(_lib.pf_batch_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def run(self, y, outputs: bool = True):
+        """y: (F, T, dy_max) float32 (numpy, or torch on host or device).  Returns
+        dict(inc (F, T), mean (F, T, d_max), ess (F, T)) (numpy for host input, torch otherwise)."""
+        torch = _torch()
+        if isinstance(y, torch.Tensor):
+            yt = y.to(torch.float32).contiguous()
+            T = yt.shape[1]
+            ptr, keep, on_dev = ctypes.c_void_p(yt.data_ptr()), yt, yt.is_cuda
+        else:
+            ya = np.ascontiguousarray(np.asarray(y, dtype=np.float32))
+            T = ya.shape[1]
+            ptr, keep, on_dev = ya.ctypes.data_as(ctypes.c_void_p), ya, False
+        res = None
+        ip = mp = ep = None
+        if outputs:
+            if on_dev:
+                res = dict(inc=torch.empty((self.F, T), dtype=torch.float64, device=self.device),
+                           mean=torch.empty((self.F, T, self.d_max), dtype=torch.float32, device=self.device),
+                           ess=torch.empty((self.F, T), dtype=torch.float32, device=self.device))
+                ip, mp, ep = (ctypes.c_void_p(res[k].data_ptr()) for k in ("inc", "mean", "ess"))
+            else:
+                res = dict(inc=np.empty((self.F, T)), mean=np.empty((self.F, T, self.d_max), dtype=np.float32),
+                           ess=np.empty((self.F, T), dtype=np.float32))
+                ip, mp, ep = (res[k].ctypes.data_as(ctypes.c_void_p) for k in ("inc", "mean", "ess"))
+        self._check(_lib.pf_batch_run(self._h, ptr, int(T), ip, mp, ep))
+        del keep
+        self.steps += T
+        return res
+
+    def loglik(self) -> np.ndarray:
+        out = np.empty(self.F)
+        self._check(_lib.pf_batch_loglik(self._h, out.ctypes.data_as(ctypes.c_void_p)))
+        return out
+
+    def state(self, f: int):
+        """(x (N, d), lV, dict(n, loglik, mu, mu_used)) of filter f."""
+        m = len(self.radices[f])
+        kp = (self.steps - 1) % m
+        x = np.empty((self.d[f], self.N[f]), dtype=np.float32)
+        lv = np.empty(self.N[f] // self.radices[f][kp], dtype=np.float32)
+        sc = np.empty(4)
+        self._check(_lib.pf_batch_get_state(self._h, int(f), x.ctypes.data_as(ctypes.c_void_p),
+                                            lv.ctypes.data_as(ctypes.c_void_p), sc.ctypes.data_as(ctypes.c_void_p)))
+        return x.T.copy(), lv, dict(n=int(sc[0]), loglik=float(sc[1]), mu=float(sc[2]), mu_used=float(sc[3]))
+
+
 def philox_blocks(seed: int, counter, count: int, device=None):
     """Philox4x32-10 words for counters (c0 + j, c1, c2, c3), j < count: a (count, 4) int64
     tensor of uint32 values (computed on the GPU by the library)."""
@@ -304,4 +419,4 @@ def philox_blocks(seed: int, counter, count: int, device=None):
     return (out.to(torch.int64) & 0xFFFFFFFF).reshape(count, 4)
 
 
-__all__ = ["ButterflyFilter", "PFError", "philox_blocks", "load_library", "make_model", "LIB_PATH"]
+__all__ = ["ButterflyFilter", "FilterBatch", "PFError", "philox_blocks", "load_library", "make_model", "LIB_PATH"]

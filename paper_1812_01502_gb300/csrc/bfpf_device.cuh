@@ -132,6 +132,15 @@ __device__ __forceinline__ void normals4_fast(uint4 w, float z[4]) {
   box_muller_fast(w.z, w.w, z[2], z[3]);
 }
 
+// exp(x) for the integer weights, x = lw - max <= 0: ex2.approx.ftz.f32 of
+// x log2(e).  The PTX ISA specifies ex2.approx(+-0) = +1, and 0 * log2(e) is
+// exactly 0, so the group maximum always weighs exactly 1 (q = 2^B).
+__device__ __forceinline__ float exp_weight(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x * 1.4426950408889634f));
+  return r;
+}
+
 // ---------------------------------------------------------------------------
 // Division by an invariant divisor: q = floor(x / d) for 0 <= x < 2^32.
 // With l = ceil(log2 d) and mul = floor(2^32 (2^l - d) / d) + 1,

@@ -36,6 +36,10 @@ struct GlobalKernels {
 };
 bool select_global_kernels(int d, int kind, GlobalKernels& gk);
 
+// Batched filters (batch.cu): batch_step_kernel(BatchParams), batch_init_kernel(BatchParams).
+const void* batch_step_kernel_ptr();
+const void* batch_init_kernel_ptr();
+
 cudaError_t launch_philox_blocks(uint64_t seed, uint4 c, uint32_t count, uint32_t* out,
                                  cudaStream_t stream);
 

@@ -15,6 +15,7 @@
 #include <vector>
 
 #include "bfpf.h"
+#include "bfpf_batch.cuh"
 #include "bfpf_device.cuh"
 #include "bfpf_kernels.h"
 
@@ -894,3 +895,315 @@ extern "C" pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int
   out[2] = (double)ess;
   return PF_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Batches of independent filters
+// ---------------------------------------------------------------------------
+struct pf_batch {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  bool own_ws = false;
+  unsigned char* ws = nullptr;
+  size_t ws_bytes = 0;
+  int F = 0, ring = 64, dy_max = 1, d_max = 1;
+  size_t smem = 0;
+  BatchParams BP{};
+  std::vector<BatchFilter> host_filters;    // host copy (pointers, sizes, geometry)
+  std::vector<uint32_t> order;
+  uint64_t n_host = 0;
+  cudaGraphExec_t graph = nullptr;
+  std::string err;
+};
+
+namespace {
+
+struct BatchLayout {
+  size_t state, filters, order, y_ring, inc_ring, mean_ring, ess_ring, total;
+  std::vector<size_t> x, lv0, lv1;
+};
+
+// Plan every filter and lay the batch out in one workspace.
+pf_status plan_batch(int32_t F, const pf_model* models, const int64_t* N, const int32_t* radices, const int32_t* m,
+                     const pf_options* opts, std::vector<Plan>& plans, BatchLayout& L, int& ring, int& dy_max,
+                     int& d_max, size_t& smem, std::string& msg) {
+  if (F < 1 || !models || !N || !radices || !m) { msg = "need F >= 1 and non-NULL arrays"; return PF_EINVAL; }
+  plans.resize(F);
+  ring = (opts && opts->chunk_len > 0) ? std::min<int>(opts->chunk_len, (int)kRing) : 64;
+  dy_max = d_max = 1;
+  smem = 0;
+  size_t roff = 0;
+  for (int32_t f = 0; f < F; ++f) {
+    if (m[f] < 1 || m[f] > kMaxDigits) { msg = "filter " + std::to_string(f) + ": need 1 <= m <= 32"; return PF_EINVAL; }
+    pf_options o{};
+    const int d = models[f].d;
+    o.tile = (opts && opts->tile > 0) ? opts->tile : (d <= 1 ? 4096 : d <= 4 ? 2048 : 1024);
+    pf_status s = make_plan(&models[f], N[f], radices + roff, m[f], &o, plans[f], msg);
+    if (s != PF_OK) { msg = "filter " + std::to_string(f) + ": " + msg; return s; }
+    roff += (size_t)m[f];
+    if (plans[f].global || plans[f].wide) {
+      msg = "filter " + std::to_string(f) + ": batches need radices <= 256 (and N <= 1024 when m = 1)";
+      return PF_EINVAL;
+    }
+    dy_max = std::max(dy_max, plans[f].dy);
+    d_max = std::max(d_max, plans[f].d);
+    smem = std::max(smem, plans[f].smem);
+  }
+  size_t off = 0;
+  auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
+  L.state = take(sizeof(BatchState));
+  L.filters = take(sizeof(BatchFilter) * (size_t)F);
+  L.order = take(4 * (size_t)F);
+  L.y_ring = take((size_t)4 * F * ring * dy_max);
+  L.inc_ring = take((size_t)8 * F * ring);
+  L.mean_ring = take((size_t)4 * F * ring * d_max);
+  L.ess_ring = take((size_t)4 * F * ring);
+  L.x.resize(F);
+  L.lv0.resize(F);
+  L.lv1.resize(F);
+  for (int32_t f = 0; f < F; ++f) {
+    L.x[f] = take((size_t)4 * plans[f].d * plans[f].N);
+    L.lv0[f] = take((size_t)4 * (plans[f].N / plans[f].min_a));
+    L.lv1[f] = take((size_t)4 * (plans[f].N / plans[f].min_a));
+  }
+  L.total = off;
+  return PF_OK;
+}
+
+pf_status bfail(const pf_batch* b, pf_status s, const std::string& msg) {
+  if (b) const_cast<pf_batch*>(b)->err = msg;
+  else t_error = msg;
+  return s;
+}
+
+#define PF_BCUDA(b, call)                                                              \
+  do {                                                                                 \
+    cudaError_t e_ = (call);                                                           \
+    if (e_ != cudaSuccess)                                                             \
+      return bfail((b), PF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+}  // namespace
+
+extern "C" {
+
+pf_status pf_batch_workspace_size(int32_t F, const pf_model* models, const int64_t* N, const int32_t* radices,
+                                  const int32_t* m, const pf_options* opts, size_t* bytes) {
+  if (!bytes) return bfail(nullptr, PF_EINVAL, "bytes is NULL");
+  std::vector<Plan> plans;
+  BatchLayout L;
+  int ring, dy_max, d_max;
+  size_t smem;
+  std::string msg;
+  pf_status s = plan_batch(F, models, N, radices, m, opts, plans, L, ring, dy_max, d_max, smem, msg);
+  if (s != PF_OK) return bfail(nullptr, s, msg);
+  *bytes = L.total;
+  return PF_OK;
+}
+
+pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, const int32_t* radices,
+                          const int32_t* m, const uint64_t* seeds, const pf_options* opts, void* workspace,
+                          size_t workspace_bytes, pf_batch** out) {
+  if (!out || !seeds) return bfail(nullptr, PF_EINVAL, "NULL argument");
+  *out = nullptr;
+  pf_batch* b = new (std::nothrow) pf_batch();
+  if (!b) return bfail(nullptr, PF_ENOMEM, "host allocation failed");
+  std::vector<Plan> plans;
+  BatchLayout L;
+  std::string msg;
+  pf_status s = plan_batch(F, models, N, radices, m, opts, plans, L, b->ring, b->dy_max, b->d_max, b->smem, msg);
+  if (s != PF_OK) {
+    delete b;
+    return bfail(nullptr, s, msg);
+  }
+  cudaError_t e = cudaGetDevice(&b->device);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(batch_step_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+  if (e != cudaSuccess) {
+    delete b;
+    return bfail(nullptr, PF_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+  }
+  b->F = F;
+  b->stream = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+  if (workspace) {
+    if (workspace_bytes < L.total || reinterpret_cast<uintptr_t>(workspace) % kAlign) {
+      delete b;
+      return bfail(nullptr, PF_EINVAL, "workspace too small or not 256-byte aligned");
+    }
+    b->ws = static_cast<unsigned char*>(workspace);
+    b->ws_bytes = workspace_bytes;
+  } else {
+    e = cudaMalloc(&b->ws, L.total);
+    if (e != cudaSuccess) {
+      delete b;
+      return bfail(nullptr, PF_ENOMEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+    }
+    b->own_ws = true;
+    b->ws_bytes = L.total;
+  }
+  e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    if (b->own_ws) cudaFree(b->ws);
+    delete b;
+    return bfail(nullptr, PF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
+  }
+  b->host_filters.resize(F);
+  std::vector<std::pair<double, uint32_t>> work(F);
+  for (int32_t f = 0; f < F; ++f) {
+    BatchFilter& bf = b->host_filters[f];
+    std::memset(&bf, 0, sizeof(bf));
+    const Plan& pl = plans[f];
+    bf.x = reinterpret_cast<float*>(b->ws + L.x[f]);
+    bf.lV[0] = reinterpret_cast<float*>(b->ws + L.lv0[f]);
+    bf.lV[1] = reinterpret_cast<float*>(b->ws + L.lv1[f]);
+    bf.N = pl.N;
+    bf.m = (uint32_t)pl.m;
+    bf.cap = pl.cap;
+    bf.rk = make_round_keys(seeds[f]);
+    bf.model = pl.mp;
+    std::memcpy(bf.geom, pl.geom, sizeof(bf.geom));
+    work[f] = {-(double)pl.N * (pl.d + 1), (uint32_t)f};
+  }
+  std::sort(work.begin(), work.end());
+  b->order.resize(F);
+  for (int32_t f = 0; f < F; ++f) b->order[f] = work[f].second;
+  BatchParams& P = b->BP;
+  P.filters = reinterpret_cast<BatchFilter*>(b->ws + L.filters);
+  P.order = reinterpret_cast<const uint32_t*>(b->ws + L.order);
+  P.state = reinterpret_cast<BatchState*>(b->ws + L.state);
+  P.y_ring = reinterpret_cast<const float*>(b->ws + L.y_ring);
+  P.inc_ring = reinterpret_cast<double*>(b->ws + L.inc_ring);
+  P.mean_ring = reinterpret_cast<float*>(b->ws + L.mean_ring);
+  P.ess_ring = reinterpret_cast<float*>(b->ws + L.ess_ring);
+  P.F = (uint32_t)F;
+  P.ring = (uint32_t)b->ring;
+  P.dy_max = (uint32_t)b->dy_max;
+  P.d_max = (uint32_t)b->d_max;
+  auto bail = [&](cudaError_t err, const char* what) {
+    std::string m2 = std::string(what) + ": " + cudaGetErrorString(err);
+    cudaStreamSynchronize(b->stream);
+    cudaStreamDestroy(b->cap_stream);
+    if (b->own_ws) cudaFree(b->ws);
+    delete b;
+    return bfail(nullptr, PF_ECUDA, m2);
+  };
+  e = cudaMemcpyAsync(P.filters, b->host_filters.data(), sizeof(BatchFilter) * (size_t)F, cudaMemcpyHostToDevice,
+                      b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(const_cast<uint32_t*>(P.order), b->order.data(), 4 * (size_t)F, cudaMemcpyHostToDevice,
+                        b->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(P.state, 0, sizeof(BatchState), b->stream);
+  for (int32_t f = 0; f < F && e == cudaSuccess; ++f)
+    e = cudaMemsetAsync(b->ws + L.lv0[f], 0, (size_t)4 * (plans[f].N / plans[f].min_a), b->stream);
+  if (e != cudaSuccess) return bail(e, "batch set-up copy");
+  void* args[] = {&b->BP};
+  e = cudaLaunchKernel(batch_init_kernel_ptr(), dim3(F), dim3(kBlock), args, 0, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);   // host copies above must complete
+  if (e != cudaSuccess) return bail(e, "batch init");
+  *out = b;
+  return PF_OK;
+}
+
+pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_incs, float* means, float* ess) {
+  if (!b) return bfail(nullptr, PF_EINVAL, "batch is NULL");
+  if (T < 0 || (T > 0 && !y)) return bfail(b, PF_EINVAL, "need T >= 0 and y != NULL");
+  const int R = b->ring, F = b->F;
+  void* args[] = {&b->BP};
+  int32_t done = 0;
+  while (done < T) {
+    const uint32_t slot0 = (uint32_t)(b->n_host % (uint64_t)R);
+    const int32_t L = std::min<int32_t>(R - (int32_t)slot0, T - done);
+    const size_t yw = (size_t)4 * b->dy_max;
+    PF_BCUDA(b, cudaMemcpy2DAsync(const_cast<float*>(b->BP.y_ring) + (size_t)slot0 * b->dy_max, yw * R,
+                                  y + (size_t)done * b->dy_max, yw * T, yw * L, F, cudaMemcpyDefault, b->stream));
+    if (L == R && R > 1) {
+      if (!b->graph) {
+        cudaGraph_t graph = nullptr;
+        PF_BCUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = cudaSuccess;
+        for (int j = 0; j < L && le == cudaSuccess; ++j)
+          le = cudaLaunchKernel(batch_step_kernel_ptr(), dim3(F), dim3(kBlock), args, b->smem, b->cap_stream);
+        cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
+        if (le != cudaSuccess) return bfail(b, PF_ECUDA, std::string("capture launch: ") + cudaGetErrorString(le));
+        if (ce != cudaSuccess) return bfail(b, PF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
+        cudaError_t ie = cudaGraphInstantiate(&b->graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (ie != cudaSuccess) {
+          b->graph = nullptr;
+          return bfail(b, PF_ECUDA, std::string("cudaGraphInstantiate: ") + cudaGetErrorString(ie));
+        }
+      }
+      PF_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
+    } else {
+      for (int j = 0; j < L; ++j)
+        PF_BCUDA(b, cudaLaunchKernel(batch_step_kernel_ptr(), dim3(F), dim3(kBlock), args, b->smem, b->stream));
+    }
+    if (loglik_incs)
+      PF_BCUDA(b, cudaMemcpy2DAsync(loglik_incs + done, (size_t)8 * T, b->BP.inc_ring + slot0, (size_t)8 * R,
+                                    (size_t)8 * L, F, cudaMemcpyDefault, b->stream));
+    if (ess)
+      PF_BCUDA(b, cudaMemcpy2DAsync(ess + done, (size_t)4 * T, b->BP.ess_ring + slot0, (size_t)4 * R, (size_t)4 * L,
+                                    F, cudaMemcpyDefault, b->stream));
+    if (means) {
+      const size_t mw = (size_t)4 * b->d_max;
+      PF_BCUDA(b, cudaMemcpy2DAsync(means + (size_t)done * b->d_max, mw * T, b->BP.mean_ring + (size_t)slot0 * b->d_max,
+                                    mw * R, mw * L, F, cudaMemcpyDefault, b->stream));
+    }
+    b->n_host += L;
+    done += L;
+  }
+  PF_BCUDA(b, cudaGetLastError());
+  if (loglik_incs || means || ess) PF_BCUDA(b, cudaStreamSynchronize(b->stream));
+  return PF_OK;
+}
+
+pf_status pf_batch_loglik(const pf_batch* b, double* out) {
+  if (!b || !out) return bfail(b, PF_EINVAL, "NULL argument");
+  std::vector<BatchFilter> tmp(b->F);
+  PF_BCUDA(b, cudaMemcpyAsync(tmp.data(), b->BP.filters, sizeof(BatchFilter) * (size_t)b->F, cudaMemcpyDeviceToHost,
+                              b->stream));
+  PF_BCUDA(b, cudaStreamSynchronize(b->stream));
+  for (int f = 0; f < b->F; ++f) out[f] = tmp[f].st.loglik;
+  return PF_OK;
+}
+
+pf_status pf_batch_get_state(const pf_batch* b, int32_t f, float* x, float* lV, double* scalars) {
+  if (!b || f < 0 || f >= b->F) return bfail(b, PF_EINVAL, "bad batch or filter index");
+  BatchFilter bf;
+  BatchState bs;
+  PF_BCUDA(b, cudaMemcpyAsync(&bf, b->BP.filters + f, sizeof(bf), cudaMemcpyDeviceToHost, b->stream));
+  PF_BCUDA(b, cudaMemcpyAsync(&bs, b->BP.state, sizeof(bs), cudaMemcpyDeviceToHost, b->stream));
+  PF_BCUDA(b, cudaStreamSynchronize(b->stream));
+  if (x) PF_BCUDA(b, cudaMemcpyAsync(x, bf.x, (size_t)4 * bf.model.d * bf.N, cudaMemcpyDeviceToHost, b->stream));
+  if (lV) {
+    const uint32_t kp = (bs.n + bf.m - 1) % bf.m;
+    PF_BCUDA(b, cudaMemcpyAsync(lV, bf.lV[bs.n & 1u], (size_t)4 * (bf.N / bf.geom[kp].a), cudaMemcpyDeviceToHost,
+                                b->stream));
+  }
+  PF_BCUDA(b, cudaStreamSynchronize(b->stream));
+  if (scalars) {
+    scalars[0] = (double)bs.n;
+    scalars[1] = bf.st.loglik;
+    scalars[2] = bf.st.mu;
+    scalars[3] = (double)bf.st.mu_f;
+  }
+  return PF_OK;
+}
+
+const char* pf_batch_last_error(const pf_batch* b) {
+  if (b) return b->err.c_str();
+  return t_error.c_str();
+}
+
+pf_status pf_batch_destroy(pf_batch* b) {
+  if (!b) return PF_OK;
+  cudaError_t e = cudaStreamSynchronize(b->stream);
+  if (b->graph) cudaGraphExecDestroy(b->graph);
+  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
+  if (b->own_ws && b->ws) cudaFree(b->ws);
+  delete b;
+  if (e != cudaSuccess) return bfail(nullptr, PF_ECUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
+  return PF_OK;
+}
+
+}  // extern "C"

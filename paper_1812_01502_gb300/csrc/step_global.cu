@@ -106,9 +106,7 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
   for (int q = 0; q < kScanItems; ++q) {
     unsigned long long w = 0;
     if (gmax != -INFINITY) {
-      const float dl = lwv[q] - gmax;
-      float e = __expf(dl);
-      e = (dl == 0.0f) ? 1.0f : e;
+      const float e = exp_weight(lwv[q] - gmax);
       w = __float2ull_rz(e * 4294967296.0f);
     }
     tot += w;

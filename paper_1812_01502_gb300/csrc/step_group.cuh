@@ -121,9 +121,7 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
     for (int t = 0; t < D; ++t) sx[t] = 0.0f;
 #pragma unroll
     for (int mm = 0; mm < M; ++mm) {
-      const float dl = lw[mm] - mx;
-      float e = __expf(dl);
-      e = (dl == 0.0f) ? 1.0f : e;                      // the group maximum weighs exactly 2^24
+      const float e = exp_weight(lw[mm] - mx);         // the group maximum weighs exactly 1
       s1 += e;
       s2 = fmaf(e, e, s2);
 #pragma unroll
@@ -151,8 +149,7 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
       for (int t = 0; t < D; ++t) sx[t] = 0.0f;
 #pragma unroll
       for (int mm = 0; mm < M; ++mm) {
-        const float dl = lw[mm] - mx;
-        const float e = live ? ((dl == 0.0f) ? 1.0f : __expf(dl)) : 0.0f;
+        const float e = live ? exp_weight(lw[mm] - mx) : 0.0f;
         s1 += e;
         s2 = fmaf(e, e, s2);
 #pragma unroll

@@ -1,0 +1,236 @@
+// step_tile.cuh - the shared-memory tile form of one time step (general
+// radices up to 1024), shared by the single-filter kernel (step_butterfly.cu)
+// and the batched kernel (batch.cu).
+//
+// Tile: nh blocks of the digits above k x a_k rows x nl columns of the digits
+// below k; tile position p = row*nl + col, row = hh*a_k + r; global index
+// i = base + row*s_k + col.  Per tile: coalesced load of the states into
+// shared memory, weights, per-group max / log-sum-exp / integer prefix sums
+// (one thread per group), then per member quad: group-major Philox draws,
+// ancestor search, gather from shared memory, mutation, store.
+#pragma once
+
+#include <cfloat>
+#include <type_traits>
+
+#include "bfpf_device.cuh"
+#include "bfpf_epilogue.cuh"
+#include "bfpf_model.cuh"
+
+namespace bfpf {
+
+__device__ __forceinline__ unsigned long long mulhi64(unsigned long long a, unsigned long long b) {
+  return __umul64hi(a, b);
+}
+
+// Everything one time step does to the tiles first, first + stride, ... of one
+// filter (the tile loop of the general kernel; also run by the batched kernel).
+struct TileCtx {
+  float* x;                  // [d][N] states (updated in place)
+  const float* lV_in;        // carried log weights, groups of the previous digit
+  float* lV_out;             // new carried log weights, groups of this digit
+  int32_t* anc;              // ancestors (nullptr: not recorded)
+  const RoundKeys* rk;
+  const ModelParams* mp;
+  const DigitGeom* g;        // geometry of this step's digit
+  uint32_t N, n, cap;
+  float muf;
+  float y[kMaxDim];
+};
+
+template <int D, int KIND, bool WIDE>
+__device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, uint32_t stride,
+                                           unsigned char* smem_raw, Partial& acc, float* accx,
+                                           uint32_t& status) {
+  using PT = typename std::conditional<WIDE, unsigned long long, uint32_t>::type;
+  const uint32_t tid = threadIdx.x;
+  const uint32_t cap = ctx.cap;
+  float* s_x = reinterpret_cast<float*>(smem_raw);
+  float* s_lw = s_x + D * cap;
+  PT* s_P = reinterpret_cast<PT*>(s_lw + cap);
+  const ModelParams& mp = *ctx.mp;
+  const RoundKeys& rk = *ctx.rk;
+  const DigitGeom& g = *ctx.g;
+  const uint32_t a = g.a, s = g.s, nl = g.nl, tn = g.tile_n;
+  const bool wide_digit = g.wide != 0;
+  const float* __restrict__ lV_in = ctx.lV_in;
+  float* __restrict__ lV_out = ctx.lV_out;
+  float* __restrict__ X = ctx.x;
+  const float muf = ctx.muf;
+  const uint32_t N = ctx.N, n = ctx.n;
+  const float* y = ctx.y;
+  const uint32_t ngroups = g.nh * nl;   // groups per tile
+  // lifting steps of the ancestor search: largest power of two < a (0 if a == 1)
+  uint32_t step0 = 1;
+  while ((step0 << 1) < a) step0 <<= 1;
+  if (a == 1) step0 = 0;
+
+  for (uint32_t tile = first; tile < g.ntiles; tile += stride) {
+    const uint32_t th = fdiv(tile, g.div_tiles_l);
+    const uint32_t tl = tile - th * g.tiles_l;
+    const uint32_t h0 = th * g.nh, l0 = tl * nl;
+    const uint32_t base = h0 * a * s + l0;
+
+    __syncthreads();  // the previous tile's readers are done with shared memory
+
+    // ---- load the tile's states (coalesced rows) ----
+    if (g.quad) {
+      for (uint32_t q = tid; q < (tn >> 2); q += kBlock) {
+        const uint32_t pos = q << 2;
+        const uint32_t row = fdiv(pos, g.div_nl);
+        const uint32_t i = base + row * s + (pos - row * nl);
+#pragma unroll
+        for (int t = 0; t < D; ++t) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(X + (size_t)t * N + i));
+          *reinterpret_cast<float4*>(s_x + t * cap + pos) = v;
+        }
+      }
+    } else {
+      for (uint32_t pos = tid; pos < tn; pos += kBlock) {
+        const uint32_t row = fdiv(pos, g.div_nl);
+        const uint32_t i = base + row * s + (pos - row * nl);
+#pragma unroll
+        for (int t = 0; t < D; ++t) s_x[t * cap + pos] = __ldcs(X + (size_t)t * N + i);
+      }
+    }
+    __syncthreads();
+
+    // ---- weights: lw = lV(group of the previous digit) + log g_n(x) - mu ----
+    for (uint32_t pos = tid; pos < tn; pos += kBlock) {
+      const uint32_t row = fdiv(pos, g.div_nl);
+      const uint32_t i = base + row * s + (pos - row * nl);
+      const uint32_t hp = fdiv(i, g.div_prev_as);
+      const uint32_t lo = i - fdiv(i, g.div_prev_s) * g.prev_s;
+      const float lv = __ldg(lV_in + hp * g.prev_s + lo);
+      float xv[D];
+#pragma unroll
+      for (int t = 0; t < D; ++t) xv[t] = s_x[t * cap + pos];
+      s_lw[pos] = sanitize_logweight(lv + obs_log_term<D, KIND>(mp, y, xv) - muf, status);
+    }
+    __syncthreads();
+
+    // ---- per group: max, log-sum-exp, integer weights and prefix sums ----
+    for (uint32_t gid = tid; gid < ngroups; gid += kBlock) {
+      const uint32_t hh = fdiv(gid, g.div_nl);
+      const uint32_t col = gid - hh * nl;
+      const uint32_t p0 = hh * a * nl + col;
+      float M = -INFINITY;
+      for (uint32_t r = 0; r < a; ++r) M = fmaxf(M, s_lw[p0 + r * nl]);
+      float s1 = 0.0f, s2 = 0.0f, sx[D];
+#pragma unroll
+      for (int t = 0; t < D; ++t) sx[t] = 0.0f;
+      float L;
+      if (M == -INFINITY) {
+        for (uint32_t r = 0; r < a; ++r) s_P[p0 + r * nl] = 0;
+        status |= kStatusZeroGroup;
+        L = -INFINITY;
+      } else {
+        PT P = 0;
+        for (uint32_t r = 0; r < a; ++r) {
+          const uint32_t pos = p0 + r * nl;
+          const float e = exp_weight(s_lw[pos] - M);
+          s1 += e;
+          s2 = fmaf(e, e, s2);
+#pragma unroll
+          for (int t = 0; t < D; ++t) sx[t] = fmaf(e, s_x[t * cap + pos], sx[t]);
+          PT q;
+          if (WIDE && wide_digit) q = (PT)__float2ull_rz(e * 4294967296.0f);
+          else q = (PT)__float2uint_rz(e * 16777216.0f);
+          P += q;
+          s_P[pos] = P;
+        }
+        L = M + logf(s1);
+      }
+      lV_out[(h0 + hh) * s + l0 + col] = L - g.log_a;
+      merge_partial<D>(acc, accx, M, s1, s2, sx);
+    }
+    __syncthreads();
+
+    // ---- draw ancestors (group-major counters), gather, mutate, store ----
+    // Work item = (member quad rq, group gid of the tile); consecutive threads
+    // take consecutive groups, i.e. consecutive columns of a row.
+    const uint32_t nq = (a + 3) >> 2;
+    const bool a4 = (a & 3u) == 0;
+    for (uint32_t it = tid; it < ngroups * nq; it += kBlock) {
+      const uint32_t rq = fdiv(it, g.div_tgroups);
+      const uint32_t gid = it - rq * ngroups;
+      const uint32_t hh = fdiv(gid, g.div_nl);
+      const uint32_t col = gid - hh * nl;
+      const uint32_t gb = hh * a * nl + col;                 // tile position of member 0
+      const uint32_t gc = (h0 + hh) * s + l0 + col;          // group index h*s + l
+      const uint32_t ib = base + hh * a * s + col;           // global index of member 0
+      const PT Q = s_P[gb + (a - 1) * nl];
+      const uint32_t r0 = rq << 2;
+      const uint32_t pi0 = gc * a + r0;
+      uint32_t rw[4] = {0u, 0u, 0u, 0u};
+      unsigned long long rw64[4] = {0ull, 0ull, 0ull, 0ull};
+      float z[4 * D];
+      if (a4) {   // pi0 % 4 == 0: whole counter blocks
+        if (WIDE && wide_digit) {
+          const uint4 w0 = philox4x32_10(make_uint4(pi0 >> 1, n, kPurposeResampleWide, 0), rk);
+          const uint4 w1 = philox4x32_10(make_uint4((pi0 >> 1) + 1, n, kPurposeResampleWide, 0), rk);
+          rw64[0] = ((unsigned long long)w0.y << 32) | w0.x;
+          rw64[1] = ((unsigned long long)w0.w << 32) | w0.z;
+          rw64[2] = ((unsigned long long)w1.y << 32) | w1.x;
+          rw64[3] = ((unsigned long long)w1.w << 32) | w1.z;
+        } else {
+          const uint4 w = philox4x32_10(make_uint4(pi0 >> 2, n, kPurposeResample, 0), rk);
+          rw[0] = w.x; rw[1] = w.y; rw[2] = w.z; rw[3] = w.w;
+        }
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
+          normals4(w, z + 4 * b);
+        }
+      } else {    // members straddle counter blocks: one block per draw / normal
+#pragma unroll
+        for (int jj = 0; jj < 4; ++jj) {
+          const uint32_t pi = pi0 + jj;
+          if (r0 + jj >= a) break;
+          if (WIDE && wide_digit) {
+            const uint4 w = philox4x32_10(make_uint4(pi >> 1, n, kPurposeResampleWide, 0), rk);
+            rw64[jj] = (pi & 1u) ? (((unsigned long long)w.w << 32) | w.z) : (((unsigned long long)w.y << 32) | w.x);
+          } else {
+            const uint4 w = philox4x32_10(make_uint4(pi >> 2, n, kPurposeResample, 0), rk);
+            const uint32_t sel = pi & 3u;
+            rw[jj] = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
+          }
+#pragma unroll
+          for (int t = 0; t < D; ++t) {
+            const uint32_t nu = pi * D + t;
+            const uint4 w = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), rk);
+            float zz[4];
+            normals4(w, zz);
+            z[jj * D + t] = zz[nu & 3u];
+          }
+        }
+      }
+#pragma unroll
+      for (int jj = 0; jj < 4; ++jj) {
+        const uint32_t r = r0 + jj;
+        if (r >= a) break;
+        PT u;
+        if (WIDE && wide_digit) u = (PT)mulhi64(rw64[jj], (unsigned long long)Q);
+        else u = (PT)(((unsigned long long)rw[jj] * Q) >> 32);
+        uint32_t c = 0;
+        for (uint32_t stp = step0; stp; stp >>= 1) {
+          const uint32_t cand = c + stp;
+          if (cand <= a - 1 && s_P[gb + (cand - 1) * nl] <= u) c = cand;
+        }
+        if (Q == 0) c = r;
+        const uint32_t pa = gb + c * nl;
+        float xh[D], xo[D];
+#pragma unroll
+        for (int t = 0; t < D; ++t) xh[t] = s_x[t * cap + pa];
+        mutate<D, KIND>(mp, xh, z + jj * D, xo);
+        const uint32_t i = ib + r * s;
+#pragma unroll
+        for (int t = 0; t < D; ++t) __stcs(X + (size_t)t * N + i, xo[t]);
+        if (ctx.anc) ctx.anc[i] = (int32_t)(ib + c * s);
+      }
+    }
+  }
+
+}
+
+}  // namespace bfpf
