@@ -50,6 +50,9 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-global", action="store_true", help="skip the global-resampling comparator legs")
     p.add_argument("--global-steps", type=int, default=200)
+    p.add_argument("--no-batched", action="store_true", help="skip the batched-filters leg")
+    p.add_argument("--batched-filters", type=int, default=4096)
+    p.add_argument("--batched-steps", type=int, default=500)
     p.add_argument("--oracle-rate", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--oracle-n", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--oracle-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
@@ -253,6 +256,40 @@ def _timed_flushed_steps(bf, filt, y_dev, K, W, flush, stream, dev):
     return [s_.elapsed_time(e_) for s_, e_ in zip(starts, ends)]
 
 
+def batched_leg(bf, dev, F=4096, T=500):
+    """4096 independent linear-Gaussian filters (d in {1,4,8}, N = 2^U(8,16), random
+    radix factorisations, own seeds), T steps through pf_batch_run with device
+    observations and device outputs; particle-steps/s over the whole batch and the
+    HBM bytes the steps must move."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    specs = S.batched_specs(F, T=T)
+    y = torch.tensor(S.simulate_batch(specs, T), dtype=torch.float32, device=dev)
+    b = bf.FilterBatch([(w.model, w.N, w.radices, w.filter_seed) for w in specs], device=dev)
+    b.run(y[:, :8])                         # graph capture, first touch
+    torch.cuda.synchronize(dev)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(b.stream)
+    r = b.run(y[:, 8:])
+    e1.record(b.stream)
+    torch.cuda.synchronize(dev)
+    ms = e0.elapsed_time(e1)
+    steps = T - 8
+    ps = sum(w.N for w in specs) * steps
+    nbytes = 0
+    for w in specs:
+        m = len(w.radices)
+        for n in range(8, T):
+            nbytes += algorithmic_bytes(w, n)
+    ok = bool(torch.isfinite(r["inc"]).all().item())
+    b.close()
+    return {"filters": F, "steps": steps, "particle_steps_per_s": ps / (ms * 1e-3), "ms_per_step": ms / steps,
+            "hbm_gbs_algorithmic": nbytes / (ms * 1e-3) / 1e9, "total_particles": sum(w.N for w in specs),
+            "d": "uniform over {1,4,8}", "N": "2^round(U(8,16))", "outputs_finite": ok,
+            "launches_per_step": 1}
+
+
 def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
     """Filter-mean MSE (Section 6.1: sum over steps and components, mean over runs)
     against the number of particles, for the butterfly (radix 16) and the global-
@@ -412,6 +449,9 @@ def ours_main(a):
     eq = None
     if not a.no_global and rank == 0 and w.model.kind == "sv" and w.N == (1 << 24):
         eq = equal_error_leg(bf, w, dev)
+    batched = None
+    if not a.no_batched and rank == 0:
+        batched = batched_leg(bf, dev, a.batched_filters, a.batched_steps)
 
     if world > 1:
         t = torch.tensor([total_ms, e2e_s, resident_ms], device=dev, dtype=torch.float64)
@@ -462,6 +502,7 @@ def ours_main(a):
         "clocks": clk,
         "global_resampling": glob,
         "equal_error": eq,
+        "batched": batched,
     }
     print(json.dumps(line))
     filt.close()

@@ -100,6 +100,17 @@ pf_status fail(const pf_handle* h, pf_status s, const std::string& msg) {
       return fail((h), PF_ECUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// True if p is host memory (outputs written there need the stream synchronised).
+bool is_host_ptr(const void* p) {
+  if (!p) return false;
+  cudaPointerAttributes attr;
+  if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) {
+    cudaGetLastError();
+    return true;
+  }
+  return attr.type == cudaMemoryTypeHost || attr.type == cudaMemoryTypeUnregistered;
+}
+
 bool is_lower_triangular(const double* M, int n) {
   for (int i = 0; i < n; ++i)
     for (int j = i + 1; j < n; ++j)
@@ -630,7 +641,7 @@ pf_status pf_advance(pf_handle* h, int32_t T, float* means, double* loglik_incs,
     done += L;
   }
   PF_CUDA(h, cudaGetLastError());
-  if (means || loglik_incs || ess) PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  if (is_host_ptr(means) || is_host_ptr(loglik_incs) || is_host_ptr(ess)) PF_CUDA(h, cudaStreamSynchronize(h->stream));
   return PF_OK;
 }
 

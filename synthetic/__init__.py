@@ -29,7 +29,7 @@ import numpy as np
 __all__ = [
     "LinearGaussian", "StochVol", "Workload",
     "simulate", "lg_scalar", "lg_dense", "sv_model", "random_walk",
-    "workload", "WORKLOADS", "batched_specs", "serving_stream",
+    "workload", "WORKLOADS", "batched_specs", "simulate_batch", "serving_stream",
 ]
 
 
@@ -208,6 +208,37 @@ def batched_specs(n_filters: int = 4096, T: int = 500, seed: int = 4,
         specs.append(Workload(f"batch{f}", model, N, radices, T,
                               data_seed=seed * 7919 + f, filter_seed=seed * 104729 + f))
     return specs
+
+
+def simulate_batch(specs, T: int) -> np.ndarray:
+    """Observations of many linear-Gaussian workloads at once, vectorised over the
+    filters of equal dimension: returns y of shape (F, T, dy_max), zero padded.
+    Each filter's series uses its own data seed (numpy PCG64), so it differs from
+    ``simulate(model, T, seed)`` draw by draw but has the same law."""
+    F = len(specs)
+    dy_max = max(w.model.dy for w in specs)
+    y = np.zeros((F, T, dy_max))
+    by_d = {}
+    for f, w in enumerate(specs):
+        if w.model.kind != "lg":
+            y[f, :, :1] = simulate(w.model, T, w.data_seed)[1]
+            continue
+        by_d.setdefault((w.model.d, w.model.dy), []).append(f)
+    for (d, dy), idx in by_d.items():
+        A = np.stack([specs[f].model.A for f in idx])
+        Lq = np.stack([specs[f].model.Lq for f in idx])
+        H = np.stack([specs[f].model.H for f in idx])
+        Lr = np.stack([specs[f].model.Lr for f in idx])
+        m0 = np.stack([specs[f].model.m0 for f in idx])
+        L0 = np.stack([specs[f].model.L0 for f in idx])
+        gens = [np.random.default_rng(specs[f].data_seed) for f in idx]
+        eps = np.stack([g.standard_normal((T, d + dy)) for g in gens])       # (Fd, T, d + dy)
+        x = m0 + np.einsum("fij,fj->fi", L0, eps[:, 0, :d])
+        for n in range(T):
+            if n > 0:
+                x = np.einsum("fij,fj->fi", A, x) + np.einsum("fij,fj->fi", Lq, eps[:, n, :d])
+            y[idx, n, :dy] = np.einsum("fij,fj->fi", H, x) + np.einsum("fij,fj->fi", Lr, eps[:, n, d:])
+    return y
 
 
 def serving_stream(n_requests: int, rate_hz: float, seed: int = 5,

@@ -1,0 +1,62 @@
+"""Serving loop: continuous batching with memory admission; every request's
+result is the same alone and in the mix."""
+import numpy as np
+import pytest
+
+import synthetic as S
+
+pytestmark = pytest.mark.gpu
+
+
+def _requests(serve, n=12, seed=11):
+    rng = np.random.default_rng(seed)
+    reqs = []
+    for r in range(n):
+        kind = r % 4
+        model = [S.lg_scalar(), S.lg_dense(4, seed=r), S.lg_dense(8, seed=r), S.sv_model()][kind]
+        N = int(2 ** rng.integers(10, 15))
+        radices = (16,) * (int(np.log2(N)) // 4) + ((2 ** (int(np.log2(N)) % 4),) if np.log2(N) % 4 else ())
+        T = int(rng.integers(100, 260))
+        y = S.simulate(model, T, seed=500 + r)[1]
+        reqs.append(serve.Request(rid=r, arrival=0.002 * r, model=model, N=N, radices=radices,
+                                  seed=7000 + r, y=y))
+    return reqs
+
+
+def test_results_same_alone_and_in_the_mix(bfpf):
+    from paper_1812_01502_gb300 import serve
+    mix = _requests(serve)
+    srv = serve.Server(memory_budget=8 << 30, slots=6)
+    done = {r.rid: r for r in srv.run(mix)}
+    assert len(done) == len(mix)
+    assert srv.max_active > 1                        # requests overlapped on the device
+    for rid in (0, 3, 7, 10):
+        alone = _requests(serve)[rid]
+        alone.arrival = 0.0
+        one = serve.Server(memory_budget=8 << 30, slots=1).run([alone])[0]
+        assert np.array_equal(one.means, done[rid].means)
+        assert np.array_equal(one.incs, done[rid].incs)
+        assert one.loglik == done[rid].loglik
+    s = serve.summarize(list(done.values()), srv.wall)
+    print("serving", s)
+    assert s["p99_latency_s"] >= s["p50_latency_s"] > 0
+
+
+def test_memory_admission_limits_concurrency(bfpf):
+    from paper_1812_01502_gb300 import serve
+    reqs = _requests(serve, n=8, seed=3)
+    need = max(serve.workspace_bytes(r.model, r.N, r.radices) for r in reqs)
+    budget = 2 * need + 1
+    srv = serve.Server(memory_budget=budget, slots=8)
+    done = srv.run(reqs)
+    assert len(done) == len(reqs)
+    assert srv.max_in_use <= budget              # admission never exceeded the budget
+    assert srv.max_active < len(reqs)            # so some requests had to wait
+    assert all(np.all(np.isfinite(r.incs)) for r in done)
+
+
+def test_request_larger_than_budget_is_refused(bfpf):
+    from paper_1812_01502_gb300 import serve
+    req = _requests(serve, n=1)[0]
+    with pytest.raises(MemoryError):
+        serve.Server(memory_budget=1024, slots=2).run([req])
