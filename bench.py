@@ -53,6 +53,9 @@ def _args():
     p.add_argument("--no-batched", action="store_true", help="skip the batched-filters leg")
     p.add_argument("--batched-filters", type=int, default=4096)
     p.add_argument("--batched-steps", type=int, default=500)
+    p.add_argument("--no-serving", action="store_true", help="skip the serving leg")
+    p.add_argument("--serving-requests", type=int, default=160)
+    p.add_argument("--serving-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
     p.add_argument("--oracle-rate", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--oracle-n", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--oracle-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
@@ -290,6 +293,21 @@ def batched_leg(bf, dev, F=4096, T=500):
             "launches_per_step": 1}
 
 
+def serving_leg(dev, n_requests=160, rate=40.0):
+    """Poisson arrivals of filtering requests (LG d in {1,4,8} or SV; N = 2^U{10..20};
+    T = U(100, 2000); observations in chunks of 50) served with memory admission and
+    continuous batching; p50/p99 request latency beside throughput."""
+    import synthetic as S
+    from paper_1812_01502_gb300 import serve
+    reqs = serve.requests_from_stream(S.serving_stream(n_requests, rate_hz=rate), chunk=50)
+    srv = serve.Server(memory_budget=24 << 30, slots=32, device=dev)
+    done = srv.run(reqs)
+    out = serve.summarize(done, srv.wall)
+    out.update({"arrival_rate_hz": rate, "slots": 32, "memory_budget_gb": 24, "chunk": 50,
+                "max_concurrent": srv.max_active})
+    return out
+
+
 def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
     """Filter-mean MSE (Section 6.1: sum over steps and components, mean over runs)
     against the number of particles, for the butterfly (radix 16) and the global-
@@ -452,6 +470,9 @@ def ours_main(a):
     batched = None
     if not a.no_batched and rank == 0:
         batched = batched_leg(bf, dev, a.batched_filters, a.batched_steps)
+    serving = None
+    if not a.no_serving and rank == 0:
+        serving = serving_leg(dev, a.serving_requests, a.serving_rate)
 
     if world > 1:
         t = torch.tensor([total_ms, e2e_s, resident_ms], device=dev, dtype=torch.float64)
@@ -503,6 +524,7 @@ def ours_main(a):
         "global_resampling": glob,
         "equal_error": eq,
         "batched": batched,
+        "serving": serving,
     }
     print(json.dumps(line))
     filt.close()
