@@ -152,11 +152,15 @@ class ButterflyFilter:
 
     def __init__(self, model, N: int, radices: Sequence[int], seed: int, *, tile: int = 0,
                  chunk_len: int = 0, record_ancestors: bool = False, grid: int = 0,
-                 device=None, stream=None):
+                 device=None, stream=None, tune: bool = False):
         torch = _torch()
         lib = load_library()
         if not torch.cuda.is_available():
             raise PFError(PF_ECUDA, "no CUDA device: the butterfly filter runs only on the GPU")
+        if tune:    # launch configuration from the autotuner (cached per device and problem)
+            from . import autotune
+            best = autotune.tune(model, int(N), tuple(radices), device=device)
+            tile, grid = int(best["tile"]), int(best["grid"])
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.model = model
