@@ -120,6 +120,60 @@ def summaries(lw: np.ndarray, x: np.ndarray, c_n: float, mu_sub: float, mu: floa
     return inc, mean, ess, lme
 
 
+def stage(radices: Sequence[int], seed: int, x: np.ndarray, lw: np.ndarray, k: int, t: int):
+    """One stage of Algorithm 3 on digit k with log-weights lw (V_{s-1} g, in logs):
+    new stage weights V_s = A_k V_{s-1} (eq. (V_defn_proofs)) and the draws
+    xi_s^i ~ (V_s^i)^{-1} sum_j A_k^{ij} V_{s-1}^j delta_{xi_{s-1}^j} (integer rule),
+    keyed by the stage counter t.  Returns (x gathered, lV_new, ancestors, q, u, pi)."""
+    N = x.shape[0]
+    a = radices[k]
+    s_k = strides(radices)[k]
+    Hh = N // (a * s_k)
+    lwg = lw.reshape(Hh, a, s_k)
+    Mg = np.max(lwg, axis=1, keepdims=True)
+    with np.errstate(invalid="ignore"):
+        Lg = Mg + np.log(np.sum(np.exp(lwg - Mg), axis=1, keepdims=True))
+    lV_new = np.broadcast_to(Lg - np.log(a), lwg.shape).reshape(N).copy()
+    q = resample.quantise(lwg, axis=1)
+    Q = np.sum(q, axis=1, keepdims=True, dtype=np.uint64)
+    pi = group_major(N, radices, k)            # counter numbering of the draws at this stage
+    if a <= resample.NARROW_MAX_RADIX:
+        r = philox.resample_words_at(seed, t, pi).reshape(Hh, a, s_k)
+        u = resample.scaled_uniform(r, Q, a)
+    else:
+        lo, hi = philox.resample_words_wide_at(seed, t, pi)
+        u = resample.scaled_uniform(lo.reshape(Hh, a, s_k), Q, a, hi.reshape(Hh, a, s_k))
+    member = resample.draw(q, u, axis=1)
+    h_idx = np.arange(Hh)[:, None, None]
+    l_idx = np.arange(s_k)[None, None, :]
+    anc = (h_idx * (a * s_k) + member * s_k + l_idx).reshape(N)
+    return x[anc], lV_new, anc, q.reshape(N), u.reshape(N), pi
+
+
+def step_all_stages(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
+                    mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
+    """One time step with the paper's schedule: Algorithm 1 whose Resample is the
+    whole of Algorithm 3 - g_n weights stage 1 (V_0 = g), then all S = m stages
+    s = 1..S on digits 0..m-1 in turn, then the mutation (Section 3).  Stage s of
+    time step n draws with counter t = n m + s - 1; the mutation uses time n.
+    By Lemma 3(c) the weights after the last stage are all equal."""
+    radices = [int(a) for a in radices]
+    m = len(radices)
+    n = st.n
+    mu_sub = st.mu if mu_used is None else float(mu_used)
+    lw, c_n = weigh(model, st.x, st.lV, mu_sub, y_n)
+    inc, mean, ess, lme = summaries(lw, st.x, c_n, mu_sub, st.mu)
+    x = st.x
+    stages = []
+    for k in range(m):
+        x, lV_new, anc, q, u, pi = stage(radices, seed, x, lw, k, n * m + k)
+        stages.append(dict(k=k, anc=anc, q=q, u=u, lw=lw, lV_new=lV_new))
+        lw = lV_new
+    x_next = mutate(model, x, n, seed, idx=np.arange(st.x.shape[0]))
+    new = State(x=x_next, lV=lw, mu=lme, n=n + 1, loglik=st.loglik + inc)
+    return new, dict(stages=stages, inc=inc, mean=mean, ess=ess, lV_new=lw, c=c_n)
+
+
 def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
          mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
     """One time step n = st.n: weight, one augmented-resampling stage, mutate.
@@ -174,8 +228,9 @@ def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
 
 
 def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
-        keep_ancestors: bool = False) -> Dict[str, np.ndarray]:
-    """Run the filter over y[0:T].  Returns per-step inc, mean, ess and the final loglik."""
+        keep_ancestors: bool = False, all_stages: bool = False) -> Dict[str, np.ndarray]:
+    """Run the filter over y[0:T].  Returns per-step inc, mean, ess and the final loglik.
+    all_stages: the paper's schedule (all m stages per time step) instead of one digit."""
     if int(np.prod(radices)) != N:
         raise ValueError("product of radices must equal N")
     y = np.asarray(y, dtype=np.float64).reshape(len(y), -1)
@@ -186,9 +241,9 @@ def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
     ess = np.empty(T)
     ancs = [] if keep_ancestors else None
     for t in range(T):
-        st, o = step(model, radices, seed, st, y[t])
+        st, o = (step_all_stages if all_stages else step)(model, radices, seed, st, y[t])
         incs[t], means[t], ess[t] = o["inc"], o["mean"], o["ess"]
-        if keep_ancestors:
+        if keep_ancestors and not all_stages:
             ancs.append(o["anc"])
     out = dict(inc=incs, mean=means, ess=ess, loglik=st.loglik, state=st)
     if keep_ancestors:

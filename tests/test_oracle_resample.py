@@ -209,3 +209,28 @@ def test_step_on_groups_equals_full_step(radices, n):
     np.testing.assert_allclose(g["x_next"].reshape(-1, 3), new.x[flat], rtol=1e-13, atol=1e-13)
     lv_c = o["lV_new"].reshape(H, a, s_k)[:, 0, :].reshape(-1)
     np.testing.assert_allclose(g["lV_new"], lv_c[groups[:, 0] * s_k + groups[:, 1]], rtol=1e-13)
+
+
+@pytest.mark.parametrize("radices", [(2, 2, 2), (4, 8), (3, 5, 2)])
+def test_all_stages_schedule_lemma3_and_textbook_increment(radices):
+    """The paper's schedule (all stages of Algorithm 3 per time step): after each
+    step the carried weights are all equal (Lemma 3(c)), and the likelihood
+    increment equals the textbook BPF's log N^-1 sum_i g_n(zeta_i) on the same
+    particles (since V_S = N^-1 sum g)."""
+    N = int(np.prod(radices))
+    model = S.lg_scalar()
+    y = S.simulate(model, 6, seed=13)[1]
+    st = bpf.init_state(model, N, seed=21)
+    for n in range(6):
+        s_x, c = bpf.obs_terms(model, st.x, y[n])
+        mx = s_x.max()
+        textbook = mx + np.log(np.mean(np.exp(s_x - mx))) + c
+        st, o = bpf.step_all_stages(model, radices, 21, st, y[n])
+        np.testing.assert_allclose(st.lV, st.lV[0], rtol=0, atol=1e-12)
+        assert abs(o["inc"] - textbook) < 1e-10
+        # every stage moves particles only inside their digit-k groups
+        for sg in o["stages"]:
+            k = sg["k"]
+            a, s = radices[k], butterfly.strides(radices)[k]
+            idx = np.arange(N)
+            assert np.array_equal(sg["anc"] // (a * s), idx // (a * s)) and np.array_equal(sg["anc"] % s, idx % s)
