@@ -82,11 +82,20 @@ typedef struct {
 
 /* pf_options.flags */
 #define PF_RECORD_ANCESTORS 1u   /* keep the ancestor index of every particle of the last step */
+/* Run every stage of Algorithm 3 in each time step (Algorithm 1 whose
+ * Resample is the whole of Algorithm 3, Section 3): step n weights with
+ * g_n, then resamples on digits 0, 1, ..., m-1 in turn with stage weights
+ * V_s = A_s V_{s-1} (Section 3, eq. (V_defn_proofs)), then mutates.  After the
+ * last stage every carried weight is equal (Lemma 3(c)).  Without the flag
+ * each step runs the one stage on digit n mod m (the default, cheapest
+ * schedule).  Costs m kernel launches per time step.  Cannot be combined
+ * with PF_RECORD_ANCESTORS (EINVAL).  Ignored when m = 1. */
+#define PF_ALL_STAGES 2u
 
 typedef struct {
     int32_t tile;        /* target particles per thread-block tile; 0 = automatic            */
     int32_t chunk_len;   /* time steps per CUDA-graph replay in pf_run; 0 = 64 (max 1024)    */
-    uint32_t flags;      /* PF_RECORD_ANCESTORS                                              */
+    uint32_t flags;      /* PF_RECORD_ANCESTORS | PF_ALL_STAGES                              */
     int32_t grid;        /* persistent thread blocks; 0 = automatic (SMs x occupancy)        */
     void* stream;        /* cudaStream_t to run on; NULL = the legacy default stream          */
 } pf_options;

@@ -169,7 +169,9 @@ def step_all_stages(model, radices: Sequence[int], seed: int, st: State, y_n: np
         x, lV_new, anc, q, u, pi = stage(radices, seed, x, lw, k, n * m + k)
         stages.append(dict(k=k, anc=anc, q=q, u=u, lw=lw, lV_new=lV_new))
         lw = lV_new
-    x_next = mutate(model, x, n, seed, idx=np.arange(st.x.shape[0]))
+    # the mutation's normals are numbered like the draws of the stage that mutates
+    # (group-major on digit m-1), as in the one-digit step
+    x_next = mutate(model, x, n, seed, idx=pi)
     new = State(x=x_next, lV=lw, mu=lme, n=n + 1, loglik=st.loglik + inc)
     return new, dict(stages=stages, inc=inc, mean=mean, ess=ess, lV_new=lw, c=c_n)
 

@@ -29,6 +29,7 @@ PF_OK, PF_EINVAL, PF_ENOMEM, PF_ECUDA, PF_ETIMEOUT, PF_ESTATE = range(6)
 PF_MODEL_LINEAR_GAUSSIAN = 1
 PF_MODEL_STOCH_VOL = 2
 PF_RECORD_ANCESTORS = 1
+PF_ALL_STAGES = 2
 STATUS_NAMES = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",
                 PF_ETIMEOUT: "PF_ETIMEOUT", PF_ESTATE: "PF_ESTATE"}
 
@@ -145,6 +146,8 @@ def _cuda_ptr(t):
 class ButterflyFilter:
     """A filter handle: N = prod(radices) particles, digit k = n mod m interacts at step n.
 
+    all_stages=True runs every stage of Algorithm 3 in each step instead
+    (digits 0..m-1 in turn; m launches per step).
     radices = (N,) is the global-resampling bootstrap filter (Algorithm 1 + 2).
     The workspace is a torch uint8 tensor on ``device``; work runs on the
     current torch stream of that device unless ``stream`` is given.
@@ -152,7 +155,7 @@ class ButterflyFilter:
 
     def __init__(self, model, N: int, radices: Sequence[int], seed: int, *, tile: int = 0,
                  chunk_len: int = 0, record_ancestors: bool = False, grid: int = 0,
-                 device=None, stream=None, tune: bool = False):
+                 device=None, stream=None, tune: bool = False, all_stages: bool = False):
         torch = _torch()
         lib = load_library()
         if not torch.cuda.is_available():
@@ -172,9 +175,11 @@ class ButterflyFilter:
         self.d, self.dy = self._pm.d, self._pm.dy
         self._rad = (ctypes.c_int32 * self.m)(*self.radices)
         self._opts = PFOptions(tile=int(tile), chunk_len=int(chunk_len),
-                               flags=PF_RECORD_ANCESTORS if record_ancestors else 0, grid=int(grid),
+                               flags=(PF_RECORD_ANCESTORS if record_ancestors else 0)
+                               | (PF_ALL_STAGES if all_stages else 0), grid=int(grid),
                                stream=ctypes.c_void_p(self.stream.cuda_stream))
         self.record_ancestors = record_ancestors
+        self.all_stages = bool(all_stages)
         with torch.cuda.device(self.device):
             nbytes = ctypes.c_size_t(0)
             _check(lib.pf_workspace_size(ctypes.byref(self._pm), self.N, self._rad, self.m,
@@ -278,7 +283,8 @@ class ButterflyFilter:
 
     def state(self):
         """(x (N, d) float32, lV (N / a_prev,) float32, dict(n, loglik, mu, mu_used))."""
-        kp = (self.steps - 1) % self.m
+        t = self.steps * (self.m if self.all_stages else 1)    # stages run so far
+        kp = (t - 1) % self.m
         x = np.empty((self.d, self.N), dtype=np.float32)
         lv = np.empty(self.N // self.radices[kp], dtype=np.float32)
         sc = np.empty(4, dtype=np.float64)

@@ -74,6 +74,9 @@ __device__ __forceinline__ void batch_filter_step(const BatchParams& bp, BatchFi
   TileCtx ctx;
   const uint32_t k = n % f.m;
   ctx.n = n;
+  ctx.t = n;          // one stage per time step
+  ctx.obs = true;
+  ctx.mut = true;
   ctx.x = f.x;
   ctx.lV_in = f.lV[n & 1u];
   ctx.lV_out = f.lV[(n & 1u) ^ 1u];

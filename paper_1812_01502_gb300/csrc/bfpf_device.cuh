@@ -233,12 +233,13 @@ struct DevState {
   float gmax;          // global resampling: maximum log-weight of the step
   uint32_t done2;      // global resampling: blocks finished with the draw kernel
   unsigned long long ticket;   // global resampling: scan tiles handed out so far
+  uint32_t stage;      // next stage of time step n (0 unless every stage runs in each step)
 };
 
 struct StepParams {
   RoundKeys rk;        // Philox round keys of the seed
   float* x;            // [d][N] particle states (updated in place)
-  float* lV[2];        // carried log stage weights, ping-pong by time-step parity
+  float* lV[2];        // carried log stage weights, ping-pong by stage-counter parity
   int32_t* anc;        // [N] ancestors of the last step (nullptr = not recorded)
   DevState* st;
   float* partials;     // [grid][3 + d] per-block partial sums
@@ -251,9 +252,35 @@ struct StepParams {
   uint32_t seed_lo, seed_hi;
   uint32_t tile_cap;   // shared-memory tile capacity (particles)
   float inv_N;
+  uint32_t sps;        // resampling stages per time step: 1 (one digit per step) or m (all of them)
   ModelParams model;
   DigitGeom geom[kMaxDigits];
 };
+
+// Where one launch sits in the stage schedule.  The stage counter t counts
+// every resampling stage run so far; stage t works on digit k = t mod m.
+// With one stage per step (sps = 1) t = n and each launch is a whole step.
+// With all m stages per step (Algorithm 1 whose Resample is all of Algorithm
+// 3, sps = m) step n runs stages t = n m .. n m + m - 1: only the first
+// multiplies the observation weight g_n in (V_0 = g), only the last mutates.
+struct Sched {
+  uint32_t n;     // time index (observation, mutation counters, output slot)
+  uint32_t t;     // stage counter (resampling counters, carried-weight parity)
+  uint32_t k;     // digit of this stage
+  bool obs;       // weight with g_n and produce the step's summaries
+  bool mut;       // mutate after resampling (last stage of the step)
+};
+
+__device__ __forceinline__ Sched sched_of(const StepParams& p, const DevState* st) {
+  Sched sc;
+  sc.n = st->n;
+  const uint32_t stage = st->stage;
+  sc.t = sc.n * p.sps + stage;
+  sc.k = sc.t % (uint32_t)p.m;
+  sc.obs = stage == 0;
+  sc.mut = stage + 1 == p.sps;
+  return sc;
+}
 
 // Buffers of the global-resampling path (m = 1, N > kMaxCtaRadix).
 struct GlobalParams {

@@ -10,6 +10,8 @@
 //   filter mean           sum_i e^{lw_i} x_i / sum_i e^{lw_i}
 //   ESS (Section 1.2)     (sum e^{lw})^2 / (N sum e^{2 lw})
 // and advances the device state (n, mu, cumulative FP64 log-likelihood).
+// A stage that does not weight with an observation (all-stages schedule,
+// stages after the first) writes no summaries and only moves the stage on.
 #pragma once
 
 #include "bfpf_device.cuh"
@@ -58,8 +60,9 @@ __device__ __forceinline__ void shfl_merge(Partial& acc, float* accx, int off) {
 // kernel): the last block leaves n alone and instead writes the global
 // maximum log-weight and the single group's new log weight.
 template <int D, bool ADVANCE = true>
-__device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, float* accx, uint32_t n,
+__device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, float* accx, const Sched& sc,
                                             uint32_t status, float muf, float* lv_single_out = nullptr) {
+  const uint32_t n = sc.n;
   constexpr int NP = 3 + D;
   constexpr int NW = kBlock / 32;
   __shared__ float s_red[NW][NP];
@@ -99,6 +102,19 @@ __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, fl
   __syncthreads();
   if (!s_last) return;
   __threadfence();
+  if (!sc.obs) {
+    if (tid == 0) {
+      st->done = 0;
+      __threadfence();
+      if (sc.mut) {
+        st->stage = 0;
+        st->n = n + 1;
+      } else {
+        st->stage = st->stage + 1;
+      }
+    }
+    return;
+  }
 
   // Last block: fold all block partials (fixed order, compensated FP32), finish in FP64.
   const uint32_t G = gridDim.x;
@@ -176,7 +192,12 @@ __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, fl
     st->done = 0;
     if constexpr (ADVANCE) {
       __threadfence();
-      st->n = n + 1;
+      if (sc.mut) {
+        st->stage = 0;
+        st->n = n + 1;
+      } else {
+        st->stage = 1;
+      }
     } else {
       st->gmax = Mx;
       if (lv_single_out) *lv_single_out = (float)lme;   // log of the one group's mean weight

@@ -8,24 +8,27 @@ namespace bfpf {
 
 // Kernel entry points for one (state dimension, model, wide-draw) variant.
 struct KernelSet {
-  const void* step;   // step_butterfly_kernel<D, KIND, WIDE>(StepParams)
-  const void* init;   // init_particles_kernel<D, KIND>(StepParams)
+  const void* step;          // step_butterfly_kernel<D, KIND, WIDE, false>(StepParams)
+  const void* step_staged;   // step_butterfly_kernel<D, KIND, WIDE, true>: all stages per step
+  const void* init;          // init_particles_kernel<D, KIND>(StepParams)
 };
 
 // Picks the compiled variant of the general kernel; false if (d, kind) is not supported.
 bool select_kernels(int d, int kind, bool wide, KernelSet& ks);
+// The general kernel for the all-stages schedule (step_butterfly_staged.cu).
+const void* select_staged_tile_kernel(int d, int kind, bool wide);
 
-// Register-resident group kernel step_group_kernel<d, kind, a, G>(StepParams, GroupGeom)
-// for a power-of-two radix a <= 32; sets *G (lanes per group).  nullptr if none.
-const void* select_group_kernel(int d, int kind, int a, int* G);
-const void* group_kernel_d1(int kind, int a, int* G);
-const void* group_kernel_d2(int kind, int a, int* G);
-const void* group_kernel_d3(int kind, int a, int* G);
-const void* group_kernel_d4(int kind, int a, int* G);
-const void* group_kernel_d5(int kind, int a, int* G);
-const void* group_kernel_d6(int kind, int a, int* G);
-const void* group_kernel_d7(int kind, int a, int* G);
-const void* group_kernel_d8(int kind, int a, int* G);
+// Register-resident group kernel step_group_kernel<d, kind, a, G, staged>(StepParams,
+// GroupGeom) for a power-of-two radix a <= 32; sets *G (lanes per group).  nullptr if none.
+const void* select_group_kernel(int d, int kind, int a, int* G, bool staged);
+const void* group_kernel_d1(int kind, int a, int* G, bool staged);
+const void* group_kernel_d2(int kind, int a, int* G, bool staged);
+const void* group_kernel_d3(int kind, int a, int* G, bool staged);
+const void* group_kernel_d4(int kind, int a, int* G, bool staged);
+const void* group_kernel_d5(int kind, int a, int* G, bool staged);
+const void* group_kernel_d6(int kind, int a, int* G, bool staged);
+const void* group_kernel_d7(int kind, int a, int* G, bool staged);
+const void* group_kernel_d8(int kind, int a, int* G, bool staged);
 
 // Global-resampling comparator (radices = {N}, N > 1024): three kernels per step,
 // each taking (StepParams, GlobalParams).

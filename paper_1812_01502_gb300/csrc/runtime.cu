@@ -54,6 +54,7 @@ struct Plan {
   int grid = 0;
   size_t smem = 0;
   bool record = false;
+  uint32_t sps = 1;           // resampling stages per time step (1, or m with PF_ALL_STAGES)
   int chunk_len = 64;
   KernelSet ks{};
   ModelParams mp{};
@@ -248,6 +249,7 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     g.wide = 1;
     pl.record = opts && (opts->flags & PF_RECORD_ANCESTORS);
     pl.chunk_len = (opts && opts->chunk_len > 0) ? std::min<int>(opts->chunk_len, (int)kRing) : 64;
+    pl.sps = 1;               // one digit: the single stage is the whole of Algorithm 3
     return PF_OK;
   }
   uint32_t target = (opts && opts->tile > 0) ? (uint32_t)opts->tile : (d == 1 ? 4096u : d <= 4 ? 2048u : 1024u);
@@ -289,6 +291,12 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     g.div_prev_s = make_fastdiv(pl.geom[kp].s);
   }
   for (int k = 0; k < m; ++k) pl.geom[k].div_tgroups = make_fastdiv(pl.geom[k].nh * pl.geom[k].nl);
+  pl.sps = (opts && (opts->flags & PF_ALL_STAGES)) ? (uint32_t)m : 1u;
+  if (pl.sps > 1 && opts && (opts->flags & PF_RECORD_ANCESTORS)) {
+    msg = "PF_RECORD_ANCESTORS records one stage; it cannot be combined with PF_ALL_STAGES";
+    return PF_EINVAL;
+  }
+  const bool staged = pl.sps > 1;
   // Register-resident group kernel: every radix a power of two, a_k <= 32, and the
   // groups of digit k fill whole thread-block iterations.
   bool pow2 = true;
@@ -297,7 +305,7 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     DigitPlan& dp = pl.dp[k];
     const DigitGeom& g = pl.geom[k];
     int G = 0;
-    const void* gk = (pow2 && g.a <= 32) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G) : nullptr;
+    const void* gk = (pow2 && g.a <= 32) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged) : nullptr;
     if (gk && G > 0) {
       const uint32_t gpb = kBlock / G;
       const uint32_t ngroups = pl.N / g.a;
@@ -376,9 +384,10 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess && pl.global) return finish_plan_global(pl, opts, sms, msg);
+  const void* tile_kernel = pl.sps > 1 ? pl.ks.step_staged : pl.ks.step;
   if (e == cudaSuccess)   // opt in beyond the 48 KB default whatever the size
-    e = cudaFuncSetAttribute(pl.ks.step, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, pl.ks.step, kBlock, pl.smem);
+    e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tile_kernel, kBlock, pl.smem);
   if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
   if (nb < 1) { msg = "tile does not fit in shared memory; choose a smaller tile"; return PF_EINVAL; }
   pl.max_grid = 0;
@@ -390,7 +399,7 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
       if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
       units = (int)dp.gg.nbatch;
     } else {
-      dp.kernel = pl.ks.step;
+      dp.kernel = tile_kernel;
       dp.smem = pl.smem;
       per_sm = nb;
       units = (int)pl.geom[k].ntiles;
@@ -418,8 +427,8 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   return PF_OK;
 }
 
-// Launch the step kernel(s) for time step n (digit n mod m).
-cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t n) {
+// Launch the kernel(s) of stage t of the schedule (digit t mod m).
+cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
   if (h->plan.global) {
     void* args[] = {&h->P, &h->GP};
     cudaError_t e = cudaLaunchKernel(h->plan.gk.weight, dim3(h->plan.grid_weight), dim3(kBlock), args, 0, stream);
@@ -427,7 +436,7 @@ cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t n) {
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.draw, dim3(h->plan.grid_draw), dim3(kBlock), args, 0, stream);
     return e;
   }
-  DigitPlan& dp = h->plan.dp[n % (uint64_t)h->plan.m];
+  DigitPlan& dp = h->plan.dp[t % (uint64_t)h->plan.m];
   if (dp.group) {
     void* args[] = {&h->P, &dp.gg};
     return cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, 0, stream);
@@ -513,6 +522,7 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   P.rk = make_round_keys(seed);
   P.tile_cap = pl.cap;
   P.inv_N = (float)(1.0 / pl.N);
+  P.sps = pl.sps;
   P.model = pl.mp;
   std::memcpy(P.geom, pl.geom, sizeof(P.geom));
   if (pl.global) {
@@ -585,20 +595,22 @@ pf_status pf_push_observations(pf_handle* h, const float* y, int32_t T) {
 
 namespace {
 
-// L steps on pushed observations, starting at step h->n_host: a captured graph
-// (one per radix phase n mod m, since the kernel depends on the digit) when L
-// is the chunk length, else individual launches.
+// L steps on pushed observations, starting at step h->n_host (L * sps stage
+// launches, from stage counter t0 = n_host * sps): a captured graph (one per
+// radix phase t0 mod m, since the kernel depends on the digit) when L is the
+// chunk length, else individual launches.
 pf_status enqueue_steps(pf_handle* h, int32_t L) {
   const Plan& pl = h->plan;
-  const uint64_t n0 = h->n_host;
+  const uint64_t t0 = h->n_host * pl.sps;
+  const int64_t launches = (int64_t)L * pl.sps;
   if (L == pl.chunk_len && L > 1) {
     if (h->graphs.empty()) h->graphs.assign(pl.m, nullptr);
-    cudaGraphExec_t& exec = h->graphs[n0 % (uint64_t)pl.m];
+    cudaGraphExec_t& exec = h->graphs[t0 % (uint64_t)pl.m];
     if (!exec) {
       cudaGraph_t graph = nullptr;
       PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
       cudaError_t le = cudaSuccess;
-      for (int j = 0; j < L && le == cudaSuccess; ++j) le = launch_step(h, h->cap_stream, n0 + j);
+      for (int64_t j = 0; j < launches && le == cudaSuccess; ++j) le = launch_step(h, h->cap_stream, t0 + j);
       cudaError_t ce = cudaStreamEndCapture(h->cap_stream, &graph);
       if (le != cudaSuccess) return fail(h, PF_ECUDA, std::string("capture launch: ") + cudaGetErrorString(le));
       if (ce != cudaSuccess) return fail(h, PF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
@@ -611,7 +623,7 @@ pf_status enqueue_steps(pf_handle* h, int32_t L) {
     }
     PF_CUDA(h, cudaGraphLaunch(exec, h->stream));
   } else {
-    for (int j = 0; j < L; ++j) PF_CUDA(h, launch_step(h, h->stream, n0 + j));
+    for (int64_t j = 0; j < launches; ++j) PF_CUDA(h, launch_step(h, h->stream, t0 + j));
   }
   return PF_OK;
 }
@@ -682,10 +694,10 @@ pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars)
   if (x) PF_CUDA(h, cudaMemcpyAsync(x, xcur, (size_t)4 * pl.d * pl.N, cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   if (lV) {
-    const uint32_t n = st.n;
-    const int kp = (int)((n + pl.m - 1) % pl.m);
+    const uint64_t t = (uint64_t)st.n * pl.sps + st.stage;   // stage counter
+    const int kp = (int)((t + pl.m - 1) % pl.m);
     const size_t cnt = pl.global ? 1 : pl.N / pl.geom[kp].a;
-    PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[n & 1u], 4 * cnt, cudaMemcpyDeviceToHost, h->stream));
+    PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[t & 1u], 4 * cnt, cudaMemcpyDeviceToHost, h->stream));
     PF_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   if (scalars) {
@@ -718,7 +730,7 @@ pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
   if (!h || !buf || len == 0) return fail(h, PF_EINVAL, "NULL argument");
   const Plan& pl = h->plan;
   std::string o = "{\"N\": " + std::to_string(pl.N) + ", \"d\": " + std::to_string(pl.d) +
-                  ", \"digits\": [";
+                  ", \"stages_per_step\": " + std::to_string(pl.sps) + ", \"digits\": [";
   if (pl.global)
     o += "{\"a\": " + std::to_string(pl.N) + ", \"s\": 1, \"kernel\": \"global\", \"scan_tiles\": " +
          std::to_string(pl.nscan) + ", \"grid\": " + std::to_string(pl.grid_draw) + "}";
@@ -822,6 +834,7 @@ struct NoAllocStart {
 __global__ void noalloc_start_kernel(DevState* st, float* y_ring, NoAllocStart s) {
   if (threadIdx.x == 0) {
     st->n = s.n;
+    st->stage = 0;
     st->done = 0;
     st->status = 0;
     st->mu = s.mu;
@@ -872,6 +885,7 @@ extern "C" pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int
   P.seed_hi = (uint32_t)(seed >> 32);
   P.tile_cap = pl.cap;
   P.inv_N = (float)(1.0 / pl.N);
+  P.sps = 1;
   P.model = pl.mp;
   std::memcpy(P.geom, pl.geom, sizeof(P.geom));
 

@@ -35,34 +35,6 @@
 
 namespace bfpf {
 
-template <int D, int KIND, bool WIDE>
-__global__ void __launch_bounds__(kBlock) step_butterfly_kernel(const __grid_constant__ StepParams p) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  DevState* st = p.st;
-  TileCtx c;
-  c.n = st->n;
-  const uint32_t k = c.n % (uint32_t)p.m;
-  c.x = p.x;
-  c.lV_in = p.lV[c.n & 1u];
-  c.lV_out = p.lV[(c.n & 1u) ^ 1u];
-  c.anc = p.anc;
-  c.rk = &p.rk;
-  c.mp = &p.model;
-  c.g = &p.geom[k];
-  c.N = p.N;
-  c.cap = p.tile_cap;
-  c.muf = st->mu_f;
-#pragma unroll
-  for (int j = 0; j < kMaxDim; ++j) c.y[j] = (j < p.model.dy) ? p.y_ring[(c.n % kRing) * p.model.dy + j] : 0.0f;
-  uint32_t status = 0;
-  Partial acc{-INFINITY, 0.0f, 0.0f};
-  float accx[D];
-#pragma unroll
-  for (int t = 0; t < D; ++t) accx[t] = 0.0f;
-  tile_steps<D, KIND, WIDE>(c, blockIdx.x, gridDim.x, smem_raw, acc, accx, status);
-  finish_step<D>(p, acc, accx, c.n, status, c.muf);
-}
-
 // Initial particles zeta_0 ~ pi_0 (Algorithm 1, first loop).
 template <int D, int KIND>
 __global__ void __launch_bounds__(kBlock) init_particles_kernel(const __grid_constant__ StepParams p) {
@@ -104,7 +76,8 @@ __global__ void philox_blocks_kernel(uint32_t k0, uint32_t k1, uint4 c, uint32_t
 // ---------------------------------------------------------------------------
 template <int D, int KIND, bool WIDE>
 static void fill_step(KernelSet& ks) {
-  ks.step = reinterpret_cast<const void*>(&step_butterfly_kernel<D, KIND, WIDE>);
+  ks.step = reinterpret_cast<const void*>(&step_butterfly_kernel<D, KIND, WIDE, false>);
+  ks.step_staged = select_staged_tile_kernel(D, KIND, WIDE);
   ks.init = reinterpret_cast<const void*>(&init_particles_kernel<D, KIND>);
 }
 
@@ -135,16 +108,16 @@ bool select_kernels(int d, int kind, bool wide, KernelSet& ks) {
 #undef BFPF_CASE
 }
 
-const void* select_group_kernel(int d, int kind, int a, int* G) {
+const void* select_group_kernel(int d, int kind, int a, int* G, bool staged) {
   switch (d) {
-    case 1: return group_kernel_d1(kind, a, G);
-    case 2: return group_kernel_d2(kind, a, G);
-    case 3: return group_kernel_d3(kind, a, G);
-    case 4: return group_kernel_d4(kind, a, G);
-    case 5: return group_kernel_d5(kind, a, G);
-    case 6: return group_kernel_d6(kind, a, G);
-    case 7: return group_kernel_d7(kind, a, G);
-    case 8: return group_kernel_d8(kind, a, G);
+    case 1: return group_kernel_d1(kind, a, G, staged);
+    case 2: return group_kernel_d2(kind, a, G, staged);
+    case 3: return group_kernel_d3(kind, a, G, staged);
+    case 4: return group_kernel_d4(kind, a, G, staged);
+    case 5: return group_kernel_d5(kind, a, G, staged);
+    case 6: return group_kernel_d6(kind, a, G, staged);
+    case 7: return group_kernel_d7(kind, a, G, staged);
+    case 8: return group_kernel_d8(kind, a, G, staged);
     default: return nullptr;
   }
 }

@@ -70,7 +70,8 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
       merge_partial<D>(acc, accx, lw, 1.0f, 1.0f, one);
     }
   }
-  finish_step<D, false>(p, acc, accx, n, status, muf, p.lV[(n & 1u) ^ 1u]);
+  const Sched sc{n, n, 0u, true, true};   // one digit (m = 1): every step is one whole stage
+  finish_step<D, false>(p, acc, accx, sc, status, muf, p.lV[(n & 1u) ^ 1u]);
 }
 
 __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_constant__ StepParams p,

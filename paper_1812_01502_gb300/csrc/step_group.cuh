@@ -30,7 +30,11 @@
 
 namespace bfpf {
 
-template <int D, int KIND, int A, int G>
+// STAGED = false: one stage per time step (every launch weights and mutates).
+// STAGED = true: the stage schedule of the device state decides both (all
+// stages per step, Sched); a separate instantiation keeps the default path's
+// registers unchanged.
+template <int D, int KIND, int A, int G, bool STAGED>
 __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constant__ StepParams p,
                                                            const __grid_constant__ GroupGeom gg) {
   static_assert(A >= 2 && A <= 32 && (A & (A - 1)) == 0, "radix must be a power of two <= 32");
@@ -53,9 +57,12 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
   const uint32_t tg = tid / G, j = tid % G;
   const ModelParams& mp = p.model;
   DevState* st = p.st;
-  const uint32_t n = st->n;
-  const float* __restrict__ lV_in = p.lV[n & 1u];
-  float* __restrict__ lV_out = p.lV[(n & 1u) ^ 1u];
+  const Sched sc = STAGED ? sched_of(p, st) : Sched{st->n, st->n, 0u, true, true};
+  const bool obs = STAGED ? sc.obs : true;
+  const bool mut = STAGED ? sc.mut : true;
+  const uint32_t n = sc.n;
+  const float* __restrict__ lV_in = p.lV[sc.t & 1u];
+  float* __restrict__ lV_out = p.lV[(sc.t & 1u) ^ 1u];
   float* __restrict__ X = p.x;
   const float muf = st->mu_f;
   const uint32_t N = p.N;
@@ -105,8 +112,10 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
         lw[mm] = __ldg(lvp + mm * gg.lv_mul);
       }
     }
+    if (obs) {
 #pragma unroll
-    for (int mm = 0; mm < M; ++mm) lw[mm] += obs_log_term<D, KIND>(mp, y, xv[mm]) - muf;
+      for (int mm = 0; mm < M; ++mm) lw[mm] += obs_log_term<D, KIND>(mp, y, xv[mm]) - muf;
+    }
 
     // ---- group max, weights, integer prefix sums ----
     float mx = lw[0];
@@ -211,7 +220,7 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
       constexpr int MQ = (M < 4) ? M : 4;             // members handled in this round
       uint32_t rw[MQ];
       {
-        const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) + q4, n, kPurposeResample, 0), p.rk);
+        const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) + q4, sc.t, kPurposeResample, 0), p.rk);
         if constexpr (M >= 4) {
           rw[0] = w.x; rw[1] = w.y; rw[2] = w.z; rw[3] = w.w;
         } else {
@@ -223,7 +232,9 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
         }
       }
       float z[MQ * D];
-      if constexpr ((MQ * D) % 4 == 0) {              // then the first normal number is a multiple of 4
+      if (!mut) {
+        // not the last stage of the step: no mutation, no propagation normals
+      } else if constexpr ((MQ * D) % 4 == 0) {              // then the first normal number is a multiple of 4
         const uint32_t c0 = ((pi0 + 4 * q4) * D) >> 2;
 #pragma unroll
         for (int b = 0; b < MQ * D / 4; ++b) {
@@ -280,7 +291,12 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
         float xh[D];
 #pragma unroll
         for (int t = 0; t < D; ++t) xh[t] = __uint_as_float(col[(t * A + c) * LD]);
-        mutate<D, KIND>(mp, xh, z + mq * D, xo[mm]);
+        if (mut) {
+          mutate<D, KIND>(mp, xh, z + mq * D, xo[mm]);
+        } else {
+#pragma unroll
+          for (int t = 0; t < D; ++t) xo[mm][t] = xh[t];
+        }
         coff[mm] = c;
       }
     }
@@ -303,7 +319,7 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
     }
     __syncwarp();
   }
-  finish_step<D>(p, acc, accx, n, status, muf);
+  finish_step<D>(p, acc, accx, sc, status, muf);
 }
 
 // Lanes per group: each lane keeps M = A / G members, M * D <= 16 state values.
@@ -313,24 +329,29 @@ constexpr int group_members_per_lane(int A, int D) {
   return m;
 }
 
-template <int D, int KIND, int A>
+template <int D, int KIND, int A, bool STAGED>
 inline const void* group_kernel_pick(int& G) {
   constexpr int M = group_members_per_lane(A, D);
   constexpr int GG = A / M;
   G = GG;
-  return reinterpret_cast<const void*>(&step_group_kernel<D, KIND, A, GG>);
+  return reinterpret_cast<const void*>(&step_group_kernel<D, KIND, A, GG, STAGED>);
+}
+
+template <int D, int KIND, bool STAGED>
+inline const void* group_kernel_for_s(int a, int& G) {
+  switch (a) {
+    case 2: return group_kernel_pick<D, KIND, 2, STAGED>(G);
+    case 4: return group_kernel_pick<D, KIND, 4, STAGED>(G);
+    case 8: return group_kernel_pick<D, KIND, 8, STAGED>(G);
+    case 16: return group_kernel_pick<D, KIND, 16, STAGED>(G);
+    case 32: return group_kernel_pick<D, KIND, 32, STAGED>(G);
+    default: return nullptr;
+  }
 }
 
 template <int D, int KIND>
-inline const void* group_kernel_for(int a, int& G) {
-  switch (a) {
-    case 2: return group_kernel_pick<D, KIND, 2>(G);
-    case 4: return group_kernel_pick<D, KIND, 4>(G);
-    case 8: return group_kernel_pick<D, KIND, 8>(G);
-    case 16: return group_kernel_pick<D, KIND, 16>(G);
-    case 32: return group_kernel_pick<D, KIND, 32>(G);
-    default: return nullptr;
-  }
+inline const void* group_kernel_for(int a, int& G, bool staged) {
+  return staged ? group_kernel_for_s<D, KIND, true>(a, G) : group_kernel_for_s<D, KIND, false>(a, G);
 }
 
 }  // namespace bfpf

@@ -4,10 +4,10 @@
 
 namespace bfpf {
 
-const void* group_kernel_d2(int kind, int a, int* G) {
+const void* group_kernel_d2(int kind, int a, int* G, bool staged) {
 
   if (kind != kLinearGaussian) return nullptr;
-  return group_kernel_for<2, kLinearGaussian>(a, *G);
+  return group_kernel_for<2, kLinearGaussian>(a, *G, staged);
 }
 
 }  // namespace bfpf

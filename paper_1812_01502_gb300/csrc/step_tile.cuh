@@ -34,11 +34,15 @@ struct TileCtx {
   const ModelParams* mp;
   const DigitGeom* g;        // geometry of this step's digit
   uint32_t N, n, cap;
+  uint32_t t;                // stage counter (resampling counters)
+  bool obs, mut;             // weight with g_n / mutate (see Sched)
   float muf;
   float y[kMaxDim];
 };
 
-template <int D, int KIND, bool WIDE>
+// STAGED = false: every call weights with g_n and mutates (one stage per
+// step); STAGED = true: ctx.obs / ctx.mut decide (all stages per step).
+template <int D, int KIND, bool WIDE, bool STAGED = false>
 __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, uint32_t stride,
                                            unsigned char* smem_raw, Partial& acc, float* accx,
                                            uint32_t& status) {
@@ -57,7 +61,9 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
   float* __restrict__ lV_out = ctx.lV_out;
   float* __restrict__ X = ctx.x;
   const float muf = ctx.muf;
-  const uint32_t N = ctx.N, n = ctx.n;
+  const uint32_t N = ctx.N, n = ctx.n, t_st = STAGED ? ctx.t : ctx.n;
+  const bool obs = STAGED ? ctx.obs : true;
+  const bool mut = STAGED ? ctx.mut : true;
   const float* y = ctx.y;
   const uint32_t ngroups = g.nh * nl;   // groups per tile
   // lifting steps of the ancestor search: largest power of two < a (0 if a == 1)
@@ -105,7 +111,7 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
       float xv[D];
 #pragma unroll
       for (int t = 0; t < D; ++t) xv[t] = s_x[t * cap + pos];
-      s_lw[pos] = sanitize_logweight(lv + obs_log_term<D, KIND>(mp, y, xv) - muf, status);
+      s_lw[pos] = sanitize_logweight(obs ? lv + obs_log_term<D, KIND>(mp, y, xv) - muf : lv, status);
     }
     __syncthreads();
 
@@ -167,20 +173,22 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
       float z[4 * D];
       if (a4) {   // pi0 % 4 == 0: whole counter blocks
         if (WIDE && wide_digit) {
-          const uint4 w0 = philox4x32_10(make_uint4(pi0 >> 1, n, kPurposeResampleWide, 0), rk);
-          const uint4 w1 = philox4x32_10(make_uint4((pi0 >> 1) + 1, n, kPurposeResampleWide, 0), rk);
+          const uint4 w0 = philox4x32_10(make_uint4(pi0 >> 1, t_st, kPurposeResampleWide, 0), rk);
+          const uint4 w1 = philox4x32_10(make_uint4((pi0 >> 1) + 1, t_st, kPurposeResampleWide, 0), rk);
           rw64[0] = ((unsigned long long)w0.y << 32) | w0.x;
           rw64[1] = ((unsigned long long)w0.w << 32) | w0.z;
           rw64[2] = ((unsigned long long)w1.y << 32) | w1.x;
           rw64[3] = ((unsigned long long)w1.w << 32) | w1.z;
         } else {
-          const uint4 w = philox4x32_10(make_uint4(pi0 >> 2, n, kPurposeResample, 0), rk);
+          const uint4 w = philox4x32_10(make_uint4(pi0 >> 2, t_st, kPurposeResample, 0), rk);
           rw[0] = w.x; rw[1] = w.y; rw[2] = w.z; rw[3] = w.w;
         }
+        if (mut) {
 #pragma unroll
-        for (int b = 0; b < D; ++b) {
-          const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
-          normals4(w, z + 4 * b);
+          for (int b = 0; b < D; ++b) {
+            const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
+            normals4(w, z + 4 * b);
+          }
         }
       } else {    // members straddle counter blocks: one block per draw / normal
 #pragma unroll
@@ -188,13 +196,14 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
           const uint32_t pi = pi0 + jj;
           if (r0 + jj >= a) break;
           if (WIDE && wide_digit) {
-            const uint4 w = philox4x32_10(make_uint4(pi >> 1, n, kPurposeResampleWide, 0), rk);
+            const uint4 w = philox4x32_10(make_uint4(pi >> 1, t_st, kPurposeResampleWide, 0), rk);
             rw64[jj] = (pi & 1u) ? (((unsigned long long)w.w << 32) | w.z) : (((unsigned long long)w.y << 32) | w.x);
           } else {
-            const uint4 w = philox4x32_10(make_uint4(pi >> 2, n, kPurposeResample, 0), rk);
+            const uint4 w = philox4x32_10(make_uint4(pi >> 2, t_st, kPurposeResample, 0), rk);
             const uint32_t sel = pi & 3u;
             rw[jj] = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
           }
+          if (!mut) continue;
 #pragma unroll
           for (int t = 0; t < D; ++t) {
             const uint32_t nu = pi * D + t;
@@ -222,7 +231,12 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
         float xh[D], xo[D];
 #pragma unroll
         for (int t = 0; t < D; ++t) xh[t] = s_x[t * cap + pa];
-        mutate<D, KIND>(mp, xh, z + jj * D, xo);
+        if (mut) {
+          mutate<D, KIND>(mp, xh, z + jj * D, xo);
+        } else {
+#pragma unroll
+          for (int t = 0; t < D; ++t) xo[t] = xh[t];
+        }
         const uint32_t i = ib + r * s;
 #pragma unroll
         for (int t = 0; t < D; ++t) __stcs(X + (size_t)t * N + i, xo[t]);
@@ -231,6 +245,40 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
     }
   }
 
+}
+
+// The general kernel: the tiles of one stage split over a persistent grid,
+// then the end-of-step epilogue (step_butterfly.cu, step_butterfly_staged.cu
+// instantiate it).
+template <int D, int KIND, bool WIDE, bool STAGED>
+__global__ void __launch_bounds__(kBlock) step_butterfly_kernel(const __grid_constant__ StepParams p) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  DevState* st = p.st;
+  const Sched sc = STAGED ? sched_of(p, st) : Sched{st->n, st->n, st->n % (uint32_t)p.m, true, true};
+  TileCtx c;
+  c.n = sc.n;
+  c.t = sc.t;
+  c.obs = sc.obs;
+  c.mut = sc.mut;
+  c.x = p.x;
+  c.lV_in = p.lV[sc.t & 1u];
+  c.lV_out = p.lV[(sc.t & 1u) ^ 1u];
+  c.anc = p.anc;
+  c.rk = &p.rk;
+  c.mp = &p.model;
+  c.g = &p.geom[sc.k];
+  c.N = p.N;
+  c.cap = p.tile_cap;
+  c.muf = st->mu_f;
+#pragma unroll
+  for (int j = 0; j < kMaxDim; ++j) c.y[j] = (j < p.model.dy) ? p.y_ring[(c.n % kRing) * p.model.dy + j] : 0.0f;
+  uint32_t status = 0;
+  Partial acc{-INFINITY, 0.0f, 0.0f};
+  float accx[D];
+#pragma unroll
+  for (int t = 0; t < D; ++t) accx[t] = 0.0f;
+  tile_steps<D, KIND, WIDE, STAGED>(c, blockIdx.x, gridDim.x, smem_raw, acc, accx, status);
+  finish_step<D>(p, acc, accx, sc, status, c.muf);
 }
 
 }  // namespace bfpf

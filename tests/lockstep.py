@@ -173,3 +173,49 @@ def check_step_sampled(filt, model, radices, seed, y_n, n, n_groups, rng):
                   mismatched_undecidable=int(np.sum(member_gpu != member_o)),
                   max_state_err=e_x, max_logweight_err=e_lv, max_inc_err=e_inc, max_mean_err=e_mean,
                   max_ess_err=e_ess)
+
+
+def check_step_all_stages(filt, model, radices, seed, y_n, n):
+    """GPU time step n with every stage of Algorithm 3 (PF_ALL_STAGES) against the
+    oracle's all-stages step from the same state.
+
+    After the first stage the stage weights are group sums of the previous
+    stage's weights, independent of which particles were drawn, so the integer
+    weights and uniforms of every stage are comparable between the sides.  A
+    particle's final state must match the oracle's when every draw on its line
+    of ancestry (one per stage) is decidable; increment, mean, ESS and the new
+    carried weights (all equal, Lemma 3(c)) must match always."""
+    N = int(np.prod(radices))
+    m = len(radices)
+    x0, lv0, sc = filt.state()
+    assert sc["n"] == n
+    mean, inc, ess = filt.step(y_n)
+    x1, lv1, sc1 = filt.state()
+    lV = per_particle_lV(lv0, radices, n * m).astype(np.float64)
+    st = bpf.State(x=x0.astype(np.float64), lV=lV, mu=sc["mu"], n=n)
+    new, o = bpf.step_all_stages(model, radices, seed, st, y_n, mu_used=sc["mu_used"])
+    strides = butterfly.strides(radices)
+    line = None
+    undecidable = 0
+    for sg in o["stages"]:
+        k = sg["k"]
+        a, s = int(radices[k]), strides[k]
+        H = N // (a * s)
+        lo, hi = plausible_members(sg["q"].reshape(H, a, s), sg["u"].reshape(H, a, s), axis=1)
+        dec = (lo == hi).reshape(N)
+        undecidable += int(np.sum(~dec))
+        line = dec if line is None else dec & line[sg["anc"]]
+    e_x = rel_err(x1[line], new.x[line])
+    e_lv = rel_err(lv1, np.full(lv1.shape, new.lV[0]))
+    e_inc = abs(inc - o["inc"]) / max(1.0, abs(o["inc"]))
+    e_mean = rel_err(mean, o["mean"])
+    e_ess = abs(ess - o["ess"]) / max(o["ess"], 1e-12)
+    assert e_x <= TOL_STATE, f"step {n}: state error {e_x}"
+    assert e_lv <= TOL_STATE, f"step {n}: log-weight error {e_lv}"
+    assert e_inc <= TOL_INC, f"step {n}: likelihood increment error {e_inc}"
+    assert e_mean <= TOL_STATE, f"step {n}: mean error {e_mean}"
+    assert e_ess <= 1e-4, f"step {n}: ess error {e_ess}"
+    assert abs(sc1["mu"] - new.mu) <= 1e-6 * max(1.0, abs(new.mu))
+    return Report(draws=N * m, undecidable=undecidable, undecided_lines=int(np.sum(~line)),
+                  max_state_err=e_x, max_logweight_err=e_lv, max_inc_err=e_inc, max_mean_err=e_mean,
+                  max_ess_err=e_ess)

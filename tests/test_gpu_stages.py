@@ -1,0 +1,64 @@
+"""The paper's schedule (PF_ALL_STAGES): every stage of Algorithm 3 inside each
+time step, checked step by step against the oracle's all-stages step."""
+import numpy as np
+import pytest
+
+import synthetic as S
+import lockstep as LS
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("name,model,radices,T", [
+    ("lg_radix2", S.lg_scalar(), (2,) * 10, 5),
+    ("sv_group", S.sv_model(), (16, 16, 4), 5),
+    ("lg4_group", S.lg_dense(4, seed=3), (8, 8, 4), 4),
+    ("lg8_group", S.lg_dense(8, seed=4), (32, 32), 3),
+    ("lg1_mixed_tile", S.lg_scalar(), (3, 5, 7), 5),
+    ("lg2_tile", S.lg_dense(2, seed=5), (64, 16), 4),
+    ("sv_wide", S.sv_model(), (300, 4), 4),
+])
+def test_all_stages_lockstep(bfpf, name, model, radices, T):
+    N = int(np.prod(radices))
+    y = S.simulate(model, T, seed=23)[1]
+    seed = 777
+    f = bfpf.ButterflyFilter(model, N, radices, seed, all_stages=True)
+    assert f.describe()["stages_per_step"] == len(radices)
+    rep = LS.Report()
+    for n in range(T):
+        rep.merge(LS.check_step_all_stages(f, model, radices, seed, y[n], n))
+    f.close()
+    print(name, dict(rep))
+    assert rep["undecided_lines"] <= max(8, 0.02 * N * T)
+
+
+def test_all_stages_graph_equals_steps(bfpf):
+    """Chunks replayed from CUDA graphs (m launches per step) equal single steps."""
+    model, radices = S.sv_model(), (16, 8, 4)
+    N = int(np.prod(radices))
+    y = S.simulate(model, 40, seed=29)[1]
+    a = bfpf.ButterflyFilter(model, N, radices, 31, all_stages=True, chunk_len=8)
+    ra = a.run(y)
+    b = bfpf.ButterflyFilter(model, N, radices, 31, all_stages=True)
+    inc_b = [b.step(y[n])[1] for n in range(len(y))]
+    assert np.array_equal(ra["inc"], np.array(inc_b))
+    assert np.array_equal(a.state()[0], b.state()[0])
+    a.close()
+    b.close()
+
+
+def test_all_stages_single_digit_is_default(bfpf):
+    """With one digit the two schedules are the same filter."""
+    model = S.lg_scalar()
+    y = S.simulate(model, 12, seed=31)[1]
+    a = bfpf.ButterflyFilter(model, 512, (512,), 5, all_stages=True)
+    b = bfpf.ButterflyFilter(model, 512, (512,), 5)
+    ra, rb = a.run(y), b.run(y)
+    assert np.array_equal(ra["inc"], rb["inc"]) and np.array_equal(a.state()[0], b.state()[0])
+    a.close()
+    b.close()
+
+
+def test_all_stages_rejects_ancestor_recording(bfpf):
+    with pytest.raises(bfpf.PFError):
+        bfpf.ButterflyFilter(S.lg_scalar(), 64, (8, 8), 1, all_stages=True, record_ancestors=True)

@@ -234,3 +234,16 @@ def test_all_stages_schedule_lemma3_and_textbook_increment(radices):
             a, s = radices[k], butterfly.strides(radices)[k]
             idx = np.arange(N)
             assert np.array_equal(sg["anc"] // (a * s), idx // (a * s)) and np.array_equal(sg["anc"] % s, idx % s)
+
+
+def test_all_stages_with_one_digit_is_the_one_digit_step():
+    """With m = 1 the two schedules coincide, counters included (t = n)."""
+    model = S.sv_model()
+    y = S.simulate(model, 4, seed=3)[1]
+    a = bpf.init_state(model, 64, seed=8)
+    b = bpf.init_state(model, 64, seed=8)
+    for n in range(4):
+        a, oa = bpf.step(model, (64,), 8, a, y[n])
+        b, ob = bpf.step_all_stages(model, (64,), 8, b, y[n])
+        assert np.array_equal(a.x, b.x) and np.array_equal(oa["anc"], ob["stages"][0]["anc"])
+        assert oa["inc"] == ob["inc"]
