@@ -39,6 +39,7 @@ class State:
     mu: float                # carried normaliser mu_n
     n: int                   # time index of the next observation
     loglik: float = 0.0      # log p^(y_0..y_{n-1})
+    start: int = 0           # fully adapted schedule: digit the next step's stages start at
 
 
 def obs_terms(model, x: np.ndarray, y: np.ndarray):
@@ -176,6 +177,55 @@ def step_all_stages(model, radices: Sequence[int], seed: int, st: State, y_n: np
     return new, dict(stages=stages, inc=inc, mean=mean, ess=ess, lV_new=lw, c=c_n)
 
 
+def ess_of(lv: np.ndarray) -> float:
+    """Effective sample size (Section 1.2) of the weights exp(lv): (sum w)^2 / (N sum w^2)."""
+    w = np.exp(lv - np.max(lv))
+    return float(np.sum(w) ** 2 / (len(lv) * np.sum(w * w)))
+
+
+def step_adaptive(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray, theta: float,
+                  rotate: bool = False, mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
+    """One time step with fully adapted augmented resampling (Section 1.2): weight
+    with g_n, then run the stages of Algorithm 3 one after another, evaluating the
+    ESS of the current weights before each stage and skipping the remaining
+    stages once it reaches theta; then mutate.  Weights that were not equalised
+    carry over to the next step (per particle).
+
+    Launch j = 0..m-1 of step n works on digit k = (start + j) mod m and draws with
+    stage counter t = n m + j; start = 0 unless ``rotate``, in which case the next
+    step starts one digit after the last stage executed (Section 6.4's proposal),
+    and stays put after a step without resampling.  The mutation's normals are
+    numbered group-major on the digit of launch m-1, as in the other schedules.
+    theta > 1 runs every stage (the all-stages step); theta <= 1/N runs none
+    (sequential importance sampling)."""
+    radices = [int(a) for a in radices]
+    m = len(radices)
+    n = st.n
+    N = st.x.shape[0]
+    mu_sub = st.mu if mu_used is None else float(mu_used)
+    lw, c_n = weigh(model, st.x, st.lV, mu_sub, y_n)
+    inc, mean, ess, lme = summaries(lw, st.x, c_n, mu_sub, st.mu)
+    x = st.x
+    cur = lw
+    e = ess
+    stages = []
+    for j in range(m):
+        if e >= theta:
+            break
+        k = (st.start + j) % m
+        x, lV_new, anc, q, u, pi = stage(radices, seed, x, cur, k, n * m + j)
+        stages.append(dict(k=k, j=j, anc=anc, q=q, u=u, lw=cur, lV_new=lV_new, ess_before=e))
+        cur = lV_new
+        e = ess_of(cur)
+    k_last = (st.start + m - 1) % m
+    x_next = mutate(model, x, n, seed, idx=group_major(N, radices, k_last))
+    start = st.start
+    if rotate and stages:
+        start = (stages[-1]["k"] + 1) % m
+    new = State(x=x_next, lV=cur, mu=lme, n=n + 1, loglik=st.loglik + inc, start=start)
+    return new, dict(stages=stages, inc=inc, mean=mean, ess=ess, ess_final=e, lV_new=cur, c=c_n)
+
+
 def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
          mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
     """One time step n = st.n: weight, one augmented-resampling stage, mutate.
@@ -230,9 +280,11 @@ def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
 
 
 def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
-        keep_ancestors: bool = False, all_stages: bool = False) -> Dict[str, np.ndarray]:
+        keep_ancestors: bool = False, all_stages: bool = False, theta: Optional[float] = None,
+        rotate: bool = False) -> Dict[str, np.ndarray]:
     """Run the filter over y[0:T].  Returns per-step inc, mean, ess and the final loglik.
-    all_stages: the paper's schedule (all m stages per time step) instead of one digit."""
+    all_stages: the paper's schedule (all m stages per time step) instead of one digit;
+    theta: fully adapted resampling with ESS threshold theta (optionally rotated)."""
     if int(np.prod(radices)) != N:
         raise ValueError("product of radices must equal N")
     y = np.asarray(y, dtype=np.float64).reshape(len(y), -1)
@@ -242,12 +294,17 @@ def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
     means = np.empty((T, model.d))
     ess = np.empty(T)
     ancs = [] if keep_ancestors else None
+    executed = 0
     for t in range(T):
-        st, o = (step_all_stages if all_stages else step)(model, radices, seed, st, y[t])
+        if theta is not None:
+            st, o = step_adaptive(model, radices, seed, st, y[t], theta, rotate)
+            executed += len(o["stages"])
+        else:
+            st, o = (step_all_stages if all_stages else step)(model, radices, seed, st, y[t])
         incs[t], means[t], ess[t] = o["inc"], o["mean"], o["ess"]
-        if keep_ancestors and not all_stages:
+        if keep_ancestors and not all_stages and theta is None:
             ancs.append(o["anc"])
-    out = dict(inc=incs, mean=means, ess=ess, loglik=st.loglik, state=st)
+    out = dict(inc=incs, mean=means, ess=ess, loglik=st.loglik, state=st, stages_executed=executed)
     if keep_ancestors:
         out["anc"] = np.stack(ancs)
     return out

@@ -247,3 +247,68 @@ def test_all_stages_with_one_digit_is_the_one_digit_step():
         b, ob = bpf.step_all_stages(model, (64,), 8, b, y[n])
         assert np.array_equal(a.x, b.x) and np.array_equal(oa["anc"], ob["stages"][0]["anc"])
         assert oa["inc"] == ob["inc"]
+
+
+def test_adaptive_theta_above_one_is_all_stages():
+    """ESS <= 1 < theta: every stage runs, so the step is the all-stages step."""
+    model, radices = S.lg_scalar(), (4, 2, 8)
+    y = S.simulate(model, 4, seed=5)[1]
+    a = bpf.init_state(model, 64, seed=3)
+    b = bpf.init_state(model, 64, seed=3)
+    for n in range(4):
+        a, oa = bpf.step_all_stages(model, radices, 3, a, y[n])
+        b, ob = bpf.step_adaptive(model, radices, 3, b, y[n], theta=1.5, rotate=True)
+        assert len(ob["stages"]) == 3 and b.start == 0
+        assert np.array_equal(a.x, b.x) and np.array_equal(a.lV, b.lV) and oa["inc"] == ob["inc"]
+
+
+def test_adaptive_theta_zero_is_sequential_importance_sampling():
+    """theta <= 1/N never resamples: each particle keeps its own path and the
+    likelihood estimate is log N^-1 sum_i prod_n g_n(x_i^n), computed here
+    directly from the unresampled paths."""
+    model = S.lg_dense(2, seed=6)
+    radices, N, T = (4, 4), 16, 5
+    y = S.simulate(model, T, seed=8)[1]
+    st = bpf.init_state(model, N, seed=9)
+    x = st.x.copy()
+    logg = np.zeros(N)
+    const = 0.0
+    for n in range(T):
+        s_x, c = bpf.obs_terms(model, x, y[n])
+        logg += s_x
+        const += c
+        st, o = bpf.step_adaptive(model, radices, 9, st, y[n], theta=0.0)
+        assert o["stages"] == []
+        x = bpf.mutate(model, x, n, 9, idx=butterfly.group_major(N, radices, 1))
+        np.testing.assert_allclose(st.x, x, rtol=0, atol=0)
+    mx = logg.max()
+    direct = mx + np.log(np.mean(np.exp(logg - mx))) + const
+    assert abs(st.loglik - direct) < 1e-9 * max(1.0, abs(direct))
+
+
+@pytest.mark.parametrize("rotate", [False, True])
+def test_adaptive_stopping_rule_and_weight_mass(rotate):
+    """Stages run in rotation order while the ESS is below theta and stop once it
+    reaches theta; each stage preserves the total weight (doubly stochastic A)."""
+    model, radices = S.sv_model(), (4, 4, 4)
+    N, theta = 64, 0.7
+    y = S.simulate(model, 12, seed=12)[1]
+    st = bpf.init_state(model, N, seed=13)
+    starts = []
+    for n in range(12):
+        start = st.start
+        starts.append(start)
+        st, o = bpf.step_adaptive(model, radices, 13, st, y[n], theta=theta, rotate=rotate)
+        for j, sg in enumerate(o["stages"]):
+            assert sg["j"] == j and sg["k"] == (start + j) % 3 and sg["ess_before"] < theta
+            mx = sg["lw"].max()
+            np.testing.assert_allclose(np.sum(np.exp(sg["lV_new"] - mx)), np.sum(np.exp(sg["lw"] - mx)),
+                                       rtol=1e-12)
+        if len(o["stages"]) < 3:
+            assert o["ess_final"] >= theta
+        if rotate and o["stages"]:
+            assert st.start == (o["stages"][-1]["k"] + 1) % 3
+        if not rotate:
+            assert st.start == 0
+    if rotate:
+        assert len(set(starts)) > 1
