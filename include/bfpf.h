@@ -91,13 +91,28 @@ typedef struct {
  * schedule).  Costs m kernel launches per time step.  Cannot be combined
  * with PF_RECORD_ANCESTORS (EINVAL).  Ignored when m = 1. */
 #define PF_ALL_STAGES 2u
+/* Fully adapted augmented resampling (Section 1.2): each time step weights
+ * with g_n, then runs the stages of Algorithm 3 on digits 0, 1, ..., m-1 in
+ * turn while the effective sample size (Section 1.2) of the current weights
+ * is below pf_options.ess_threshold, skipping the rest once it is reached;
+ * then mutates.  Weights that were not equalised carry over to the next
+ * step, so carried log-weights are kept per particle (N floats; pf_get_state
+ * returns N of them).  m + 1 kernel launches per time step.  Radices must
+ * keep every group within one thread block (each a_k <= 1024; m = 1 needs
+ * N <= 1024).  Cannot be combined with PF_ALL_STAGES or PF_RECORD_ANCESTORS. */
+#define PF_ADAPTIVE 4u
+/* With PF_ADAPTIVE: start each step's stages one digit after the last stage
+ * executed (the rotation proposed in Section 6.4) instead of at digit 0. */
+#define PF_ROTATE 8u
 
 typedef struct {
     int32_t tile;        /* target particles per thread-block tile; 0 = automatic            */
     int32_t chunk_len;   /* time steps per CUDA-graph replay in pf_run; 0 = 64 (max 1024)    */
-    uint32_t flags;      /* PF_RECORD_ANCESTORS | PF_ALL_STAGES                              */
+    uint32_t flags;      /* PF_RECORD_ANCESTORS | PF_ALL_STAGES | PF_ADAPTIVE | PF_ROTATE     */
     int32_t grid;        /* persistent thread blocks; 0 = automatic (SMs x occupancy)        */
     void* stream;        /* cudaStream_t to run on; NULL = the legacy default stream          */
+    float ess_threshold; /* PF_ADAPTIVE: a stage runs while ESS < ess_threshold; 0 = 0.5.     */
+                         /* Values above 1 run every stage; values <= 1/N run none.          */
 } pf_options;
 
 typedef struct pf_handle pf_handle;
@@ -173,9 +188,10 @@ pf_status pf_loglik(const pf_handle* h, double* out);
  * Copy the filter state to host memory (synchronises; any pointer may be NULL):
  *   x        N*d floats, state-major: x[t*N + i] = component t of particle i;
  *   lV       N / a_{k'} floats: carried log stage weights, one per group of the
- *            digit k' = (n-1) mod m used by the last step (all zero before the
- *            first step), group index  (i / (a_{k'} s_{k'})) * s_{k'} + i % s_{k'},
- *            s_{k'} = a_0 ... a_{k'-1};
+ *            digit k' of the last stage run (k' = (n-1) mod m; m-1 with
+ *            PF_ALL_STAGES; all zero before the first step), group index
+ *            (i / (a_{k'} s_{k'})) * s_{k'} + i % s_{k'}, s_{k'} = a_0 ... a_{k'-1};
+ *            with PF_ADAPTIVE: N floats, one per particle;
  *   scalars  4 doubles: { n, loglik, mu, mu_used }, where mu is the carried
  *            normaliser subtracted from the log-weights at the next step (FP64)
  *            and mu_used its FP32 value the kernels subtract.
@@ -190,6 +206,10 @@ pf_status pf_get_ancestors(const pf_handle* h, int32_t* anc);
  * non-finite log-weight was seen and treated as weight zero; bit 1 = a group
  * had zero total weight and kept its particles.  Synchronises. */
 pf_status pf_get_status(const pf_handle* h, uint32_t* bits);
+
+/* Number of resampling stages executed so far (PF_ADAPTIVE counts only the
+ * stages its ESS test let run; otherwise one per stage launched).  Synchronises. */
+pf_status pf_stage_count(const pf_handle* h, uint64_t* out);
 
 /*
  * Describe the launch plan as a JSON object (NUL-terminated, truncated to

@@ -30,6 +30,8 @@ PF_MODEL_LINEAR_GAUSSIAN = 1
 PF_MODEL_STOCH_VOL = 2
 PF_RECORD_ANCESTORS = 1
 PF_ALL_STAGES = 2
+PF_ADAPTIVE = 4
+PF_ROTATE = 8
 STATUS_NAMES = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",
                 PF_ETIMEOUT: "PF_ETIMEOUT", PF_ESTATE: "PF_ESTATE"}
 
@@ -44,7 +46,7 @@ class PFModel(ctypes.Structure):
 
 class PFOptions(ctypes.Structure):
     _fields_ = [("tile", ctypes.c_int32), ("chunk_len", ctypes.c_int32), ("flags", ctypes.c_uint32),
-                ("grid", ctypes.c_int32), ("stream", ctypes.c_void_p)]
+                ("grid", ctypes.c_int32), ("stream", ctypes.c_void_p), ("ess_threshold", ctypes.c_float)]
 
 
 class PFError(RuntimeError):
@@ -80,6 +82,7 @@ def load_library(path: str = LIB_PATH):
         "pf_get_state": (i32, [vp, vp, vp, vp]),
         "pf_get_ancestors": (i32, [vp, vp]),
         "pf_get_status": (i32, [vp, c.POINTER(u32)]),
+        "pf_stage_count": (i32, [vp, c.POINTER(c.c_uint64)]),
         "pf_destroy": (i32, [vp]),
         "pf_describe": (i32, [vp, c.c_char_p, c.c_size_t]),
         "pf_last_error": (c.c_char_p, [vp]),
@@ -147,7 +150,9 @@ class ButterflyFilter:
     """A filter handle: N = prod(radices) particles, digit k = n mod m interacts at step n.
 
     all_stages=True runs every stage of Algorithm 3 in each step instead
-    (digits 0..m-1 in turn; m launches per step).
+    (digits 0..m-1 in turn; m launches per step).  adaptive=True is fully
+    adapted augmented resampling: stages run while the ESS is below
+    ``ess_threshold`` (optionally from a rotated start, ``rotate``).
     radices = (N,) is the global-resampling bootstrap filter (Algorithm 1 + 2).
     The workspace is a torch uint8 tensor on ``device``; work runs on the
     current torch stream of that device unless ``stream`` is given.
@@ -155,7 +160,8 @@ class ButterflyFilter:
 
     def __init__(self, model, N: int, radices: Sequence[int], seed: int, *, tile: int = 0,
                  chunk_len: int = 0, record_ancestors: bool = False, grid: int = 0,
-                 device=None, stream=None, tune: bool = False, all_stages: bool = False):
+                 device=None, stream=None, tune: bool = False, all_stages: bool = False,
+                 adaptive: bool = False, ess_threshold: float = 0.5, rotate: bool = False):
         torch = _torch()
         lib = load_library()
         if not torch.cuda.is_available():
@@ -176,10 +182,13 @@ class ButterflyFilter:
         self._rad = (ctypes.c_int32 * self.m)(*self.radices)
         self._opts = PFOptions(tile=int(tile), chunk_len=int(chunk_len),
                                flags=(PF_RECORD_ANCESTORS if record_ancestors else 0)
-                               | (PF_ALL_STAGES if all_stages else 0), grid=int(grid),
-                               stream=ctypes.c_void_p(self.stream.cuda_stream))
+                               | (PF_ALL_STAGES if all_stages else 0) | (PF_ADAPTIVE if adaptive else 0)
+                               | (PF_ROTATE if rotate else 0), grid=int(grid),
+                               stream=ctypes.c_void_p(self.stream.cuda_stream),
+                               ess_threshold=float(ess_threshold) if adaptive else 0.0)
         self.record_ancestors = record_ancestors
         self.all_stages = bool(all_stages)
+        self.adaptive = bool(adaptive)
         with torch.cuda.device(self.device):
             nbytes = ctypes.c_size_t(0)
             _check(lib.pf_workspace_size(ctypes.byref(self._pm), self.N, self._rad, self.m,
@@ -286,7 +295,7 @@ class ButterflyFilter:
         t = self.steps * (self.m if self.all_stages else 1)    # stages run so far
         kp = (t - 1) % self.m
         x = np.empty((self.d, self.N), dtype=np.float32)
-        lv = np.empty(self.N // self.radices[kp], dtype=np.float32)
+        lv = np.empty(self.N if self.adaptive else self.N // self.radices[kp], dtype=np.float32)
         sc = np.empty(4, dtype=np.float64)
         _check(_lib.pf_get_state(self._h, x.ctypes.data_as(ctypes.c_void_p), lv.ctypes.data_as(ctypes.c_void_p),
                                  sc.ctypes.data_as(ctypes.c_void_p)), self._h)
@@ -308,6 +317,12 @@ class ButterflyFilter:
         b = ctypes.c_uint32(0)
         _check(_lib.pf_get_status(self._h, ctypes.byref(b)), self._h)
         return b.value
+
+    def stage_count(self) -> int:
+        """Resampling stages executed so far (with adaptive=True, those the ESS test let run)."""
+        c = ctypes.c_uint64(0)
+        _check(_lib.pf_stage_count(self._h, ctypes.byref(c)), self._h)
+        return int(c.value)
 
 
 class FilterBatch:

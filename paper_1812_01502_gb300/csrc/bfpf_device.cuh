@@ -234,6 +234,12 @@ struct DevState {
   uint32_t done2;      // global resampling: blocks finished with the draw kernel
   unsigned long long ticket;   // global resampling: scan tiles handed out so far
   uint32_t stage;      // next stage of time step n (0 unless every stage runs in each step)
+  // fully adapted schedule (per-particle carried weights)
+  uint32_t lvp;        // which lV buffer holds the current weights
+  uint32_t skip;       // the ESS reached the threshold: the step's remaining stages are skipped
+  int32_t last_k;      // digit of the last stage executed in this step (-1: none yet)
+  uint32_t start;      // digit the step's stages start at (rotated start)
+  unsigned long long nstages;   // resampling stages executed so far
 };
 
 struct StepParams {
@@ -253,6 +259,8 @@ struct StepParams {
   uint32_t tile_cap;   // shared-memory tile capacity (particles)
   float inv_N;
   uint32_t sps;        // resampling stages per time step: 1 (one digit per step) or m (all of them)
+  float theta;         // fully adapted schedule: ESS threshold in (0, 1] (above 1: every stage)
+  uint32_t rotate;     // fully adapted schedule: start each step one digit after the last stage run
   ModelParams model;
   DigitGeom geom[kMaxDigits];
 };

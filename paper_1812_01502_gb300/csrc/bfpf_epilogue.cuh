@@ -55,21 +55,21 @@ __device__ __forceinline__ void shfl_merge(Partial& acc, float* accx, int off) {
   merge_partial<D>(acc, accx, o.m, o.s1, o.s2, ox);
 }
 
-// Called by every thread of every block exactly once, after its last tile.
-// ADVANCE = false (global resampling, which finishes the step in a later
-// kernel): the last block leaves n alone and instead writes the global
-// maximum log-weight and the single group's new log weight.
-template <int D, bool ADVANCE = true>
-__device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, float* accx, const Sched& sc,
-                                            uint32_t status, float muf, float* lv_single_out = nullptr) {
-  const uint32_t n = sc.n;
+// Grid-wide fold of the per-thread partials, called by every thread of every
+// block exactly once.  Each block writes its partial; the last block to
+// arrive (last-block-done) folds all block partials in a fixed order with
+// compensated FP32 sums.  Returns true in thread 0 of the last block only,
+// with S[0] = sum e^{lw - Mx}, S[1] = sum e^{2(lw - Mx)}, S[2 + t] = sum
+// e^{lw - Mx} x_t (FP64) and Mx the global maximum.
+template <int D>
+__device__ __forceinline__ bool fold_partials(const StepParams& p, Partial acc, float* accx, uint32_t status,
+                                              double* S, float& Mx_out) {
   constexpr int NP = 3 + D;
   constexpr int NW = kBlock / 32;
   __shared__ float s_red[NW][NP];
   __shared__ float s_redlo[NW][NP];
   __shared__ uint32_t s_last;
   DevState* st = p.st;
-  const ModelParams& mp = p.model;
   const uint32_t tid = threadIdx.x;
   if (status) atomicOr(&st->status, status);
   const uint32_t lane = tid & 31u, warp = tid >> 5;
@@ -100,21 +100,8 @@ __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, fl
     s_last = (prev == gridDim.x - 1) ? 1u : 0u;
   }
   __syncthreads();
-  if (!s_last) return;
+  if (!s_last) return false;
   __threadfence();
-  if (!sc.obs) {
-    if (tid == 0) {
-      st->done = 0;
-      __threadfence();
-      if (sc.mut) {
-        st->stage = 0;
-        st->n = n + 1;
-      } else {
-        st->stage = st->stage + 1;
-      }
-    }
-    return;
-  }
 
   // Last block: fold all block partials (fixed order, compensated FP32), finish in FP64.
   const uint32_t G = gridDim.x;
@@ -162,46 +149,85 @@ __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, fl
     }
   }
   __syncthreads();
-  if (tid == 0) {
-    double S[NP - 1];
-    for (int v = 0; v < NP - 1; ++v) {
-      float h = 0.0f, l = 0.0f;
-      for (int w = 0; w < NW; ++w) {
-        ff_add(h, l, s_red[w][v]);
-        l += s_redlo[w][v];
-      }
-      S[v] = (double)h + (double)l;
+  if (tid != 0) return false;
+  for (int v = 0; v < NP - 1; ++v) {
+    float h = 0.0f, l = 0.0f;
+    for (int w = 0; w < NW; ++w) {
+      ff_add(h, l, s_red[w][v]);
+      l += s_redlo[w][v];
     }
-    const uint32_t slot = n % kRing;
-    double lme, inc, ess;
-    if (Mx == -INFINITY || !(S[0] > 0.0)) {
-      lme = -INFINITY;
-      inc = -INFINITY;
-      ess = 0.0;
-    } else {
-      lme = (double)Mx + log(S[0] * (double)p.inv_N);
-      inc = lme + ((double)muf - st->mu) + mp.c_obs;
-      ess = S[0] * S[0] / ((double)p.N * S[1]);
-    }
-    p.inc_ring[slot] = inc;
-    p.ess_ring[slot] = (float)ess;
-    for (int t = 0; t < D; ++t) p.mean_ring[slot * mp.d + t] = (float)(S[2 + t] / S[0]);
-    st->loglik += inc;
-    st->mu = lme;
-    st->mu_f = (float)lme;
+    S[v] = (double)h + (double)l;
+  }
+  Mx_out = Mx;
+  return true;
+}
+
+// Writes the step's summaries from the folded sums (thread 0 of the last block):
+// likelihood increment, filter mean and ESS into the output rings, the
+// cumulative log-likelihood and the next normaliser.  Returns the ESS.
+template <int D>
+__device__ __forceinline__ double write_summaries(const StepParams& p, const double* S, float Mx, uint32_t n,
+                                                  float muf, double* lme_out = nullptr) {
+  DevState* st = p.st;
+  const ModelParams& mp = p.model;
+  const uint32_t slot = n % kRing;
+  double lme, inc, ess;
+  if (Mx == -INFINITY || !(S[0] > 0.0)) {
+    lme = -INFINITY;
+    inc = -INFINITY;
+    ess = 0.0;
+  } else {
+    lme = (double)Mx + log(S[0] * (double)p.inv_N);
+    inc = lme + ((double)muf - st->mu) + mp.c_obs;
+    ess = S[0] * S[0] / ((double)p.N * S[1]);
+  }
+  p.inc_ring[slot] = inc;
+  p.ess_ring[slot] = (float)ess;
+  for (int t = 0; t < D; ++t) p.mean_ring[slot * mp.d + t] = (float)(S[2 + t] / S[0]);
+  st->loglik += inc;
+  st->mu = lme;
+  st->mu_f = (float)lme;
+  if (lme_out) *lme_out = lme;
+  return ess;
+}
+
+// End of one launch of the one-digit or all-stages schedule.
+// ADVANCE = false (global resampling, which finishes the step in a later
+// kernel): the last block leaves n alone and instead writes the global
+// maximum log-weight and the single group's new log weight.
+template <int D, bool ADVANCE = true>
+__device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, float* accx, const Sched& sc,
+                                            uint32_t status, float muf, float* lv_single_out = nullptr) {
+  double S[2 + D];
+  float Mx;
+  if (!fold_partials<D>(p, acc, accx, status, S, Mx)) return;
+  DevState* st = p.st;
+  const uint32_t n = sc.n;
+  if (!sc.obs) {            // a later stage of the all-stages schedule: no summaries
     st->done = 0;
-    if constexpr (ADVANCE) {
-      __threadfence();
-      if (sc.mut) {
-        st->stage = 0;
-        st->n = n + 1;
-      } else {
-        st->stage = 1;
-      }
+    __threadfence();
+    if (sc.mut) {
+      st->stage = 0;
+      st->n = n + 1;
     } else {
-      st->gmax = Mx;
-      if (lv_single_out) *lv_single_out = (float)lme;   // log of the one group's mean weight
+      st->stage = st->stage + 1;
     }
+    return;
+  }
+  double lme;
+  write_summaries<D>(p, S, Mx, n, muf, &lme);
+  st->done = 0;
+  if constexpr (ADVANCE) {
+    __threadfence();
+    if (sc.mut) {
+      st->stage = 0;
+      st->n = n + 1;
+    } else {
+      st->stage = 1;
+    }
+  } else {
+    st->gmax = Mx;
+    if (lv_single_out) *lv_single_out = (float)lme;   // log of the one group's mean weight
   }
 }
 

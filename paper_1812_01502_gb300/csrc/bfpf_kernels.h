@@ -39,6 +39,14 @@ struct GlobalKernels {
 };
 bool select_global_kernels(int d, int kind, GlobalKernels& gk);
 
+// Fully adapted schedule (step_adaptive.cu): adaptive_weight_kernel(StepParams) and
+// adaptive_stage_kernel(StepParams, uint32_t j) for launch j of a step.
+struct AdaptiveKernels {
+  const void* weight;
+  const void* stage;
+};
+bool select_adaptive_kernels(int d, int kind, bool wide, AdaptiveKernels& ak);
+
 // Batched filters (batch.cu): batch_step_kernel(BatchParams), batch_init_kernel(BatchParams).
 const void* batch_step_kernel_ptr();
 const void* batch_init_kernel_ptr();

@@ -55,6 +55,10 @@ struct Plan {
   size_t smem = 0;
   bool record = false;
   uint32_t sps = 1;           // resampling stages per time step (1, or m with PF_ALL_STAGES)
+  bool adaptive = false;      // PF_ADAPTIVE: m + 1 launches per step, per-particle carried weights
+  bool rotate = false;
+  float theta = 0.5f;
+  AdaptiveKernels ak{};
   int chunk_len = 64;
   KernelSet ks{};
   ModelParams mp{};
@@ -83,6 +87,7 @@ struct pf_handle {
   uint64_t n_host = 0;     // time steps enqueued
   uint64_t n_pushed = 0;   // observations copied into the ring
   std::vector<cudaGraphExec_t> graphs;   // chunk graphs, one per radix phase (n mod m)
+  uint32_t launch_j[kMaxDigits] = {};    // stage-launch arguments of the fully adapted schedule
   std::string err;
 };
 
@@ -232,6 +237,10 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
   const int d = pl.d;
   if (m == 1 && N64 > (int64_t)kMaxCtaRadix) {
     // Global multinomial resampling (Algorithm 2) across thread blocks.
+    if (opts && (opts->flags & PF_ADAPTIVE)) {
+      msg = "PF_ADAPTIVE needs every group within one thread block (N <= 1024 when m = 1)";
+      return PF_EINVAL;
+    }
     pl.global = true;
     pl.wide = true;
     if (!select_global_kernels(d, pl.kind, pl.gk)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
@@ -296,6 +305,17 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     msg = "PF_RECORD_ANCESTORS records one stage; it cannot be combined with PF_ALL_STAGES";
     return PF_EINVAL;
   }
+  if (opts && (opts->flags & PF_ADAPTIVE)) {
+    if (opts->flags & (PF_ALL_STAGES | PF_RECORD_ANCESTORS)) {
+      msg = "PF_ADAPTIVE cannot be combined with PF_ALL_STAGES or PF_RECORD_ANCESTORS";
+      return PF_EINVAL;
+    }
+    if (!(opts->ess_threshold >= 0.0f)) { msg = "ess_threshold must be >= 0"; return PF_EINVAL; }
+    pl.adaptive = true;
+    pl.rotate = (opts->flags & PF_ROTATE) != 0;
+    pl.theta = opts->ess_threshold > 0.0f ? opts->ess_threshold : 0.5f;
+    if (!select_adaptive_kernels(d, pl.kind, pl.wide, pl.ak)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
+  }
   const bool staged = pl.sps > 1;
   // Register-resident group kernel: every radix a power of two, a_k <= 32, and the
   // groups of digit k fill whole thread-block iterations.
@@ -305,7 +325,7 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     DigitPlan& dp = pl.dp[k];
     const DigitGeom& g = pl.geom[k];
     int G = 0;
-    const void* gk = (pow2 && g.a <= 32) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged) : nullptr;
+    const void* gk = (pow2 && g.a <= 32 && !pl.adaptive) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged) : nullptr;
     if (gk && G > 0) {
       const uint32_t gpb = kBlock / G;
       const uint32_t ngroups = pl.N / g.a;
@@ -384,7 +404,7 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess && pl.global) return finish_plan_global(pl, opts, sms, msg);
-  const void* tile_kernel = pl.sps > 1 ? pl.ks.step_staged : pl.ks.step;
+  const void* tile_kernel = pl.adaptive ? pl.ak.stage : pl.sps > 1 ? pl.ks.step_staged : pl.ks.step;
   if (e == cudaSuccess)   // opt in beyond the 48 KB default whatever the size
     e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tile_kernel, kBlock, pl.smem);
@@ -415,8 +435,9 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
   L.st = take(sizeof(DevState));
   L.x = take((size_t)4 * pl.d * pl.N);
-  L.lv0 = take((size_t)4 * (pl.N / pl.min_a));
-  L.lv1 = take((size_t)4 * (pl.N / pl.min_a));
+  const size_t nlv = pl.adaptive ? pl.N : pl.N / pl.min_a;   // per particle, or per smallest group
+  L.lv0 = take((size_t)4 * nlv);
+  L.lv1 = take((size_t)4 * nlv);
   L.anc = pl.record ? take((size_t)4 * pl.N) : 0;
   L.partials = take((size_t)4 * (3 + pl.d) * grid);
   L.y_ring = take((size_t)4 * kRing * pl.dy);
@@ -435,6 +456,17 @@ cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.scan, dim3(h->plan.nscan), dim3(kBlock), args, 0, stream);
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.draw, dim3(h->plan.grid_draw), dim3(kBlock), args, 0, stream);
     return e;
+  }
+  if (h->plan.adaptive) {   // launch 0 of a step weights, launch 1 + j runs stage j
+    const Plan& pl = h->plan;
+    const uint32_t j = (uint32_t)(t % (uint64_t)(pl.m + 1));
+    if (j == 0) {
+      void* args[] = {&h->P};
+      return cudaLaunchKernel(pl.ak.weight, dim3(pl.max_grid), dim3(kBlock), args, 0, stream);
+    }
+    h->launch_j[j - 1] = j - 1;
+    void* args[] = {&h->P, &h->launch_j[j - 1]};
+    return cudaLaunchKernel(pl.ak.stage, dim3(pl.max_grid), dim3(kBlock), args, pl.smem, stream);
   }
   DigitPlan& dp = h->plan.dp[t % (uint64_t)h->plan.m];
   if (dp.group) {
@@ -523,6 +555,8 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   P.tile_cap = pl.cap;
   P.inv_N = (float)(1.0 / pl.N);
   P.sps = pl.sps;
+  P.theta = pl.theta;
+  P.rotate = pl.rotate ? 1u : 0u;
   P.model = pl.mp;
   std::memcpy(P.geom, pl.geom, sizeof(P.geom));
   if (pl.global) {
@@ -550,7 +584,8 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   };
   e = cudaMemsetAsync(h->ws + L.st, 0, sizeof(DevState), h->stream);
   if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
-  e = cudaMemsetAsync(h->ws + L.lv0, 0, pl.global ? 4 : (size_t)4 * (pl.N / pl.min_a), h->stream);
+  e = cudaMemsetAsync(h->ws + L.lv0, 0, pl.global ? 4 : (size_t)4 * (pl.adaptive ? pl.N : pl.N / pl.min_a),
+                      h->stream);
   if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
   if (pl.global) {
     e = cudaMemsetAsync(h->ws + L.flag, 0, (size_t)4 * pl.nscan, h->stream);
@@ -601,11 +636,12 @@ namespace {
 // chunk length, else individual launches.
 pf_status enqueue_steps(pf_handle* h, int32_t L) {
   const Plan& pl = h->plan;
-  const uint64_t t0 = h->n_host * pl.sps;
-  const int64_t launches = (int64_t)L * pl.sps;
+  const uint64_t lps = pl.adaptive ? (uint64_t)pl.m + 1 : pl.sps;   // launches per step
+  const uint64_t t0 = h->n_host * lps;
+  const int64_t launches = (int64_t)L * (int64_t)lps;
   if (L == pl.chunk_len && L > 1) {
     if (h->graphs.empty()) h->graphs.assign(pl.m, nullptr);
-    cudaGraphExec_t& exec = h->graphs[t0 % (uint64_t)pl.m];
+    cudaGraphExec_t& exec = h->graphs[pl.adaptive ? 0 : t0 % (uint64_t)pl.m];
     if (!exec) {
       cudaGraph_t graph = nullptr;
       PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -693,7 +729,10 @@ pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars)
   const float* xcur = pl.global ? h->GP.xbuf[st.n & 1u] : h->P.x;
   if (x) PF_CUDA(h, cudaMemcpyAsync(x, xcur, (size_t)4 * pl.d * pl.N, cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
-  if (lV) {
+  if (lV && pl.adaptive) {
+    PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[st.lvp & 1u], (size_t)4 * pl.N, cudaMemcpyDeviceToHost, h->stream));
+    PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  } else if (lV) {
     const uint64_t t = (uint64_t)st.n * pl.sps + st.stage;   // stage counter
     const int kp = (int)((t + pl.m - 1) % pl.m);
     const size_t cnt = pl.global ? 1 : pl.N / pl.geom[kp].a;
@@ -726,11 +765,23 @@ pf_status pf_get_status(const pf_handle* h, uint32_t* bits) {
   return PF_OK;
 }
 
+pf_status pf_stage_count(const pf_handle* h, uint64_t* out) {
+  if (!h || !out) return fail(h, PF_EINVAL, "NULL argument");
+  DevState st;
+  PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  *out = h->plan.adaptive ? st.nstages : (uint64_t)st.n * h->plan.sps + st.stage;
+  return PF_OK;
+}
+
 pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
   if (!h || !buf || len == 0) return fail(h, PF_EINVAL, "NULL argument");
   const Plan& pl = h->plan;
   std::string o = "{\"N\": " + std::to_string(pl.N) + ", \"d\": " + std::to_string(pl.d) +
-                  ", \"stages_per_step\": " + std::to_string(pl.sps) + ", \"digits\": [";
+                  ", \"stages_per_step\": " + std::to_string(pl.sps) +
+                  ", \"adaptive\": " + (pl.adaptive ? "true" : "false") +
+                  ", \"rotate\": " + (pl.rotate ? "true" : "false") +
+                  ", \"ess_threshold\": " + std::to_string(pl.adaptive ? pl.theta : 0.0f) + ", \"digits\": [";
   if (pl.global)
     o += "{\"a\": " + std::to_string(pl.N) + ", \"s\": 1, \"kernel\": \"global\", \"scan_tiles\": " +
          std::to_string(pl.nscan) + ", \"grid\": " + std::to_string(pl.grid_draw) + "}";

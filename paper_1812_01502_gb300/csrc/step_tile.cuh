@@ -42,7 +42,12 @@ struct TileCtx {
 
 // STAGED = false: every call weights with g_n and mutates (one stage per
 // step); STAGED = true: ctx.obs / ctx.mut decide (all stages per step).
-template <int D, int KIND, bool WIDE, bool STAGED = false>
+// ADAPT = true (fully adapted schedule): carried weights are per particle
+// (lV_in[i], lV_out[i]), the observation weight was applied by a separate
+// pass, and the partials accumulate the new stage weights V = exp(L_G - log a)
+// of every member (for the ESS after the stage) instead of the weighted
+// particles.
+template <int D, int KIND, bool WIDE, bool STAGED = false, bool ADAPT = false>
 __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, uint32_t stride,
                                            unsigned char* smem_raw, Partial& acc, float* accx,
                                            uint32_t& status) {
@@ -105,9 +110,14 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
     for (uint32_t pos = tid; pos < tn; pos += kBlock) {
       const uint32_t row = fdiv(pos, g.div_nl);
       const uint32_t i = base + row * s + (pos - row * nl);
-      const uint32_t hp = fdiv(i, g.div_prev_as);
-      const uint32_t lo = i - fdiv(i, g.div_prev_s) * g.prev_s;
-      const float lv = __ldg(lV_in + hp * g.prev_s + lo);
+      float lv;
+      if constexpr (ADAPT) {
+        lv = __ldg(lV_in + i);
+      } else {
+        const uint32_t hp = fdiv(i, g.div_prev_as);
+        const uint32_t lo = i - fdiv(i, g.div_prev_s) * g.prev_s;
+        lv = __ldg(lV_in + hp * g.prev_s + lo);
+      }
       float xv[D];
 #pragma unroll
       for (int t = 0; t < D; ++t) xv[t] = s_x[t * cap + pos];
@@ -147,8 +157,17 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
         }
         L = M + logf(s1);
       }
-      lV_out[(h0 + hh) * s + l0 + col] = L - g.log_a;
-      merge_partial<D>(acc, accx, M, s1, s2, sx);
+      if constexpr (ADAPT) {
+        const uint32_t ib = base + hh * a * s + col;       // global index of member 0
+        for (uint32_t r = 0; r < a; ++r) lV_out[ib + r * s] = L - g.log_a;
+        float zx[D];
+#pragma unroll
+        for (int t = 0; t < D; ++t) zx[t] = 0.0f;
+        merge_partial<D>(acc, accx, L, 1.0f, 1.0f / (float)a, zx);   // sum_i V_i, sum_i V_i^2 of the group
+      } else {
+        lV_out[(h0 + hh) * s + l0 + col] = L - g.log_a;
+        merge_partial<D>(acc, accx, M, s1, s2, sx);
+      }
     }
     __syncthreads();
 

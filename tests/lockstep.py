@@ -219,3 +219,52 @@ def check_step_all_stages(filt, model, radices, seed, y_n, n):
     return Report(draws=N * m, undecidable=undecidable, undecided_lines=int(np.sum(~line)),
                   max_state_err=e_x, max_logweight_err=e_lv, max_inc_err=e_inc, max_mean_err=e_mean,
                   max_ess_err=e_ess)
+
+
+def check_step_adaptive(filt, model, radices, seed, y_n, n, theta, rotate, start):
+    """GPU time step n with fully adapted resampling (PF_ADAPTIVE) against the
+    oracle's adaptive step from the same state (per-particle carried weights).
+
+    Checks the summaries, the number of stages the ESS test let run, the new
+    per-particle log-weights and the states on fully decidable lines of
+    ancestry.  An ESS within 1e-5 (relative) of theta makes the run/skip
+    decision a rounding question; such a step is reported as ambiguous and its
+    stage decisions are not compared.  Returns (Report, oracle's next start)."""
+    N = int(np.prod(radices))
+    x0, lv0, sc = filt.state()
+    assert sc["n"] == n and lv0.shape == (N,)
+    c0 = filt.stage_count()
+    mean, inc, ess = filt.step(y_n)
+    x1, lv1, sc1 = filt.state()
+    c1 = filt.stage_count()
+    st = bpf.State(x=x0.astype(np.float64), lV=lv0.astype(np.float64), mu=sc["mu"], n=n, start=start)
+    new, o = bpf.step_adaptive(model, radices, seed, st, y_n, theta, rotate, mu_used=sc["mu_used"])
+    e_inc = abs(inc - o["inc"]) / max(1.0, abs(o["inc"]))
+    e_mean = rel_err(mean, o["mean"])
+    e_ess = abs(ess - o["ess"]) / max(o["ess"], 1e-12)
+    assert e_inc <= TOL_INC, f"step {n}: likelihood increment error {e_inc}"
+    assert e_mean <= TOL_STATE, f"step {n}: mean error {e_mean}"
+    assert e_ess <= 1e-4, f"step {n}: ess error {e_ess}"
+    tested = [o["ess"]] + [bpf.ess_of(sg["lV_new"]) for sg in o["stages"]]
+    if any(abs(e - theta) <= 1e-5 * theta for e in tested):
+        return Report(ambiguous_steps=1), None
+    assert c1 - c0 == len(o["stages"]), f"step {n}: GPU ran {c1 - c0} stages, oracle {len(o['stages'])}"
+    strides = butterfly.strides(radices)
+    line = np.ones(N, dtype=bool)
+    undecidable = 0
+    for sg in o["stages"]:
+        k = sg["k"]
+        a, s = int(radices[k]), strides[k]
+        H = N // (a * s)
+        lo, hi = plausible_members(sg["q"].reshape(H, a, s), sg["u"].reshape(H, a, s), axis=1)
+        dec = (lo == hi).reshape(N)
+        undecidable += int(np.sum(~dec))
+        line = dec & line[sg["anc"]]
+    e_x = rel_err(x1[line], new.x[line])
+    e_lv = rel_err(lv1, o["lV_new"])
+    assert e_x <= TOL_STATE, f"step {n}: state error {e_x}"
+    assert e_lv <= TOL_STATE, f"step {n}: log-weight error {e_lv}"
+    assert abs(sc1["mu"] - new.mu) <= 1e-6 * max(1.0, abs(new.mu))
+    return Report(draws=N * len(o["stages"]), stages=len(o["stages"]), undecidable=undecidable,
+                  undecided_lines=int(np.sum(~line)), max_state_err=e_x, max_logweight_err=e_lv,
+                  max_inc_err=e_inc, max_mean_err=e_mean, max_ess_err=e_ess), new.start
