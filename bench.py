@@ -56,6 +56,8 @@ def _args():
     p.add_argument("--no-serving", action="store_true", help="skip the serving leg")
     p.add_argument("--serving-requests", type=int, default=160)
     p.add_argument("--serving-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
+    p.add_argument("--no-paper", action="store_true", help="skip the Section 6.1 random-walk leg")
+    p.add_argument("--no-schedules", action="store_true", help="skip the all-stages / adaptive leg")
     p.add_argument("--oracle-rate", action="store_true", help=argparse.SUPPRESS)
     p.add_argument("--oracle-n", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--oracle-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
@@ -372,6 +374,122 @@ def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
             "butterfly_ms_per_step": t_b, "global_ms_per_step_at_equal_mse": t_g,
             "speedup_at_equal_error": t_g / t_b}
 
+def _random_walk_kalman_means(y, obs_var):
+    """Kalman filtering means E[X_n | y_0..n] of the random walk X_n = X_{n-1} + N(0, I),
+    Y_n = X_n + N(0, obs_var I), X_0 ~ N(0, I): every coordinate shares one scalar
+    variance recursion (measurement reference only)."""
+    import numpy as np
+    T, d = y.shape
+    out = np.empty((T, d))
+    mean = np.zeros(d)
+    P = 1.0
+    for n in range(T):
+        if n > 0:
+            P = P + 1.0
+        K = P / (P + obs_var)
+        mean = mean + K * (y[n] - mean)
+        P = (1.0 - K) * P
+        out[n] = mean
+    return out
+
+
+def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
+    """Section 6.1's experiment on this GPU: the d = 7 Gaussian random walk with
+    R = I/4 over 8000 observations; filter-mean MSE against the Kalman mean
+    (sum over steps and components, mean over J runs) and time per step, for
+    the one-digit schedule, all stages per step, fully adapted resampling at
+    several thresholds (with and without the rotated start) and the global
+    filter.  Times are whole-run device times through pf_run (CUDA graphs)."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    w = S.workload("rw7d_paper")
+    y = w.observations()
+    kal = _random_walk_kalman_means(y, 0.25)
+    raw = float(np.sum((y - kal) ** 2))
+    yd = torch.tensor(y.astype(np.float32), device=dev)
+    scheds = [("one_digit", {}), ("all_stages", {"all_stages": True})]
+    for th in (0.2, 0.5, 0.8):
+        scheds.append((f"adaptive_{th}", {"adaptive": True, "ess_threshold": th}))
+    scheds.append(("adaptive_rot_0.5", {"adaptive": True, "ess_threshold": 0.5, "rotate": True}))
+    scheds.append(("global", None))
+    curves = []
+    for name, kw in scheds:
+        for N in Ns:
+            rad = (N,) if kw is None else _radix16(N)
+            if kw is not None and kw.get("adaptive") and len(rad) == 1 and N > 1024:
+                continue
+            mses, ts, stages = [], [], []
+            for j in range(J):
+                f = bf.ButterflyFilter(w.model, N, rad, w.filter_seed + 7919 * j + N % 101, device=dev,
+                                       chunk_len=250, **(kw or {}))
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record(f.stream)
+                r = f.run(yd)
+                e1.record(f.stream)
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1) / len(y))
+                mses.append(float(np.sum((r["mean"].double().cpu().numpy() - kal) ** 2)))
+                stages.append(f.stage_count() / len(y))
+                f.close()
+            curves.append({"schedule": name, "N": N, "radices": list(rad), "mse": float(np.mean(mses)),
+                           "mse_runs": mses, "ms_per_step": float(np.median(ts)),
+                           "stages_per_step": float(np.mean(stages))})
+    return {"model": "random walk d=7, Q=I, R=I/4, X_0~N(0,I)", "T": len(y), "runs": J,
+            "mse": "sum over steps and components of (filter mean - Kalman mean)^2, mean over runs",
+            "raw_observation_mse": raw, "curves": curves}
+
+
+def schedules_leg(bf, w, dev, flush, K=30, W=3):
+    """The paper's schedules on the main workload at full size: all stages per
+    step and fully adapted resampling (theta = 0.5, and theta > 1, which runs
+    every stage), L2 flushed before every timed step.  Algorithmic bytes per
+    step: every stage launch reads and writes the states and its carried
+    weights (compact per group; per particle in the adaptive schedule, whose
+    weight pass reads the states and weights and writes the weights, and whose
+    last launch still reads and writes the states when it was skipped)."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    y = S.simulate(w.model, W + K, w.data_seed)[1].astype(np.float32)
+    yd = torch.tensor(y, device=dev)
+    d, N, m = w.model.d, w.N, len(w.radices)
+    out = {}
+    for name, kw in (("all_stages", {"all_stages": True}),
+                     ("adaptive_0.5", {"adaptive": True, "ess_threshold": 0.5}),
+                     ("adaptive_all", {"adaptive": True, "ess_threshold": 1.5})):
+        f = bf.ButterflyFilter(w.model, N, w.radices, w.filter_seed, device=dev, **kw)
+        f.push(yd)
+        ms, nbytes, nst = [], [], []
+        with torch.cuda.stream(f.stream):
+            for j in range(W + K):
+                c0 = f.stage_count()
+                flush.zero_()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(f.stream)
+                f.advance(1)
+                e1.record(f.stream)
+                torch.cuda.synchronize(dev)
+                if j < W:
+                    continue
+                sj = f.stage_count() - c0
+                ms.append(e0.elapsed_time(e1))
+                nst.append(sj)
+                if kw.get("adaptive"):
+                    nbytes.append((4 * d + 8) * N + sj * (8 * d + 8) * N + (8 * d * N if sj < m else 0))
+                else:
+                    nbytes.append(sum(algorithmic_bytes(w, k) for k in range(m)))
+        f.close()
+        t = float(np.mean(ms))
+        out[name] = {"ms_per_step": t, "p99_ms": float(np.percentile(ms, 99)), "steps": K,
+                     "stages_per_step": float(np.mean(nst)),
+                     "launches_per_step": m + 1 if kw.get("adaptive") else m,
+                     "particle_steps_per_s": N / (t * 1e-3),
+                     "hbm_gbs_algorithmic": float(np.sum(nbytes)) / (float(np.sum(ms)) * 1e-3) / 1e9}
+    return out
+
+
 def ours_main(a):
     import numpy as np
     import torch
@@ -473,6 +591,12 @@ def ours_main(a):
     serving = None
     if not a.no_serving and rank == 0:
         serving = serving_leg(dev, a.serving_requests, a.serving_rate)
+    paper = None
+    if not a.no_paper and rank == 0:
+        paper = paper_workload_leg(bf, dev)
+    scheds = None
+    if not a.no_schedules and rank == 0:
+        scheds = schedules_leg(bf, w, dev, flush)
 
     if world > 1:
         t = torch.tensor([total_ms, e2e_s, resident_ms], device=dev, dtype=torch.float64)
@@ -525,6 +649,8 @@ def ours_main(a):
         "equal_error": eq,
         "batched": batched,
         "serving": serving,
+        "paper_workload": paper,
+        "schedules": scheds,
     }
     print(json.dumps(line))
     filt.close()
