@@ -226,6 +226,73 @@ def step_adaptive(model, radices: Sequence[int], seed: int, st: State, y_n: np.n
     return new, dict(stages=stages, inc=inc, mean=mean, ess=ess, ess_final=e, lV_new=cur, c=c_n)
 
 
+def island_stages(lW: np.ndarray, seed: int, n: int, modified: bool = True):
+    """Augmented island resampling (Algorithm 6; Algorithm 7 when ``modified``) on the
+    log island weights lW (m = 2^S islands).  Stage s = 1..S pairs island i with
+    i xor 2^(s-1) (matrices bold-A_s); both members of a pair get the pair's mean
+    weight, and each island draws, by the integer rule on the pair's two weights
+    with its own uniform (island_words_at(seed, n, s, i)), the island whose whole
+    sample it holds next.  Algorithm 7 undoes a draw in which the two islands
+    would merely swap their samples.  Returns (holder, lW_final, per-stage info):
+    holder[i] = the island whose input sample island i ends up holding."""
+    m = len(lW)
+    S = int(np.log2(m))
+    if 1 << S != m:
+        raise ValueError("the number of islands must be a power of two")
+    V = np.asarray(lW, dtype=np.float64).copy()
+    holder = np.arange(m)
+    info = []
+    for s in range(1, S + 1):
+        b = 1 << (s - 1)
+        H = m // (2 * b)
+        Vr = V.reshape(H, 2, b)
+        q = resample.quantise(Vr, axis=1)
+        Q = np.sum(q, axis=1, keepdims=True, dtype=np.uint64)
+        u = resample.scaled_uniform(philox.island_words_at(seed, n, s, np.arange(m)).reshape(H, 2, b), Q, 2)
+        member = resample.draw(q, u, axis=1)
+        member = np.where(Q == 0, np.arange(2)[None, :, None], member)   # an all-zero pair keeps its samples
+        swapped = np.zeros((H, 1, b), dtype=bool)
+        if modified:
+            swapped = ((member[:, 0, :] == 1) & (member[:, 1, :] == 0))[:, None, :]
+            member = np.where(swapped, np.arange(2)[None, :, None], member)
+        h_idx = np.arange(H)[:, None, None]
+        l_idx = np.arange(b)[None, None, :]
+        c = (h_idx * 2 * b + member * b + l_idx).reshape(m)
+        Mx = np.max(Vr, axis=1, keepdims=True)
+        with np.errstate(invalid="ignore", divide="ignore"):
+            Lp = Mx + np.log(np.sum(np.exp(Vr - Mx), axis=1, keepdims=True)) - np.log(2.0)
+        V = np.broadcast_to(Lp, Vr.shape).reshape(m).copy()
+        holder = holder[c]
+        info.append(dict(s=s, q=q.reshape(m), u=u.reshape(m), choice=c, swaps_undone=int(np.sum(swapped))))
+    return holder, V, info
+
+
+def step_islands(model, M: int, m: int, seed: int, st: State, y_n: np.ndarray, modified: bool = True,
+                 mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
+    """One time step of AIRPF (Algorithm 4): N = M m particles in m islands of M
+    consecutive particles.  Weight with g_n; within-island multinomial resampling
+    (Algorithm 5: the stage on digit 0 of radices (M, m), island weight = mean g of
+    the island, eq. (out weight)), drawn with stage counter t = 2n; augmented island
+    resampling (Algorithm 6 / 7) over S = log2 m stages; every particle of island i
+    takes the particle at the same place in the sample island i holds; mutation
+    (normals numbered by the particle index).  Afterwards all weights are equal."""
+    N = M * m
+    radices = (M, m)
+    n = st.n
+    mu_sub = st.mu if mu_used is None else float(mu_used)
+    lw, c_n = weigh(model, st.x, st.lV, mu_sub, y_n)
+    inc, mean, ess, lme = summaries(lw, st.x, c_n, mu_sub, st.mu)
+    x1, lV1, anc1, q1, u1, _ = stage(radices, seed, st.x, lw, 0, 2 * n)
+    lW = lV1[::M]
+    holder, V, info = island_stages(lW, seed, n, modified)
+    src = (holder[np.arange(N) // M] * M + np.arange(N) % M)
+    x_hat = x1[src]
+    x_next = mutate(model, x_hat, n, seed, idx=np.arange(N))
+    new = State(x=x_next, lV=np.full(N, V[0]), mu=lme, n=n + 1, loglik=st.loglik + inc)
+    return new, dict(inc=inc, mean=mean, ess=ess, within=dict(anc=anc1, q=q1, u=u1, lV=lV1), holder=holder,
+                     island_info=info, lW=lW, lW_final=V, x_within=x1, c=c_n)
+
+
 def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
          mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
     """One time step n = st.n: weight, one augmented-resampling stage, mutate.
@@ -281,7 +348,7 @@ def step(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
 
 def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
         keep_ancestors: bool = False, all_stages: bool = False, theta: Optional[float] = None,
-        rotate: bool = False) -> Dict[str, np.ndarray]:
+        rotate: bool = False, islands: Optional[str] = None) -> Dict[str, np.ndarray]:
     """Run the filter over y[0:T].  Returns per-step inc, mean, ess and the final loglik.
     all_stages: the paper's schedule (all m stages per time step) instead of one digit;
     theta: fully adapted resampling with ESS threshold theta (optionally rotated)."""
@@ -296,13 +363,15 @@ def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
     ancs = [] if keep_ancestors else None
     executed = 0
     for t in range(T):
-        if theta is not None:
+        if islands is not None:      # "modified" (Algorithm 7) or "plain" (Algorithm 6); radices = (M, m)
+            st, o = step_islands(model, radices[0], radices[1], seed, st, y[t], islands == "modified")
+        elif theta is not None:
             st, o = step_adaptive(model, radices, seed, st, y[t], theta, rotate)
             executed += len(o["stages"])
         else:
             st, o = (step_all_stages if all_stages else step)(model, radices, seed, st, y[t])
         incs[t], means[t], ess[t] = o["inc"], o["mean"], o["ess"]
-        if keep_ancestors and not all_stages and theta is None:
+        if keep_ancestors and not all_stages and theta is None and islands is None:
             ancs.append(o["anc"])
     out = dict(inc=incs, mean=means, ess=ess, loglik=st.loglik, state=st, stages_executed=executed)
     if keep_ancestors:

@@ -48,6 +48,7 @@ PURPOSE_INIT = 0
 PURPOSE_PROPAGATE = 1
 PURPOSE_RESAMPLE = 2
 PURPOSE_RESAMPLE_WIDE = 3
+PURPOSE_ISLAND = 4
 
 
 def philox4x32(c0, c1, c2, c3, key, rounds: int = 10):
@@ -145,3 +146,11 @@ def resample_words_wide_at(seed: int, n: int, idx):
     lo = np.where(odd, w2, w0).astype(np.uint64)
     hi = np.where(odd, w3, w1).astype(np.uint64)
     return lo, hi
+
+
+def island_words_at(seed: int, n: int, stage: int, idx) -> np.ndarray:
+    """32-bit uniforms of islands ``idx`` at island-resampling stage ``stage`` of time n:
+    counter (i / 4, n, PURPOSE_ISLAND, stage), word i mod 4."""
+    idx = np.asarray(idx, dtype=np.uint64)
+    w = philox4x32(idx >> np.uint64(2), n, PURPOSE_ISLAND, stage, seed_key(seed))
+    return np.choose((idx & np.uint64(3)).astype(np.int64), w).astype(np.uint64)
