@@ -104,11 +104,24 @@ typedef struct {
 /* With PF_ADAPTIVE: start each step's stages one digit after the last stage
  * executed (the rotation proposed in Section 6.4) instead of at digit 0. */
 #define PF_ROTATE 8u
+/* Augmented island resampling particle filter (AIRPF, Algorithm 4) with the
+ * modified island resampling of Algorithm 7: radices must be (M, m) -- m =
+ * 2^S islands of M consecutive particles (2 <= M <= 1024, 2 <= m <= 16384,
+ * m a power of two).  Each step weights with g_n, resamples multinomially
+ * within every island (Algorithm 5; island weight = mean g of the island),
+ * runs the S stages of augmented island resampling on the island weights
+ * (whole islands are copied; a draw in which two paired islands would only
+ * swap their samples is undone), then mutates.  3 kernel launches per step.
+ * Cannot be combined with the other schedule flags or PF_RECORD_ANCESTORS. */
+#define PF_ISLANDS 16u
+/* With PF_ISLANDS: island resampling as in Algorithm 6 (swaps are kept). */
+#define PF_ISLANDS_PLAIN 32u
 
 typedef struct {
     int32_t tile;        /* target particles per thread-block tile; 0 = automatic            */
     int32_t chunk_len;   /* time steps per CUDA-graph replay in pf_run; 0 = 64 (max 1024)    */
-    uint32_t flags;      /* PF_RECORD_ANCESTORS | PF_ALL_STAGES | PF_ADAPTIVE | PF_ROTATE     */
+    uint32_t flags;      /* PF_RECORD_ANCESTORS | PF_ALL_STAGES | PF_ADAPTIVE | PF_ROTATE |  */
+                         /* PF_ISLANDS | PF_ISLANDS_PLAIN                                    */
     int32_t grid;        /* persistent thread blocks; 0 = automatic (SMs x occupancy)        */
     void* stream;        /* cudaStream_t to run on; NULL = the legacy default stream          */
     float ess_threshold; /* PF_ADAPTIVE: a stage runs while ESS < ess_threshold; 0 = 0.5.     */

@@ -32,6 +32,8 @@ PF_RECORD_ANCESTORS = 1
 PF_ALL_STAGES = 2
 PF_ADAPTIVE = 4
 PF_ROTATE = 8
+PF_ISLANDS = 16
+PF_ISLANDS_PLAIN = 32
 STATUS_NAMES = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",
                 PF_ETIMEOUT: "PF_ETIMEOUT", PF_ESTATE: "PF_ESTATE"}
 
@@ -153,6 +155,8 @@ class ButterflyFilter:
     (digits 0..m-1 in turn; m launches per step).  adaptive=True is fully
     adapted augmented resampling: stages run while the ESS is below
     ``ess_threshold`` (optionally from a rotated start, ``rotate``).
+    islands="modified" (or "plain") is AIRPF with radices (M, m): m islands of
+    M particles, island resampling by Algorithm 7 (or 6).
     radices = (N,) is the global-resampling bootstrap filter (Algorithm 1 + 2).
     The workspace is a torch uint8 tensor on ``device``; work runs on the
     current torch stream of that device unless ``stream`` is given.
@@ -161,7 +165,8 @@ class ButterflyFilter:
     def __init__(self, model, N: int, radices: Sequence[int], seed: int, *, tile: int = 0,
                  chunk_len: int = 0, record_ancestors: bool = False, grid: int = 0,
                  device=None, stream=None, tune: bool = False, all_stages: bool = False,
-                 adaptive: bool = False, ess_threshold: float = 0.5, rotate: bool = False):
+                 adaptive: bool = False, ess_threshold: float = 0.5, rotate: bool = False,
+                 islands: Optional[str] = None):
         torch = _torch()
         lib = load_library()
         if not torch.cuda.is_available():
@@ -183,12 +188,15 @@ class ButterflyFilter:
         self._opts = PFOptions(tile=int(tile), chunk_len=int(chunk_len),
                                flags=(PF_RECORD_ANCESTORS if record_ancestors else 0)
                                | (PF_ALL_STAGES if all_stages else 0) | (PF_ADAPTIVE if adaptive else 0)
-                               | (PF_ROTATE if rotate else 0), grid=int(grid),
+                               | (PF_ROTATE if rotate else 0)
+                               | (PF_ISLANDS if islands else 0) | (PF_ISLANDS_PLAIN if islands == "plain" else 0),
+                               grid=int(grid),
                                stream=ctypes.c_void_p(self.stream.cuda_stream),
                                ess_threshold=float(ess_threshold) if adaptive else 0.0)
         self.record_ancestors = record_ancestors
         self.all_stages = bool(all_stages)
         self.adaptive = bool(adaptive)
+        self.islands = islands
         with torch.cuda.device(self.device):
             nbytes = ctypes.c_size_t(0)
             _check(lib.pf_workspace_size(ctypes.byref(self._pm), self.N, self._rad, self.m,
@@ -292,7 +300,7 @@ class ButterflyFilter:
 
     def state(self):
         """(x (N, d) float32, lV (N / a_prev,) float32, dict(n, loglik, mu, mu_used))."""
-        t = self.steps * (self.m if self.all_stages else 1)    # stages run so far
+        t = self.steps * (self.m if (self.all_stages or self.islands) else 1)    # stage counter
         kp = (t - 1) % self.m
         x = np.empty((self.d, self.N), dtype=np.float32)
         lv = np.empty(self.N if self.adaptive else self.N // self.radices[kp], dtype=np.float32)

@@ -35,6 +35,7 @@ constexpr uint32_t kPurposeInit = 0;
 constexpr uint32_t kPurposePropagate = 1;
 constexpr uint32_t kPurposeResample = 2;
 constexpr uint32_t kPurposeResampleWide = 3;
+constexpr uint32_t kPurposeIsland = 4;       // island-level draws of augmented island resampling
 
 constexpr uint32_t kStatusNonFinite = 1u;
 constexpr uint32_t kStatusZeroGroup = 2u;
@@ -301,6 +302,18 @@ struct GlobalParams {
   uint32_t* flag;                 // [nscan] 2n+1: aggregate ready, 2n+2: prefix ready (step n)
   uint32_t nscan;                 // scan tiles of kScanTile particles
   uint32_t ntop, top_shift;
+};
+
+// Augmented island resampling (AIRPF): islands of M consecutive particles.
+constexpr int kIslandThreads = 1024;
+constexpr uint32_t kMaxIslands = 16384;   // island weights and holders fit in shared memory
+struct IslandParams {
+  float* x_out;         // [d][N] states after the island gather and the mutation
+  int32_t* src;         // [islands] island whose sample island i holds after the island stages
+  const float* lW;      // [islands] log island weights from the within-island stage
+  float* lV_next;       // [M] carried log weights of the next step (all equal)
+  uint32_t M, islands, S;
+  uint32_t plain;       // 1: Algorithm 6 as printed (no undoing of swaps)
 };
 
 constexpr int kScanItems = 16;

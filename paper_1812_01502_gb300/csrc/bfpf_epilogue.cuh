@@ -191,6 +191,21 @@ __device__ __forceinline__ double write_summaries(const StepParams& p, const dou
   return ess;
 }
 
+// Last-block-done without partial sums: the last thread block of a launch to
+// get here returns true in its thread 0 (the block counter is left for the
+// caller to reset).
+__device__ __forceinline__ bool last_block_done(DevState* st) {
+  __shared__ uint32_t s_last_blk;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    const uint32_t prev = atomicAdd(&st->done, 1u);
+    s_last_blk = (prev == gridDim.x - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  return s_last_blk && threadIdx.x == 0;
+}
+
 // End of one launch of the one-digit or all-stages schedule.
 // ADVANCE = false (global resampling, which finishes the step in a later
 // kernel): the last block leaves n alone and instead writes the global

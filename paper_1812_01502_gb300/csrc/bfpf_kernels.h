@@ -47,6 +47,15 @@ struct AdaptiveKernels {
 };
 bool select_adaptive_kernels(int d, int kind, bool wide, AdaptiveKernels& ak);
 
+// AIRPF (step_islands.cu): island_stages_kernel(StepParams, IslandParams), one block of
+// kIslandThreads threads with 8 * islands bytes of shared memory, and
+// island_gather_kernel(StepParams, IslandParams).
+struct IslandKernels {
+  const void* stages;
+  const void* gather;
+};
+bool select_island_kernels(int d, int kind, IslandKernels& ik);
+
 // Batched filters (batch.cu): batch_step_kernel(BatchParams), batch_init_kernel(BatchParams).
 const void* batch_step_kernel_ptr();
 const void* batch_init_kernel_ptr();

@@ -31,7 +31,8 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t st, x, lv0, lv1, anc, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
-  size_t x2, lw, P, top, agg, incl, flag;   // global resampling only
+  size_t x2, lw, P, top, agg, incl, flag;   // global resampling only (x2: also AIRPF)
+  size_t src;                               // AIRPF: island sources
 };
 
 // The kernel that runs the steps on one digit.
@@ -59,6 +60,9 @@ struct Plan {
   bool rotate = false;
   float theta = 0.5f;
   AdaptiveKernels ak{};
+  bool islands = false;       // PF_ISLANDS: radices (M, m), 3 launches per step
+  bool island_plain = false;
+  IslandKernels ik{};
   int chunk_len = 64;
   KernelSet ks{};
   ModelParams mp{};
@@ -88,6 +92,8 @@ struct pf_handle {
   uint64_t n_pushed = 0;   // observations copied into the ring
   std::vector<cudaGraphExec_t> graphs;   // chunk graphs, one per radix phase (n mod m)
   uint32_t launch_j[kMaxDigits] = {};    // stage-launch arguments of the fully adapted schedule
+  StepParams Pisl[2]{};                  // AIRPF: step parameters by step parity (states ping-pong)
+  IslandParams ipar[2]{};
   std::string err;
 };
 
@@ -222,14 +228,28 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
   if (N64 < 2 || N64 >= (int64_t(1) << 31)) { msg = "need 2 <= N < 2^31"; return PF_EINVAL; }
   int64_t prod = 1;
   pl.min_a = 0xffffffffu;
+  // AIRPF: digit 1 counts the islands and is never run by the stage kernels
+  pl.islands = opts && (opts->flags & PF_ISLANDS);
+  pl.island_plain = pl.islands && (opts->flags & PF_ISLANDS_PLAIN);
+  if (pl.islands) {
+    if (opts->flags & (PF_ALL_STAGES | PF_ADAPTIVE | PF_RECORD_ANCESTORS)) {
+      msg = "PF_ISLANDS cannot be combined with PF_ALL_STAGES, PF_ADAPTIVE or PF_RECORD_ANCESTORS";
+      return PF_EINVAL;
+    }
+    if (m != 2 || radices[1] < 2 || radices[1] > (int64_t)kMaxIslands || (radices[1] & (radices[1] - 1))) {
+      msg = "PF_ISLANDS needs radices (M, m) with m a power of two, 2 <= m <= 16384";
+      return PF_EINVAL;
+    }
+  }
   for (int k = 0; k < m; ++k) {
     const int64_t a = radices[k];
+    const bool run = !(pl.islands && k == 1);
     if (a < 2) { msg = "every radix must be >= 2"; return PF_EINVAL; }
-    if (m > 1 && a > (int64_t)kMaxCtaRadix) { msg = "radices must be <= 1024 when m > 1"; return PF_EINVAL; }
+    if (run && m > 1 && a > (int64_t)kMaxCtaRadix) { msg = "radices must be <= 1024 when m > 1"; return PF_EINVAL; }
     prod *= a;
     if (prod > N64) break;
     pl.min_a = std::min<uint32_t>(pl.min_a, (uint32_t)a);
-    if (a > (int64_t)kNarrowMaxRadix) pl.wide = true;
+    if (run && a > (int64_t)kNarrowMaxRadix) pl.wide = true;
   }
   if (prod != N64) { msg = "the product of the radices must equal N"; return PF_EINVAL; }
   pl.N = (uint32_t)N64;
@@ -288,8 +308,10 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     g.div_nl = make_fastdiv(g.nl);
     g.div_a = make_fastdiv(a);
     g.div_tiles_l = make_fastdiv(g.tiles_l);
-    pl.cap = std::max(pl.cap, g.tile_n);
-    pl.max_tiles = std::max(pl.max_tiles, g.ntiles);
+    if (!(pl.islands && k == 1)) {
+      pl.cap = std::max(pl.cap, g.tile_n);
+      pl.max_tiles = std::max(pl.max_tiles, g.ntiles);
+    }
     s *= a;
   }
   for (int k = 0; k < m; ++k) {
@@ -301,6 +323,10 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
   }
   for (int k = 0; k < m; ++k) pl.geom[k].div_tgroups = make_fastdiv(pl.geom[k].nh * pl.geom[k].nl);
   pl.sps = (opts && (opts->flags & PF_ALL_STAGES)) ? (uint32_t)m : 1u;
+  if (pl.islands) {           // the within-island stage is stage 0 of a two-stage step
+    pl.sps = 2;
+    if (!select_island_kernels(d, pl.kind, pl.ik)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
+  }
   if (pl.sps > 1 && opts && (opts->flags & PF_RECORD_ANCESTORS)) {
     msg = "PF_RECORD_ANCESTORS records one stage; it cannot be combined with PF_ALL_STAGES";
     return PF_EINVAL;
@@ -444,6 +470,13 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   L.inc_ring = take((size_t)8 * kRing);
   L.mean_ring = take((size_t)4 * kRing * pl.d);
   L.ess_ring = take((size_t)4 * kRing);
+  if (pl.islands) {
+    L.x2 = take((size_t)4 * pl.d * pl.N);
+    L.src = take((size_t)4 * pl.geom[1].a);
+    const int smem_isl = (int)(8 * pl.geom[1].a);
+    e = cudaFuncSetAttribute(pl.ik.stages, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_isl);
+    if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
+  }
   L.total = off;
   return PF_OK;
 }
@@ -456,6 +489,24 @@ cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.scan, dim3(h->plan.nscan), dim3(kBlock), args, 0, stream);
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.draw, dim3(h->plan.grid_draw), dim3(kBlock), args, 0, stream);
     return e;
+  }
+  if (h->plan.islands) {    // within-island stage, island stages, gather + mutation
+    const Plan& pl = h->plan;
+    const uint64_t n = t / 3;
+    const uint32_t j = (uint32_t)(t % 3), par = (uint32_t)(n & 1u);
+    if (j == 0) {
+      const DigitPlan& dp = pl.dp[0];
+      if (dp.group) {
+        void* args[] = {&h->Pisl[par], const_cast<GroupGeom*>(&dp.gg)};
+        return cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, 0, stream);
+      }
+      void* args[] = {&h->Pisl[par]};
+      return cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, dp.smem, stream);
+    }
+    void* args[] = {&h->Pisl[par], &h->ipar[par]};
+    if (j == 1)
+      return cudaLaunchKernel(pl.ik.stages, dim3(1), dim3(kIslandThreads), args, (size_t)8 * pl.geom[1].a, stream);
+    return cudaLaunchKernel(pl.ik.gather, dim3(pl.max_grid), dim3(kBlock), args, 0, stream);
   }
   if (h->plan.adaptive) {   // launch 0 of a step weights, launch 1 + j runs stage j
     const Plan& pl = h->plan;
@@ -559,6 +610,24 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   P.rotate = pl.rotate ? 1u : 0u;
   P.model = pl.mp;
   std::memcpy(P.geom, pl.geom, sizeof(P.geom));
+  if (pl.islands) {
+    float* xb[2] = {P.x, reinterpret_cast<float*>(h->ws + L.x2)};
+    for (int par = 0; par < 2; ++par) {
+      h->Pisl[par] = P;
+      h->Pisl[par].x = xb[par];
+      IslandParams& ip = h->ipar[par];
+      ip.x_out = xb[par ^ 1];
+      ip.src = reinterpret_cast<int32_t*>(h->ws + L.src);
+      ip.lW = P.lV[1];          // the within-island stage (stage counter 2n) writes lV[1]
+      ip.lV_next = P.lV[0];     // and reads lV[0]
+      ip.M = pl.geom[0].a;
+      ip.islands = pl.geom[1].a;
+      uint32_t S = 0;
+      while ((1u << S) < ip.islands) ++S;
+      ip.S = S;
+      ip.plain = pl.island_plain ? 1u : 0u;
+    }
+  }
   if (pl.global) {
     GlobalParams& G = h->GP;
     G.xbuf[0] = P.x;
@@ -636,12 +705,12 @@ namespace {
 // chunk length, else individual launches.
 pf_status enqueue_steps(pf_handle* h, int32_t L) {
   const Plan& pl = h->plan;
-  const uint64_t lps = pl.adaptive ? (uint64_t)pl.m + 1 : pl.sps;   // launches per step
+  const uint64_t lps = pl.islands ? 3 : pl.adaptive ? (uint64_t)pl.m + 1 : pl.sps;   // launches per step
   const uint64_t t0 = h->n_host * lps;
   const int64_t launches = (int64_t)L * (int64_t)lps;
   if (L == pl.chunk_len && L > 1) {
     if (h->graphs.empty()) h->graphs.assign(pl.m, nullptr);
-    cudaGraphExec_t& exec = h->graphs[pl.adaptive ? 0 : t0 % (uint64_t)pl.m];
+    cudaGraphExec_t& exec = h->graphs[pl.islands ? h->n_host & 1u : pl.adaptive ? 0 : t0 % (uint64_t)pl.m];
     if (!exec) {
       cudaGraph_t graph = nullptr;
       PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -726,7 +795,7 @@ pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars)
   DevState st;
   PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
-  const float* xcur = pl.global ? h->GP.xbuf[st.n & 1u] : h->P.x;
+  const float* xcur = pl.global ? h->GP.xbuf[st.n & 1u] : pl.islands ? h->Pisl[st.n & 1u].x : h->P.x;
   if (x) PF_CUDA(h, cudaMemcpyAsync(x, xcur, (size_t)4 * pl.d * pl.N, cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   if (lV && pl.adaptive) {
@@ -781,7 +850,10 @@ pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
                   ", \"stages_per_step\": " + std::to_string(pl.sps) +
                   ", \"adaptive\": " + (pl.adaptive ? "true" : "false") +
                   ", \"rotate\": " + (pl.rotate ? "true" : "false") +
-                  ", \"ess_threshold\": " + std::to_string(pl.adaptive ? pl.theta : 0.0f) + ", \"digits\": [";
+                  ", \"ess_threshold\": " + std::to_string(pl.adaptive ? pl.theta : 0.0f) +
+                  ", \"islands\": " + std::to_string(pl.islands ? pl.geom[1].a : 0) +
+                  ", \"island_resampling\": \"" + (pl.islands ? (pl.island_plain ? "algorithm6" : "algorithm7") : "") +
+                  "\", \"digits\": [";
   if (pl.global)
     o += "{\"a\": " + std::to_string(pl.N) + ", \"s\": 1, \"kernel\": \"global\", \"scan_tiles\": " +
          std::to_string(pl.nscan) + ", \"grid\": " + std::to_string(pl.grid_draw) + "}";

@@ -28,19 +28,6 @@ namespace bfpf {
 
 namespace {
 
-// The last thread block of a launch to get here returns true (in thread 0).
-__device__ __forceinline__ bool last_block_arrives(DevState* st) {
-  __shared__ uint32_t s_last;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const uint32_t prev = atomicAdd(&st->done, 1u);
-    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  return s_last && threadIdx.x == 0;
-}
-
 // End of a time step (thread 0 of the last block of launch m).
 __device__ __forceinline__ void end_step(const StepParams& p, DevState* st, uint32_t n) {
   if (p.rotate && st->last_k >= 0) st->start = ((uint32_t)st->last_k + 1u) % (uint32_t)p.m;
@@ -119,7 +106,7 @@ __global__ void __launch_bounds__(kBlock) adaptive_stage_kernel(const __grid_con
 #pragma unroll
       for (int t = 0; t < D; ++t) __stcs(p.x + (size_t)t * p.N + i, xo[t]);
     }
-    if (last_block_arrives(st)) end_step(p, st, n);
+    if (last_block_done(st)) end_step(p, st, n);
     return;
   }
   const uint32_t lvp = st->lvp;

@@ -268,3 +268,50 @@ def check_step_adaptive(filt, model, radices, seed, y_n, n, theta, rotate, start
     return Report(draws=N * len(o["stages"]), stages=len(o["stages"]), undecidable=undecidable,
                   undecided_lines=int(np.sum(~line)), max_state_err=e_x, max_logweight_err=e_lv,
                   max_inc_err=e_inc, max_mean_err=e_mean, max_ess_err=e_ess), new.start
+
+
+def check_step_islands(filt, model, M, m, seed, y_n, n, modified):
+    """GPU AIRPF step n (PF_ISLANDS) against the oracle's AIRPF step from the same
+    state.  A particle's new state must match when its within-island draw and
+    every island-stage draw on its island's line of holders is decidable (with
+    Algorithm 7 an island's choice also depends on its partner's draw)."""
+    N = M * m
+    x0, lv0, sc = filt.state()
+    assert sc["n"] == n
+    mean, inc, ess = filt.step(y_n)
+    x1, lv1, sc1 = filt.state()
+    lV = per_particle_lV(lv0, (M, m), 2 * n).astype(np.float64)
+    st = bpf.State(x=x0.astype(np.float64), lV=lV, mu=sc["mu"], n=n)
+    new, o = bpf.step_islands(model, M, m, seed, st, y_n, modified, mu_used=sc["mu_used"])
+    e_inc = abs(inc - o["inc"]) / max(1.0, abs(o["inc"]))
+    e_mean = rel_err(mean, o["mean"])
+    e_ess = abs(ess - o["ess"]) / max(o["ess"], 1e-12)
+    assert e_inc <= TOL_INC, f"step {n}: likelihood increment error {e_inc}"
+    assert e_mean <= TOL_STATE, f"step {n}: mean error {e_mean}"
+    assert e_ess <= 1e-4, f"step {n}: ess error {e_ess}"
+    w = o["within"]
+    lo, hi = plausible_members(w["q"].reshape(m, M, 1), w["u"].reshape(m, M, 1), axis=1)
+    dec_w = (lo == hi).reshape(N)
+    undecidable = int(np.sum(~dec_w))
+    line = np.ones(m, dtype=bool)
+    isl = np.arange(m)
+    for info in o["island_info"]:
+        b = 1 << (info["s"] - 1)
+        H = m // (2 * b)
+        lo, hi = plausible_members(info["q"].reshape(H, 2, b), info["u"].reshape(H, 2, b), axis=1)
+        dec = (lo == hi).reshape(m)
+        undecidable += int(np.sum(~dec))
+        if modified:
+            dec = dec & dec[isl ^ b]
+        line = dec & line[info["choice"]]
+    src = o["holder"][np.arange(N) // M] * M + np.arange(N) % M
+    ok = line[np.arange(N) // M] & dec_w[src]
+    e_x = rel_err(x1[ok], new.x[ok])
+    e_lv = rel_err(lv1, np.full(lv1.shape, new.lV[0]))
+    assert e_x <= TOL_STATE, f"step {n}: state error {e_x}"
+    assert e_lv <= TOL_STATE, f"step {n}: log-weight error {e_lv}"
+    assert abs(sc1["mu"] - new.mu) <= 1e-6 * max(1.0, abs(new.mu))
+    swaps = sum(i["swaps_undone"] for i in o["island_info"])
+    return Report(draws=N + m * len(o["island_info"]), undecidable=undecidable, undecided_particles=int(np.sum(~ok)),
+                  swaps_undone=swaps, max_state_err=e_x, max_logweight_err=e_lv, max_inc_err=e_inc,
+                  max_mean_err=e_mean, max_ess_err=e_ess)
