@@ -70,6 +70,30 @@ def _env_rank():
         int(os.environ.get("LOCAL_RANK", "0"))
 
 
+def replica_seed(base: int, rank: int) -> int:
+    """Filter seed of the replica on one rank: every GPU runs an independent filter
+    (the path has no exchange between GPUs; weak scaling)."""
+    return base + rank
+
+
+def max_over_ranks(values, world: int, device=None):
+    """Element-wise maximum of per-rank timings over all ranks (the slowest rank
+    sets the whole job's time); the identity on one rank.  Needs an initialised
+    process group when world > 1 (NCCL on the GPU machine, gloo in the CPU tests)."""
+    if world <= 1:
+        return [float(v) for v in values]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v) for v in values], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return [float(v) for v in t.tolist()]
+
+
+def job_throughput(world: int, N: int, steps: int, seconds: float) -> float:
+    """Whole-job particle-steps/s: the particles all ranks advanced over the slowest rank's time."""
+    return world * N * steps / seconds
+
+
 def algorithmic_bytes(w, n: int) -> int:
     """Bytes one time step n must move: read + write the states (4 d N each),
     read the carried weights (one per group of the previous digit) and write
@@ -398,8 +422,8 @@ def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
     R = I/4 over 8000 observations; filter-mean MSE against the Kalman mean
     (sum over steps and components, mean over J runs) and time per step, for
     the one-digit schedule, all stages per step, fully adapted resampling at
-    several thresholds (with and without the rotated start) and the global
-    filter.  Times are whole-run device times through pf_run (CUDA graphs)."""
+    several thresholds (with and without the rotated start), AIRPF with 64 and
+    256 islands and the global filter.  Times are whole-run device times through pf_run (CUDA graphs)."""
     import numpy as np
     import torch
     import synthetic as S
@@ -408,15 +432,24 @@ def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
     kal = _random_walk_kalman_means(y, 0.25)
     raw = float(np.sum((y - kal) ** 2))
     yd = torch.tensor(y.astype(np.float32), device=dev)
-    scheds = [("one_digit", {}), ("all_stages", {"all_stages": True})]
+    scheds = [("one_digit", {}, 0), ("all_stages", {"all_stages": True}, 0)]
     for th in (0.2, 0.5, 0.8):
-        scheds.append((f"adaptive_{th}", {"adaptive": True, "ess_threshold": th}))
-    scheds.append(("adaptive_rot_0.5", {"adaptive": True, "ess_threshold": 0.5, "rotate": True}))
-    scheds.append(("global", None))
+        scheds.append((f"adaptive_{th}", {"adaptive": True, "ess_threshold": th}, 0))
+    scheds.append(("adaptive_rot_0.5", {"adaptive": True, "ess_threshold": 0.5, "rotate": True}, 0))
+    scheds.append(("global", None, 0))
+    for mi in (64, 256):        # AIRPF (Algorithm 4 with Algorithm 7): mi islands of N / mi particles
+        scheds.append((f"airpf_m{mi}", {"islands": "modified"}, mi))
     curves = []
-    for name, kw in scheds:
+    for name, kw, mi in scheds:
         for N in Ns:
-            rad = (N,) if kw is None else _radix16(N)
+            if kw is None:
+                rad = (N,)
+            elif mi:
+                if not 16 <= N // mi <= 1024:
+                    continue
+                rad = (N // mi, mi)
+            else:
+                rad = _radix16(N)
             if kw is not None and kw.get("adaptive") and len(rad) == 1 and N > 1024:
                 continue
             mses, ts, stages = [], [], []
@@ -506,7 +539,7 @@ def ours_main(a):
     K, W = a.steps, a.warmup
     T_need = W + K + min(K, 1000) + 8
     y = S.simulate(w.model, max(w.T, T_need), w.data_seed)[1].astype(np.float32)
-    filt = bf.ButterflyFilter(w.model, w.N, w.radices, w.filter_seed + rank, device=dev)
+    filt = bf.ButterflyFilter(w.model, w.N, w.radices, replica_seed(w.filter_seed, rank), device=dev)
     stream = filt.stream
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
 
@@ -560,7 +593,7 @@ def ours_main(a):
 
     # --- end to end through the public call, host buffers -------------------
     y_host = np.ascontiguousarray(y[:K])
-    efilt = bf.ButterflyFilter(w.model, w.N, w.radices, w.filter_seed + rank, device=dev)
+    efilt = bf.ButterflyFilter(w.model, w.N, w.radices, replica_seed(w.filter_seed, rank), device=dev)
     efilt.run(y_host[:min(W, K)])          # warm-up (graph capture, first touch)
     torch.cuda.synchronize(dev)
     if world > 1:
@@ -575,11 +608,11 @@ def ours_main(a):
     glob = None
     if not a.no_global and w.N > 1024:
         KG = max(1, min(a.global_steps, K))
-        gfilt = bf.ButterflyFilter(w.model, w.N, (w.N,), w.filter_seed + rank, device=dev)
+        gfilt = bf.ButterflyFilter(w.model, w.N, (w.N,), replica_seed(w.filter_seed, rank), device=dev)
         g_ms = _timed_flushed_steps(bf, gfilt, torch.tensor(y[:W + KG], device=dev).contiguous(), KG, W,
                                     flush, gfilt.stream, dev)
         gfilt.close()
-        glob = {"value": world * w.N * KG / (sum(g_ms) * 1e-3), "unit": METRIC, "steps": KG,
+        glob = {"value": job_throughput(world, w.N, KG, sum(g_ms) * 1e-3), "unit": METRIC, "steps": KG,
                 "ms_per_step": sum(g_ms) / KG, "p99_ms": float(np.percentile(g_ms, 99)),
                 "kernels_per_step": 3}
     eq = None
@@ -598,12 +631,9 @@ def ours_main(a):
     if not a.no_schedules and rank == 0:
         scheds = schedules_leg(bf, w, dev, flush)
 
-    if world > 1:
-        t = torch.tensor([total_ms, e2e_s, resident_ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms, e2e_s, resident_ms = (float(v) for v in t.tolist())
-    value = world * w.N * K / (total_ms * 1e-3)
-    e2e_value = world * w.N * K / e2e_s
+    total_ms, e2e_s, resident_ms = max_over_ranks([total_ms, e2e_s, resident_ms], world, dev)
+    value = job_throughput(world, w.N, K, total_ms * 1e-3)
+    e2e_value = job_throughput(world, w.N, K, e2e_s)
     if rank != 0:
         if world > 1:
             dist.barrier()
