@@ -116,6 +116,11 @@ typedef struct {
 #define PF_ISLANDS 16u
 /* With PF_ISLANDS: island resampling as in Algorithm 6 (swaps are kept). */
 #define PF_ISLANDS_PLAIN 32u
+/* Test hook for failure reporting (global resampling with N > 4096 only):
+ * the second scan tile waits on a flag that nothing sets, so its bounded wait
+ * runs out (well under a second) every step, status bit 2 is set and
+ * pf_loglik returns PF_ETIMEOUT.  The results of such a filter are invalid. */
+#define PF_TEST_SCAN_TIMEOUT 0x80000000u
 
 typedef struct {
     int32_t tile;        /* target particles per thread-block tile; 0 = automatic            */
@@ -194,7 +199,8 @@ pf_status pf_push_observations(pf_handle* h, const float* y, int32_t T);
 pf_status pf_advance(pf_handle* h, int32_t T, float* means, double* loglik_incs, float* ess);
 
 /* Cumulative log-likelihood estimate log p^(y_0..y_{n-1}) accumulated in
- * FP64 across time.  Synchronises the stream. */
+ * FP64 across time.  Synchronises the stream.  Returns PF_ETIMEOUT (value
+ * still written) if a bounded device-side wait gave up (status bit 2). */
 pf_status pf_loglik(const pf_handle* h, double* out);
 
 /*
@@ -217,7 +223,8 @@ pf_status pf_get_ancestors(const pf_handle* h, int32_t* anc);
 
 /* Sticky device-side status bits of the handle (0 = none): bit 0 = a
  * non-finite log-weight was seen and treated as weight zero; bit 1 = a group
- * had zero total weight and kept its particles.  Synchronises. */
+ * had zero total weight and kept its particles; bit 2 = a bounded wait of the
+ * global-resampling scan gave up (results invalid).  Synchronises. */
 pf_status pf_get_status(const pf_handle* h, uint32_t* bits);
 
 /* Number of resampling stages executed so far (PF_ADAPTIVE counts only the

@@ -34,6 +34,7 @@ PF_ADAPTIVE = 4
 PF_ROTATE = 8
 PF_ISLANDS = 16
 PF_ISLANDS_PLAIN = 32
+PF_TEST_SCAN_TIMEOUT = 0x80000000
 STATUS_NAMES = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",
                 PF_ETIMEOUT: "PF_ETIMEOUT", PF_ESTATE: "PF_ESTATE"}
 
@@ -166,7 +167,7 @@ class ButterflyFilter:
                  chunk_len: int = 0, record_ancestors: bool = False, grid: int = 0,
                  device=None, stream=None, tune: bool = False, all_stages: bool = False,
                  adaptive: bool = False, ess_threshold: float = 0.5, rotate: bool = False,
-                 islands: Optional[str] = None):
+                 islands: Optional[str] = None, extra_flags: int = 0):
         torch = _torch()
         lib = load_library()
         if not torch.cuda.is_available():
@@ -189,7 +190,8 @@ class ButterflyFilter:
                                flags=(PF_RECORD_ANCESTORS if record_ancestors else 0)
                                | (PF_ALL_STAGES if all_stages else 0) | (PF_ADAPTIVE if adaptive else 0)
                                | (PF_ROTATE if rotate else 0)
-                               | (PF_ISLANDS if islands else 0) | (PF_ISLANDS_PLAIN if islands == "plain" else 0),
+                               | (PF_ISLANDS if islands else 0) | (PF_ISLANDS_PLAIN if islands == "plain" else 0)
+                               | int(extra_flags),
                                grid=int(grid),
                                stream=ctypes.c_void_p(self.stream.cuda_stream),
                                ess_threshold=float(ess_threshold) if adaptive else 0.0)

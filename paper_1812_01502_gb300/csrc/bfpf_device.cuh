@@ -302,6 +302,7 @@ struct GlobalParams {
   uint32_t* flag;                 // [nscan] 2n+1: aggregate ready, 2n+2: prefix ready (step n)
   uint32_t nscan;                 // scan tiles of kScanTile particles
   uint32_t ntop, top_shift;
+  uint32_t stall_tile;            // test hook (0 = off): this scan tile waits on a flag nothing sets
 };
 
 // Augmented island resampling (AIRPF): islands of M consecutive particles.

@@ -641,6 +641,7 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
     G.nscan = pl.nscan;
     G.ntop = pl.ntop;
     G.top_shift = pl.top_shift;
+    G.stall_tile = (opts && (opts->flags & PF_TEST_SCAN_TIMEOUT) && pl.nscan > 1) ? 1u : 0u;
   }
 
   // Algorithm 1, first loop: zeta_0 ~ pi_0; carried weights start at zero.
@@ -786,6 +787,8 @@ pf_status pf_loglik(const pf_handle* h, double* out) {
   PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   *out = st.loglik;
+  if (st.status & kStatusTimeout)
+    return fail(h, PF_ETIMEOUT, "a bounded device-side wait gave up; this filter's results are not valid");
   return PF_OK;
 }
 

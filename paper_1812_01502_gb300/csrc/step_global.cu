@@ -28,7 +28,7 @@ namespace bfpf {
 
 namespace {
 
-constexpr uint32_t kSpinLimit = 1u << 22;   // bounded wait on a predecessor tile
+constexpr uint32_t kSpinLimit = 1u << 20;   // bounded wait on a predecessor tile (well under a second)
 
 __device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
   return *reinterpret_cast<const volatile unsigned long long*>(p);
@@ -149,8 +149,10 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
       atomicExch(gp.flag + tile, f_agg);
       int32_t t = (int32_t)tile - 1;
       uint32_t spins = 0;
+      // test hook: the stalled tile recognises no flag, so its wait runs out
+      const bool stall = gp.stall_tile != 0 && tile == gp.stall_tile;
       while (t >= 0) {
-        const uint32_t f = ld_volatile_u32(gp.flag + t);
+        const uint32_t f = stall ? 0u : ld_volatile_u32(gp.flag + t);
         if (f == f_pre) {
           __threadfence();
           prefix += ld_volatile_u64(gp.incl + t);
