@@ -105,7 +105,7 @@ def algorithmic_bytes(w, n: int) -> int:
 
 
 KERNEL_SOURCES = ("bfpf_device.cuh", "bfpf_epilogue.cuh", "bfpf_model.cuh", "step_group.cuh",
-                  "step_butterfly.cu")
+                  "step_group_d1.cu")
 
 
 def _kernel_source_hash() -> str:
