@@ -29,7 +29,7 @@ from typing import Dict, Optional, Sequence
 import numpy as np
 
 from . import philox, resample
-from .butterfly import group_major, strides
+from .butterfly import group_major, set_group_major, strides
 
 
 @dataclass
@@ -149,6 +149,75 @@ def stage(radices: Sequence[int], seed: int, x: np.ndarray, lw: np.ndarray, k: i
     l_idx = np.arange(s_k)[None, None, :]
     anc = (h_idx * (a * s_k) + member * s_k + l_idx).reshape(N)
     return x[anc], lV_new, anc, q.reshape(N), u.reshape(N), pi
+
+
+def stage_set(radices: Sequence[int], seed: int, x: np.ndarray, lw: np.ndarray, k: int, t: int):
+    """One stage of Algorithm 3 whose matrix is the digit set {0, k} (k >= 1): the
+    group of i is every index sharing all digits but 0 and k (a_0 a_k members, digit
+    k major, digit 0 minor), V_s = A V_{s-1} with A = set_A(radices, k) and the draws
+    by the integer rule, words keyed by the stage counter t and numbered group by
+    group (set_group_major).  With radices (M, 2, ..., 2) this is eq. (A matrices)."""
+    N = x.shape[0]
+    a0, a = radices[0], radices[k]
+    s_k = strides(radices)[k]
+    Hh = N // (a * s_k)
+    L = s_k // a0
+    G = a * a0
+    # (H, a_k, L, a_0) -> (H, L, a_k, a_0) -> groups (H L) x members (a_k a_0)
+    lwg = lw.reshape(Hh, a, L, a0).transpose(0, 2, 1, 3).reshape(Hh * L, G)
+    Mg = np.max(lwg, axis=1, keepdims=True)
+    with np.errstate(invalid="ignore"):
+        Lg = Mg + np.log(np.sum(np.exp(lwg - Mg), axis=1, keepdims=True))
+    q = resample.quantise(lwg, axis=1)
+    Q = np.sum(q, axis=1, keepdims=True, dtype=np.uint64)
+    pi = set_group_major(N, radices, k)
+    # members' words in group order: member rho of group g is particle with pi = g G + rho
+    order = np.argsort(pi)                     # order[g G + rho] = particle index
+    if G <= resample.NARROW_MAX_RADIX:
+        r = philox.resample_words_at(seed, t, np.arange(N)).reshape(Hh * L, G)
+        u = resample.scaled_uniform(r, Q, G)
+    else:
+        lo, hi = philox.resample_words_wide_at(seed, t, np.arange(N))
+        u = resample.scaled_uniform(lo.reshape(Hh * L, G), Q, G, hi.reshape(Hh * L, G))
+    member = resample.draw(q, u, axis=1)       # (groups, G) member drawn by member rho
+    ranks = np.arange(Hh * L)[:, None] * G
+    anc_sorted = order[ranks + member]         # ancestor particle of the draw with number g G + rho
+    anc = np.empty(N, dtype=np.int64)
+    anc[order] = anc_sorted.reshape(N)
+    lV_new = np.empty(N)
+    lV_new[order] = np.broadcast_to(Lg - np.log(G), lwg.shape).reshape(N)
+    q_p = np.empty(N, dtype=np.uint64)
+    u_p = np.empty(N, dtype=np.uint64)
+    q_p[order] = q.reshape(N)
+    u_p[order] = u.reshape(N)
+    return x[anc], lV_new, anc, q_p, u_p, pi
+
+
+def step_digit_sets(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
+                    mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
+    """One time step of Algorithm 1 with Algorithm 3 exactly as the paper defines its
+    stages (eq. (A matrices)): radices (a_0, a_1, ..., a_S), stage s = 1..S on the digit
+    set {0, s} (the within-PE digit and PE bit s-1 when radices = (M, 2, ..., 2)).
+    g_n weights stage 1, stage S mutates (normals numbered group by group on the set
+    {0, S}); stage s draws with counter t = n S + s - 1.  Afterwards every weight is
+    equal (Lemma 3(c))."""
+    radices = [int(a) for a in radices]
+    S_ = len(radices) - 1
+    if S_ < 1:
+        raise ValueError("digit sets need at least two digits")
+    n = st.n
+    mu_sub = st.mu if mu_used is None else float(mu_used)
+    lw, c_n = weigh(model, st.x, st.lV, mu_sub, y_n)
+    inc, mean, ess, lme = summaries(lw, st.x, c_n, mu_sub, st.mu)
+    x = st.x
+    stages = []
+    for s in range(1, S_ + 1):
+        x, lV_new, anc, q, u, pi = stage_set(radices, seed, x, lw, s, n * S_ + s - 1)
+        stages.append(dict(k=s, anc=anc, q=q, u=u, lw=lw, lV_new=lV_new))
+        lw = lV_new
+    x_next = mutate(model, x, n, seed, idx=pi)
+    new = State(x=x_next, lV=lw, mu=lme, n=n + 1, loglik=st.loglik + inc)
+    return new, dict(stages=stages, inc=inc, mean=mean, ess=ess, lV_new=lw, c=c_n)
 
 
 def step_all_stages(model, radices: Sequence[int], seed: int, st: State, y_n: np.ndarray,
@@ -363,7 +432,9 @@ def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
     ancs = [] if keep_ancestors else None
     executed = 0
     for t in range(T):
-        if islands is not None:      # "modified" (Algorithm 7) or "plain" (Algorithm 6); radices = (M, m)
+        if all_stages == "sets":     # Algorithm 3 with eq. (A matrices): digit sets {0, s}
+            st, o = step_digit_sets(model, radices, seed, st, y[t])
+        elif islands is not None:    # "modified" (Algorithm 7) or "plain" (Algorithm 6); radices = (M, m)
             st, o = step_islands(model, radices[0], radices[1], seed, st, y[t], islands == "modified")
         elif theta is not None:
             st, o = step_adaptive(model, radices, seed, st, y[t], theta, rotate)

@@ -87,3 +87,30 @@ def group_major(N: int, radices: Sequence[int], k: int) -> np.ndarray:
     s = strides(radices)[k]
     i = np.arange(N, dtype=np.int64)
     return group_index(i, radices, k) * a + (i // s) % a
+
+
+def set_A(radices: Sequence[int], k: int) -> np.ndarray:
+    """Stage matrix of the digit set {0, k} (k >= 1): the groups are the indices that
+    share every digit except digits 0 and k, each of size a_0 a_k, so A = A_k A_0
+    (the two digit stages commute).  With radices (M, 2, ..., 2) this is the paper's
+    A_s of eq. (A matrices) for s = k."""
+    return mixed_radix_A(radices, k) @ mixed_radix_A(radices, 0)
+
+
+def set_group_index(i, radices: Sequence[int], k: int):
+    """Group of i for the digit set {0, k}: g = h (s_k / a_0) + l' with h the digits
+    above k and l' the digits 1..k-1 of i."""
+    a0, a = int(radices[0]), int(radices[k])
+    s = strides(radices)[k]
+    i = np.asarray(i, dtype=np.int64)
+    return (i // (a * s)) * (s // a0) + (i % s) // a0
+
+
+def set_group_major(N: int, radices: Sequence[int], k: int) -> np.ndarray:
+    """pi(i) = g a_0 a_k + rho for the digit set {0, k}, rho = r_k a_0 + r_0 (digit k
+    major, digit 0 minor: the first PE's particles, then its partner's)."""
+    a0, a = int(radices[0]), int(radices[k])
+    s = strides(radices)[k]
+    i = np.arange(N, dtype=np.int64)
+    rho = ((i // s) % a) * a0 + i % a0
+    return set_group_index(i, radices, k) * (a0 * a) + rho

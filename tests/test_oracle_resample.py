@@ -312,3 +312,46 @@ def test_adaptive_stopping_rule_and_weight_mass(rotate):
             assert st.start == 0
     if rotate:
         assert len(set(starts)) > 1
+
+
+def test_digit_set_matrix_is_the_papers_A():
+    """With radices (M, 2, ..., 2) the digit set {0, s} has the paper's A_s (eq. (A matrices))."""
+    for M, S_ in ((3, 2), (2, 3)):
+        radices = (M,) + (2,) * S_
+        for s in range(1, S_ + 1):
+            np.testing.assert_allclose(butterfly.set_A(radices, s), butterfly.paper_A(S_, M, s), atol=1e-15)
+
+
+@pytest.mark.parametrize("radices", [(3, 2, 2), (4, 2, 2, 2), (2, 3, 5)])
+def test_digit_set_stage_weights_and_support(radices):
+    """V_s = A V_{s-1} for the set's matrix, ancestors inside the set group, and after
+    all S set stages every weight is equal (Lemma 3(c))."""
+    N = int(np.prod(radices))
+    model = S.lg_scalar()
+    y = S.simulate(model, 3, seed=4)[1]
+    st = bpf.init_state(model, N, seed=6)
+    for n in range(3):
+        new, o = bpf.step_digit_sets(model, radices, 6, st, y[n])
+        for sg in o["stages"]:
+            A = butterfly.set_A(radices, sg["k"])
+            mx = sg["lw"].max()
+            np.testing.assert_allclose(np.exp(sg["lV_new"] - mx), A @ np.exp(sg["lw"] - mx), rtol=1e-12)
+            gi = butterfly.set_group_index(np.arange(N), radices, sg["k"])
+            assert np.array_equal(gi[sg["anc"]], gi)
+        np.testing.assert_allclose(new.lV, new.lV[0], atol=1e-12)
+        st = new
+
+
+def test_one_digit_set_is_global_resampling():
+    """With two digits the one set {0, 1} is every particle: the step is the one-digit
+    step on radices (N,), counters and numbering included."""
+    model = S.sv_model()
+    y = S.simulate(model, 4, seed=9)[1]
+    a = bpf.init_state(model, 48, seed=2)
+    b = bpf.init_state(model, 48, seed=2)
+    for n in range(4):
+        a, oa = bpf.step(model, (48,), 2, a, y[n])
+        b, ob = bpf.step_digit_sets(model, (6, 8), 2, b, y[n])
+        assert np.array_equal(oa["anc"], ob["stages"][0]["anc"])
+        np.testing.assert_allclose(a.x, b.x, rtol=0, atol=0)
+        assert oa["inc"] == ob["inc"]
