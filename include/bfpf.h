@@ -116,6 +116,15 @@ typedef struct {
 #define PF_ISLANDS 16u
 /* With PF_ISLANDS: island resampling as in Algorithm 6 (swaps are kept). */
 #define PF_ISLANDS_PLAIN 32u
+/* Algorithm 3 with the paper's own stage matrices (eq. (A matrices)): each
+ * time step runs stages s = 1..m-1, stage s resampling within the groups of
+ * the digit SET {0, s} -- the a_0 a_s particles that share every digit except
+ * digits 0 and s (radices (M, 2, ..., 2): a PE's M particles together with
+ * its partner PE's across bit s-1).  Stage 1 weights with g_n, stage m-1
+ * mutates; afterwards every carried weight is equal (Lemma 3(c)).  Needs
+ * m >= 2 and a_0 a_s <= 1024; m - 1 launches per step.  Cannot be combined
+ * with the other schedule flags or PF_RECORD_ANCESTORS. */
+#define PF_DIGIT_SETS 64u
 /* Test hook for failure reporting (global resampling with N > 4096 only):
  * the second scan tile waits on a flag that nothing sets, so its bounded wait
  * runs out (well under a second) every step, status bit 2 is set and
@@ -126,7 +135,7 @@ typedef struct {
     int32_t tile;        /* target particles per thread-block tile; 0 = automatic            */
     int32_t chunk_len;   /* time steps per CUDA-graph replay in pf_run; 0 = 64 (max 1024)    */
     uint32_t flags;      /* PF_RECORD_ANCESTORS | PF_ALL_STAGES | PF_ADAPTIVE | PF_ROTATE |  */
-                         /* PF_ISLANDS | PF_ISLANDS_PLAIN                                    */
+                         /* PF_ISLANDS | PF_ISLANDS_PLAIN | PF_DIGIT_SETS                    */
     int32_t grid;        /* persistent thread blocks; 0 = automatic (SMs x occupancy)        */
     void* stream;        /* cudaStream_t to run on; NULL = the legacy default stream          */
     float ess_threshold; /* PF_ADAPTIVE: a stage runs while ESS < ess_threshold; 0 = 0.5.     */

@@ -35,6 +35,7 @@ PF_ROTATE = 8
 PF_ISLANDS = 16
 PF_ISLANDS_PLAIN = 32
 PF_TEST_SCAN_TIMEOUT = 0x80000000
+PF_DIGIT_SETS = 64
 STATUS_NAMES = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",
                 PF_ETIMEOUT: "PF_ETIMEOUT", PF_ESTATE: "PF_ESTATE"}
 
@@ -157,7 +158,8 @@ class ButterflyFilter:
     adapted augmented resampling: stages run while the ESS is below
     ``ess_threshold`` (optionally from a rotated start, ``rotate``).
     islands="modified" (or "plain") is AIRPF with radices (M, m): m islands of
-    M particles, island resampling by Algorithm 7 (or 6).
+    M particles, island resampling by Algorithm 7 (or 6).  digit_sets=True runs
+    Algorithm 3 with the paper's stage matrices: stage s on digits {0, s}.
     radices = (N,) is the global-resampling bootstrap filter (Algorithm 1 + 2).
     The workspace is a torch uint8 tensor on ``device``; work runs on the
     current torch stream of that device unless ``stream`` is given.
@@ -167,7 +169,7 @@ class ButterflyFilter:
                  chunk_len: int = 0, record_ancestors: bool = False, grid: int = 0,
                  device=None, stream=None, tune: bool = False, all_stages: bool = False,
                  adaptive: bool = False, ess_threshold: float = 0.5, rotate: bool = False,
-                 islands: Optional[str] = None, extra_flags: int = 0):
+                 islands: Optional[str] = None, digit_sets: bool = False, extra_flags: int = 0):
         torch = _torch()
         lib = load_library()
         if not torch.cuda.is_available():
@@ -191,7 +193,7 @@ class ButterflyFilter:
                                | (PF_ALL_STAGES if all_stages else 0) | (PF_ADAPTIVE if adaptive else 0)
                                | (PF_ROTATE if rotate else 0)
                                | (PF_ISLANDS if islands else 0) | (PF_ISLANDS_PLAIN if islands == "plain" else 0)
-                               | int(extra_flags),
+                               | (PF_DIGIT_SETS if digit_sets else 0) | int(extra_flags),
                                grid=int(grid),
                                stream=ctypes.c_void_p(self.stream.cuda_stream),
                                ess_threshold=float(ess_threshold) if adaptive else 0.0)
@@ -199,6 +201,7 @@ class ButterflyFilter:
         self.all_stages = bool(all_stages)
         self.adaptive = bool(adaptive)
         self.islands = islands
+        self.digit_sets = bool(digit_sets)
         with torch.cuda.device(self.device):
             nbytes = ctypes.c_size_t(0)
             _check(lib.pf_workspace_size(ctypes.byref(self._pm), self.N, self._rad, self.m,
@@ -304,8 +307,14 @@ class ButterflyFilter:
         """(x (N, d) float32, lV (N / a_prev,) float32, dict(n, loglik, mu, mu_used))."""
         t = self.steps * (self.m if (self.all_stages or self.islands) else 1)    # stage counter
         kp = (t - 1) % self.m
+        if self.adaptive:
+            nlv = self.N
+        elif self.digit_sets:                   # groups of the last set {0, m-1}
+            nlv = self.N // (self.radices[0] * self.radices[-1])
+        else:
+            nlv = self.N // self.radices[kp]
         x = np.empty((self.d, self.N), dtype=np.float32)
-        lv = np.empty(self.N if self.adaptive else self.N // self.radices[kp], dtype=np.float32)
+        lv = np.empty(nlv, dtype=np.float32)
         sc = np.empty(4, dtype=np.float64)
         _check(_lib.pf_get_state(self._h, x.ctypes.data_as(ctypes.c_void_p), lv.ctypes.data_as(ctypes.c_void_p),
                                  sc.ctypes.data_as(ctypes.c_void_p)), self._h)

@@ -193,6 +193,10 @@ struct DigitGeom {
   float log_a;        // log(a_k)
   uint32_t wide;      // a_k > kNarrowMaxRadix: 32-bit weights, 64-bit draws, 64-bit prefix sums
   FastDiv div_nl, div_a, div_tiles_l, div_prev_as, div_prev_s, div_tgroups;
+  // digit-set stages {0, k} (step_sets.cu): w = a_0 columns per group, prev_sw =
+  // prev_s / w; 1 and prev_s for a plain digit stage
+  uint32_t w, prev_sw;
+  FastDiv div_w, div_nlw;
 };
 
 // Geometry of one digit for the register-resident group kernel (power-of-two

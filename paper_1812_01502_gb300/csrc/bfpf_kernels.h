@@ -17,6 +17,8 @@ struct KernelSet {
 bool select_kernels(int d, int kind, bool wide, KernelSet& ks);
 // The general kernel for the all-stages schedule (step_butterfly_staged.cu).
 const void* select_staged_tile_kernel(int d, int kind, bool wide);
+// The digit-set stage kernel step_sets_kernel<d, kind, wide>(StepParams) (step_sets.cu).
+const void* select_sets_kernel(int d, int kind, bool wide);
 
 // Register-resident group kernel step_group_kernel<d, kind, a, G, staged>(StepParams,
 // GroupGeom) for a power-of-two radix a <= 32; sets *G (lanes per group).  nullptr if none.

@@ -60,6 +60,7 @@ struct Plan {
   bool rotate = false;
   float theta = 0.5f;
   AdaptiveKernels ak{};
+  bool sets = false;          // PF_DIGIT_SETS: stage s on digits {0, s}, m - 1 launches per step
   bool islands = false;       // PF_ISLANDS: radices (M, m), 3 launches per step
   bool island_plain = false;
   IslandKernels ik{};
@@ -321,8 +322,66 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     g.div_prev_as = make_fastdiv(pl.geom[kp].a * pl.geom[kp].s);
     g.div_prev_s = make_fastdiv(pl.geom[kp].s);
   }
-  for (int k = 0; k < m; ++k) pl.geom[k].div_tgroups = make_fastdiv(pl.geom[k].nh * pl.geom[k].nl);
-  pl.sps = (opts && (opts->flags & PF_ALL_STAGES)) ? (uint32_t)m : 1u;
+  for (int k = 0; k < m; ++k) {
+    DigitGeom& g = pl.geom[k];
+    g.div_tgroups = make_fastdiv(g.nh * g.nl);
+    g.w = 1;
+    g.prev_sw = g.prev_s;
+    g.div_w = make_fastdiv(1);
+    g.div_nlw = g.div_nl;
+  }
+  pl.sets = opts && (opts->flags & PF_DIGIT_SETS);
+  if (pl.sets) {
+    // Digit sets {0, k}, k = 1..m-1 (eq. (A matrices)): groups of a_0 a_k members.
+    if (opts->flags & (PF_ALL_STAGES | PF_ADAPTIVE | PF_ISLANDS | PF_RECORD_ANCESTORS)) {
+      msg = "PF_DIGIT_SETS cannot be combined with the other schedule flags or PF_RECORD_ANCESTORS";
+      return PF_EINVAL;
+    }
+    if (m < 2) { msg = "PF_DIGIT_SETS needs at least two radices"; return PF_EINVAL; }
+    const uint32_t w = (uint32_t)radices[0];
+    pl.cap = 0;
+    pl.max_tiles = 0;
+    pl.wide = false;
+    for (int k = 1; k < m; ++k) {
+      if ((uint64_t)w * (uint64_t)radices[k] > kMaxCtaRadix) {
+        msg = "PF_DIGIT_SETS needs a_0 * a_k <= 1024 for every k";
+        return PF_EINVAL;
+      }
+    }
+    for (int k = 1; k < m; ++k) {
+      DigitGeom& g = pl.geom[k];
+      const uint32_t a = g.a, sk = g.s;
+      const uint32_t G = a * w;
+      if ((uint64_t)a * sk <= target) {
+        g.nl = sk;
+        g.nh = largest_divisor_at_most(g.H, std::max<uint32_t>(1, target / (a * sk)));
+      } else {
+        g.nh = 1;
+        g.nl = w * largest_divisor_at_most(sk / w, std::max<uint32_t>(1, target / G));
+      }
+      g.tiles_l = sk / g.nl;
+      g.ntiles = (g.H / g.nh) * g.tiles_l;
+      g.tile_n = g.nh * a * g.nl;
+      g.quad = (g.nl == sk) ? ((g.tile_n % 4 == 0) && (pl.N % 4 == 0)) : ((g.nl % 4 == 0) && (sk % 4 == 0));
+      g.log_a = (float)std::log((double)G);
+      g.wide = G > kNarrowMaxRadix ? 1u : 0u;
+      g.div_nl = make_fastdiv(g.nl);
+      g.div_tiles_l = make_fastdiv(g.tiles_l);
+      const int kp = (k == 1) ? m - 1 : k - 1;          // the previous stage's set {0, kp}
+      g.prev_s = pl.geom[kp].s;
+      g.div_prev_as = make_fastdiv(pl.geom[kp].a * pl.geom[kp].s);
+      g.div_prev_s = make_fastdiv(pl.geom[kp].s);
+      g.w = w;
+      g.prev_sw = pl.geom[kp].s / w;
+      g.div_w = make_fastdiv(w);
+      g.div_nlw = make_fastdiv(g.nl / w);
+      g.div_tgroups = make_fastdiv(g.nh * (g.nl / w));
+      pl.cap = std::max(pl.cap, g.tile_n);
+      pl.max_tiles = std::max(pl.max_tiles, g.ntiles);
+      if (g.wide) pl.wide = true;
+    }
+  }
+  pl.sps = (opts && (opts->flags & PF_ALL_STAGES)) ? (uint32_t)m : pl.sets ? (uint32_t)m - 1 : 1u;
   if (pl.islands) {           // the within-island stage is stage 0 of a two-stage step
     pl.sps = 2;
     if (!select_island_kernels(d, pl.kind, pl.ik)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
@@ -351,7 +410,7 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     DigitPlan& dp = pl.dp[k];
     const DigitGeom& g = pl.geom[k];
     int G = 0;
-    const void* gk = (pow2 && g.a <= 32 && !pl.adaptive) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged) : nullptr;
+    const void* gk = (pow2 && g.a <= 32 && !pl.adaptive && !pl.sets) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged) : nullptr;
     if (gk && G > 0) {
       const uint32_t gpb = kBlock / G;
       const uint32_t ngroups = pl.N / g.a;
@@ -430,7 +489,10 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   cudaError_t e = cudaGetDevice(&dev);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (e == cudaSuccess && pl.global) return finish_plan_global(pl, opts, sms, msg);
-  const void* tile_kernel = pl.adaptive ? pl.ak.stage : pl.sps > 1 ? pl.ks.step_staged : pl.ks.step;
+  const void* tile_kernel = pl.adaptive ? pl.ak.stage
+                            : pl.sets ? select_sets_kernel(pl.d, pl.kind, pl.wide)
+                            : pl.sps > 1 ? pl.ks.step_staged : pl.ks.step;
+  if (!tile_kernel) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
   if (e == cudaSuccess)   // opt in beyond the 48 KB default whatever the size
     e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tile_kernel, kBlock, pl.smem);
@@ -519,7 +581,8 @@ cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
     void* args[] = {&h->P, &h->launch_j[j - 1]};
     return cudaLaunchKernel(pl.ak.stage, dim3(pl.max_grid), dim3(kBlock), args, pl.smem, stream);
   }
-  DigitPlan& dp = h->plan.dp[t % (uint64_t)h->plan.m];
+  const uint64_t kd = h->plan.sets ? 1 + t % (uint64_t)(h->plan.m - 1) : t % (uint64_t)h->plan.m;
+  DigitPlan& dp = h->plan.dp[kd];
   if (dp.group) {
     void* args[] = {&h->P, &dp.gg};
     return cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, 0, stream);
@@ -711,7 +774,8 @@ pf_status enqueue_steps(pf_handle* h, int32_t L) {
   const int64_t launches = (int64_t)L * (int64_t)lps;
   if (L == pl.chunk_len && L > 1) {
     if (h->graphs.empty()) h->graphs.assign(pl.m, nullptr);
-    cudaGraphExec_t& exec = h->graphs[pl.islands ? h->n_host & 1u : pl.adaptive ? 0 : t0 % (uint64_t)pl.m];
+    cudaGraphExec_t& exec =
+        h->graphs[pl.islands ? h->n_host & 1u : (pl.adaptive || pl.sets) ? 0 : t0 % (uint64_t)pl.m];
     if (!exec) {
       cudaGraph_t graph = nullptr;
       PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -806,8 +870,8 @@ pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars)
     PF_CUDA(h, cudaStreamSynchronize(h->stream));
   } else if (lV) {
     const uint64_t t = (uint64_t)st.n * pl.sps + st.stage;   // stage counter
-    const int kp = (int)((t + pl.m - 1) % pl.m);
-    const size_t cnt = pl.global ? 1 : pl.N / pl.geom[kp].a;
+    const int kp = pl.sets ? (int)(1 + (t + pl.m - 2) % (pl.m - 1)) : (int)((t + pl.m - 1) % pl.m);
+    const size_t cnt = pl.global ? 1 : pl.N / (pl.geom[kp].a * pl.geom[kp].w);
     PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[t & 1u], 4 * cnt, cudaMemcpyDeviceToHost, h->stream));
     PF_CUDA(h, cudaStreamSynchronize(h->stream));
   }
@@ -855,6 +919,7 @@ pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
                   ", \"rotate\": " + (pl.rotate ? "true" : "false") +
                   ", \"ess_threshold\": " + std::to_string(pl.adaptive ? pl.theta : 0.0f) +
                   ", \"islands\": " + std::to_string(pl.islands ? pl.geom[1].a : 0) +
+                  ", \"digit_sets\": " + (pl.sets ? "true" : "false") +
                   ", \"island_resampling\": \"" + (pl.islands ? (pl.island_plain ? "algorithm6" : "algorithm7") : "") +
                   "\", \"digits\": [";
   if (pl.global)

@@ -315,3 +315,43 @@ def check_step_islands(filt, model, M, m, seed, y_n, n, modified):
     return Report(draws=N + m * len(o["island_info"]), undecidable=undecidable, undecided_particles=int(np.sum(~ok)),
                   swaps_undone=swaps, max_state_err=e_x, max_logweight_err=e_lv, max_inc_err=e_inc,
                   max_mean_err=e_mean, max_ess_err=e_ess)
+
+
+def check_step_digit_sets(filt, model, radices, seed, y_n, n):
+    """GPU time step n with the paper's stage matrices (PF_DIGIT_SETS: stage s on the
+    digit set {0, s}) against the oracle's step from the same state; states must
+    match on lines of ancestry whose every draw is decidable."""
+    N = int(np.prod(radices))
+    m = len(radices)
+    x0, lv0, sc = filt.state()
+    assert sc["n"] == n
+    mean, inc, ess = filt.step(y_n)
+    x1, lv1, sc1 = filt.state()
+    lV = lv0[butterfly.set_group_index(np.arange(N), radices, m - 1)].astype(np.float64)
+    st = bpf.State(x=x0.astype(np.float64), lV=lV, mu=sc["mu"], n=n)
+    new, o = bpf.step_digit_sets(model, radices, seed, st, y_n, mu_used=sc["mu_used"])
+    line = np.ones(N, dtype=bool)
+    undecidable = 0
+    for sg in o["stages"]:
+        k = sg["k"]
+        G = int(radices[0]) * int(radices[k])
+        order = np.argsort(butterfly.set_group_major(N, radices, k))
+        lo, hi = plausible_members(sg["q"][order].reshape(N // G, G), sg["u"][order].reshape(N // G, G), axis=1)
+        dec = np.empty(N, dtype=bool)
+        dec[order] = (lo == hi).reshape(N)
+        undecidable += int(np.sum(~dec))
+        line = dec & line[sg["anc"]]
+    e_x = rel_err(x1[line], new.x[line])
+    e_lv = rel_err(lv1, np.full(lv1.shape, new.lV[0]))
+    e_inc = abs(inc - o["inc"]) / max(1.0, abs(o["inc"]))
+    e_mean = rel_err(mean, o["mean"])
+    e_ess = abs(ess - o["ess"]) / max(o["ess"], 1e-12)
+    assert e_x <= TOL_STATE, f"step {n}: state error {e_x}"
+    assert e_lv <= TOL_STATE, f"step {n}: log-weight error {e_lv}"
+    assert e_inc <= TOL_INC, f"step {n}: likelihood increment error {e_inc}"
+    assert e_mean <= TOL_STATE, f"step {n}: mean error {e_mean}"
+    assert e_ess <= 1e-4, f"step {n}: ess error {e_ess}"
+    assert abs(sc1["mu"] - new.mu) <= 1e-6 * max(1.0, abs(new.mu))
+    return Report(draws=N * (m - 1), undecidable=undecidable, undecided_lines=int(np.sum(~line)),
+                  max_state_err=e_x, max_logweight_err=e_lv, max_inc_err=e_inc, max_mean_err=e_mean,
+                  max_ess_err=e_ess)

@@ -62,3 +62,51 @@ def test_all_stages_single_digit_is_default(bfpf):
 def test_all_stages_rejects_ancestor_recording(bfpf):
     with pytest.raises(bfpf.PFError):
         bfpf.ButterflyFilter(S.lg_scalar(), 64, (8, 8), 1, all_stages=True, record_ancestors=True)
+
+
+@pytest.mark.parametrize("name,model,radices,T", [
+    ("sv_paper_4x8pe", S.sv_model(), (4, 2, 2, 2), 5),
+    ("lg_paper_8x16pe", S.lg_scalar(), (8, 2, 2, 2, 2), 5),
+    ("lg3_mixed", S.lg_dense(3, seed=8), (16, 4, 4, 2), 4),
+    ("sv_m100", S.sv_model(), (100, 2, 2, 2), 4),
+    ("lg1_wide_300", S.lg_scalar(r=0.2), (300, 2, 2), 4),
+    ("lg2_32x8x4", S.lg_dense(2, seed=9), (32, 8, 4), 4),
+    ("sv_two_digits", S.sv_model(), (32, 16), 4),
+    ("lg1_paper_64x1024pe", S.lg_scalar(), (64,) + (2,) * 10, 3),
+])
+def test_digit_sets_lockstep(bfpf, name, model, radices, T):
+    N = int(np.prod(radices))
+    y = S.simulate(model, T, seed=59)[1]
+    seed = 828
+    f = bfpf.ButterflyFilter(model, N, radices, seed, digit_sets=True)
+    d = f.describe()
+    assert d["digit_sets"] and d["stages_per_step"] == len(radices) - 1
+    rep = LS.Report()
+    for n in range(T):
+        rep.merge(LS.check_step_digit_sets(f, model, radices, seed, y[n], n))
+    f.close()
+    print(name, dict(rep))
+    # a draw is undecidable with probability about eta * (group size); a line crosses m - 1 stages
+    expected = sum(radices[0] * a for a in radices[1:]) * LS.ETA * N * T
+    assert rep["undecided_lines"] <= max(16, 3 * expected)
+
+
+def test_digit_sets_graph_equals_steps(bfpf):
+    model, radices = S.sv_model(), (16, 2, 2, 2, 2)
+    N = int(np.prod(radices))
+    y = S.simulate(model, 30, seed=61)[1]
+    a = bfpf.ButterflyFilter(model, N, radices, 3, digit_sets=True, chunk_len=8)
+    ra = a.run(y)
+    b = bfpf.ButterflyFilter(model, N, radices, 3, digit_sets=True)
+    inc_b = [b.step(y[n])[1] for n in range(len(y))]
+    assert np.array_equal(ra["inc"], np.array(inc_b))
+    assert np.array_equal(a.state()[0], b.state()[0])
+    a.close()
+    b.close()
+
+
+def test_digit_sets_invalid(bfpf):
+    with pytest.raises(bfpf.PFError):
+        bfpf.ButterflyFilter(S.lg_scalar(), 2048, (64, 32), 1, digit_sets=True)       # a_0 a_1 > 1024
+    with pytest.raises(bfpf.PFError):
+        bfpf.ButterflyFilter(S.lg_scalar(), 64, (8, 8), 1, digit_sets=True, all_stages=True)
