@@ -117,6 +117,20 @@ def _kernel_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
+def _profiled_issue(workload: str):
+    """Thread instructions per particle-step of the step kernel from the committed
+    ncu summary (None when the kernel source changed since it was captured)."""
+    path = os.path.join(ROOT, "profiles", f"step_group_{workload}.md")
+    if not os.path.exists(path):
+        return None
+    text = open(path).read()
+    mh = re.search(r"kernel_source_sha256_16:\s*([0-9a-f]+)", text)
+    mi = re.search(r"thread_instructions_per_particle:\s*([0-9.eE+]+)", text)
+    if not mh or not mi or mh.group(1) != _kernel_source_hash():
+        return None
+    return float(mi.group(1))
+
+
 def _profiled_traffic(workload: str):
     """DRAM bytes per launch of the step kernel from the committed ncu summary,
     or None when the kernel source changed since it was captured."""
@@ -423,7 +437,8 @@ def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
     (sum over steps and components, mean over J runs) and time per step, for
     the one-digit schedule, all stages per step, fully adapted resampling at
     several thresholds (with and without the rotated start), AIRPF with 64 and
-    256 islands and the global filter.  Times are whole-run device times through pf_run (CUDA graphs)."""
+    256 islands, the paper's own stage matrices (64 particles per PE, one stage
+    per PE bit) and the global filter.  Times are whole-run device times through pf_run (CUDA graphs)."""
     import numpy as np
     import torch
     import synthetic as S
@@ -439,11 +454,15 @@ def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
     scheds.append(("global", None, 0))
     for mi in (64, 256):        # AIRPF (Algorithm 4 with Algorithm 7): mi islands of N / mi particles
         scheds.append((f"airpf_m{mi}", {"islands": "modified"}, mi))
+    # Algorithm 3 with eq. (A matrices): 64 particles per PE, N / 64 PEs, one stage per PE bit
+    scheds.append(("paper_stages_M64", {"digit_sets": True}, -64))
     curves = []
     for name, kw, mi in scheds:
         for N in Ns:
             if kw is None:
                 rad = (N,)
+            elif mi < 0:
+                rad = (-mi,) + (2,) * int(round(np.log2(N // -mi)))
             elif mi:
                 if not 16 <= N // mi <= 1024:
                     continue
@@ -647,6 +666,17 @@ def ours_main(a):
     peak_src = "measured" if peak else "fallback"
     peak = peak or 6800.0
     traffic = _profiled_traffic(a.workload)
+    # Second roofline: instruction issue.  Peak = SMs x 4 schedulers x 32 lanes x median SM clock.
+    ipp = _profiled_issue(a.workload)
+    issue_roofline = None
+    if ipp is not None and clk.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_i = sms * 4 * 32 * clk["sm_mhz"] * 1e6
+        ach_i = ipp * value / world
+        issue_roofline = {"thread_instructions_per_particle": ipp, "achieved": ach_i, "peak": peak_i,
+                          "unit": "thread instructions/s", "frac": ach_i / peak_i,
+                          "source": "instruction count from the committed ncu capture; peak from the SM count "
+                                    "and the median SM clock sampled during the timed steps"}
     cpu = None
     if not a.no_cpu_baseline:
         try:
@@ -670,6 +700,7 @@ def ours_main(a):
                      "frac": achieved_gbs / peak, "traffic": traffic,
                      "peak_source": f"{peak_src} hbm_gbs (copy, burst)",
                      "algorithmic_bytes_per_launch": sum(bytes_steps) / K},
+        "issue_roofline": issue_roofline,
         "cpu_baseline": cpu,
         "e2e": {"value": e2e_value, "unit": METRIC, "h2d_bytes_per_step": 4 * w.model.dy,
                 "d2h_bytes_per_step": 4 * w.model.d + 8 + 4, "loglik": ll_e2e},
