@@ -295,15 +295,18 @@ def step_adaptive(model, radices: Sequence[int], seed: int, st: State, y_n: np.n
     return new, dict(stages=stages, inc=inc, mean=mean, ess=ess, ess_final=e, lV_new=cur, c=c_n)
 
 
-def island_stages(lW: np.ndarray, seed: int, n: int, modified: bool = True):
+def island_stages(lW: np.ndarray, seed: int, n: int, modified: bool = True, theta: Optional[float] = None):
     """Augmented island resampling (Algorithm 6; Algorithm 7 when ``modified``) on the
     log island weights lW (m = 2^S islands).  Stage s = 1..S pairs island i with
     i xor 2^(s-1) (matrices bold-A_s); both members of a pair get the pair's mean
     weight, and each island draws, by the integer rule on the pair's two weights
     with its own uniform (island_words_at(seed, n, s, i)), the island whose whole
     sample it holds next.  Algorithm 7 undoes a draw in which the two islands
-    would merely swap their samples.  Returns (holder, lW_final, per-stage info):
-    holder[i] = the island whose input sample island i ends up holding."""
+    would merely swap their samples.  With ``theta`` (fully adapted, Section 1.2)
+    the ESS of the island weights is evaluated before every stage and the
+    remaining stages are skipped once it reaches theta.  Returns (holder,
+    lW_final, per-stage info): holder[i] = the island whose input sample island
+    i ends up holding."""
     m = len(lW)
     S = int(np.log2(m))
     if 1 << S != m:
@@ -312,6 +315,8 @@ def island_stages(lW: np.ndarray, seed: int, n: int, modified: bool = True):
     holder = np.arange(m)
     info = []
     for s in range(1, S + 1):
+        if theta is not None and ess_of(V) >= theta:
+            break
         b = 1 << (s - 1)
         H = m // (2 * b)
         Vr = V.reshape(H, 2, b)
@@ -332,19 +337,22 @@ def island_stages(lW: np.ndarray, seed: int, n: int, modified: bool = True):
             Lp = Mx + np.log(np.sum(np.exp(Vr - Mx), axis=1, keepdims=True)) - np.log(2.0)
         V = np.broadcast_to(Lp, Vr.shape).reshape(m).copy()
         holder = holder[c]
-        info.append(dict(s=s, q=q.reshape(m), u=u.reshape(m), choice=c, swaps_undone=int(np.sum(swapped))))
+        info.append(dict(s=s, q=q.reshape(m), u=u.reshape(m), choice=c, swaps_undone=int(np.sum(swapped)),
+                         ess_before=ess_of(Vr.reshape(m))))
     return holder, V, info
 
 
 def step_islands(model, M: int, m: int, seed: int, st: State, y_n: np.ndarray, modified: bool = True,
-                 mu_used: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
+                 mu_used: Optional[float] = None, theta: Optional[float] = None) -> (State, Dict[str, np.ndarray]):
     """One time step of AIRPF (Algorithm 4): N = M m particles in m islands of M
     consecutive particles.  Weight with g_n; within-island multinomial resampling
     (Algorithm 5: the stage on digit 0 of radices (M, m), island weight = mean g of
     the island, eq. (out weight)), drawn with stage counter t = 2n; augmented island
     resampling (Algorithm 6 / 7) over S = log2 m stages; every particle of island i
     takes the particle at the same place in the sample island i holds; mutation
-    (normals numbered by the particle index).  Afterwards all weights are equal."""
+    (normals numbered by the particle index).  Afterwards all weights are equal,
+    unless ``theta`` (AIRPF2: fully adapted island stages) stopped the island
+    stages early, in which case every particle carries its island's weight."""
     N = M * m
     radices = (M, m)
     n = st.n
@@ -353,11 +361,11 @@ def step_islands(model, M: int, m: int, seed: int, st: State, y_n: np.ndarray, m
     inc, mean, ess, lme = summaries(lw, st.x, c_n, mu_sub, st.mu)
     x1, lV1, anc1, q1, u1, _ = stage(radices, seed, st.x, lw, 0, 2 * n)
     lW = lV1[::M]
-    holder, V, info = island_stages(lW, seed, n, modified)
+    holder, V, info = island_stages(lW, seed, n, modified, theta)
     src = (holder[np.arange(N) // M] * M + np.arange(N) % M)
     x_hat = x1[src]
     x_next = mutate(model, x_hat, n, seed, idx=np.arange(N))
-    new = State(x=x_next, lV=np.full(N, V[0]), mu=lme, n=n + 1, loglik=st.loglik + inc)
+    new = State(x=x_next, lV=V[np.arange(N) // M], mu=lme, n=n + 1, loglik=st.loglik + inc)
     return new, dict(inc=inc, mean=mean, ess=ess, within=dict(anc=anc1, q=q1, u=u1, lV=lV1), holder=holder,
                      island_info=info, lW=lW, lW_final=V, x_within=x1, c=c_n)
 
@@ -435,7 +443,9 @@ def run(model, N: int, radices: Sequence[int], seed: int, y: np.ndarray,
         if all_stages == "sets":     # Algorithm 3 with eq. (A matrices): digit sets {0, s}
             st, o = step_digit_sets(model, radices, seed, st, y[t])
         elif islands is not None:    # "modified" (Algorithm 7) or "plain" (Algorithm 6); radices = (M, m)
-            st, o = step_islands(model, radices[0], radices[1], seed, st, y[t], islands == "modified")
+            st, o = step_islands(model, radices[0], radices[1], seed, st, y[t], islands == "modified",
+                                 theta=theta)
+            executed += len(o["island_info"])
         elif theta is not None:
             st, o = step_adaptive(model, radices, seed, st, y[t], theta, rotate)
             executed += len(o["stages"])

@@ -307,7 +307,9 @@ class ButterflyFilter:
         """(x (N, d) float32, lV (N / a_prev,) float32, dict(n, loglik, mu, mu_used))."""
         t = self.steps * (self.m if (self.all_stages or self.islands) else 1)    # stage counter
         kp = (t - 1) % self.m
-        if self.adaptive:
+        if self.adaptive and self.islands:      # AIRPF2: one weight per island
+            nlv = self.N // self.radices[0]
+        elif self.adaptive:
             nlv = self.N
         elif self.digit_sets:                   # groups of the last set {0, m-1}
             nlv = self.N // (self.radices[0] * self.radices[-1])

@@ -319,6 +319,8 @@ struct IslandParams {
   float* lV_next;       // [M] carried log weights of the next step (all equal)
   uint32_t M, islands, S;
   uint32_t plain;       // 1: Algorithm 6 as printed (no undoing of swaps)
+  uint32_t adaptive;    // 1: ESS test before every island stage (AIRPF2); lV_next then per island
+  float theta;          // its threshold
 };
 
 constexpr int kScanItems = 16;

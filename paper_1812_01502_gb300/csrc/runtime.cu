@@ -63,6 +63,8 @@ struct Plan {
   bool sets = false;          // PF_DIGIT_SETS: stage s on digits {0, s}, m - 1 launches per step
   bool islands = false;       // PF_ISLANDS: radices (M, m), 3 launches per step
   bool island_plain = false;
+  bool island_adaptive = false;   // PF_ISLANDS | PF_ADAPTIVE (AIRPF2): ESS test before every island stage
+  float island_theta = 0.5f;
   IslandKernels ik{};
   int chunk_len = 64;
   KernelSet ks{};
@@ -233,9 +235,14 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
   pl.islands = opts && (opts->flags & PF_ISLANDS);
   pl.island_plain = pl.islands && (opts->flags & PF_ISLANDS_PLAIN);
   if (pl.islands) {
-    if (opts->flags & (PF_ALL_STAGES | PF_ADAPTIVE | PF_RECORD_ANCESTORS)) {
-      msg = "PF_ISLANDS cannot be combined with PF_ALL_STAGES, PF_ADAPTIVE or PF_RECORD_ANCESTORS";
+    if (opts->flags & (PF_ALL_STAGES | PF_ROTATE | PF_DIGIT_SETS | PF_RECORD_ANCESTORS)) {
+      msg = "PF_ISLANDS cannot be combined with PF_ALL_STAGES, PF_ROTATE, PF_DIGIT_SETS or PF_RECORD_ANCESTORS";
       return PF_EINVAL;
+    }
+    if (opts->flags & PF_ADAPTIVE) {     // AIRPF2
+      if (!(opts->ess_threshold >= 0.0f)) { msg = "ess_threshold must be >= 0"; return PF_EINVAL; }
+      pl.island_adaptive = true;
+      pl.island_theta = opts->ess_threshold > 0.0f ? opts->ess_threshold : 0.5f;
     }
     if (m != 2 || radices[1] < 2 || radices[1] > (int64_t)kMaxIslands || (radices[1] & (radices[1] - 1))) {
       msg = "PF_ISLANDS needs radices (M, m) with m a power of two, 2 <= m <= 16384";
@@ -384,13 +391,20 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
   pl.sps = (opts && (opts->flags & PF_ALL_STAGES)) ? (uint32_t)m : pl.sets ? (uint32_t)m - 1 : 1u;
   if (pl.islands) {           // the within-island stage is stage 0 of a two-stage step
     pl.sps = 2;
+    if (pl.island_adaptive) {   // carried weights per island: the within-island stage reads lV[i / M]
+      DigitGeom& g0 = pl.geom[0];
+      g0.prev_s = 1;
+      g0.prev_sw = 1;
+      g0.div_prev_as = make_fastdiv(g0.a);
+      g0.div_prev_s = make_fastdiv(1);
+    }
     if (!select_island_kernels(d, pl.kind, pl.ik)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
   }
   if (pl.sps > 1 && opts && (opts->flags & PF_RECORD_ANCESTORS)) {
     msg = "PF_RECORD_ANCESTORS records one stage; it cannot be combined with PF_ALL_STAGES";
     return PF_EINVAL;
   }
-  if (opts && (opts->flags & PF_ADAPTIVE)) {
+  if (opts && (opts->flags & PF_ADAPTIVE) && !pl.islands) {
     if (opts->flags & (PF_ALL_STAGES | PF_RECORD_ANCESTORS)) {
       msg = "PF_ADAPTIVE cannot be combined with PF_ALL_STAGES or PF_RECORD_ANCESTORS";
       return PF_EINVAL;
@@ -410,7 +424,7 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     DigitPlan& dp = pl.dp[k];
     const DigitGeom& g = pl.geom[k];
     int G = 0;
-    const void* gk = (pow2 && g.a <= 32 && !pl.adaptive && !pl.sets) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged) : nullptr;
+    const void* gk = (pow2 && g.a <= 32 && !pl.adaptive && !pl.sets && !pl.island_adaptive) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged) : nullptr;
     if (gk && G > 0) {
       const uint32_t gpb = kBlock / G;
       const uint32_t ngroups = pl.N / g.a;
@@ -689,6 +703,8 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
       while ((1u << S) < ip.islands) ++S;
       ip.S = S;
       ip.plain = pl.island_plain ? 1u : 0u;
+      ip.adaptive = pl.island_adaptive ? 1u : 0u;
+      ip.theta = pl.island_theta;
     }
   }
   if (pl.global) {
@@ -871,7 +887,8 @@ pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars)
   } else if (lV) {
     const uint64_t t = (uint64_t)st.n * pl.sps + st.stage;   // stage counter
     const int kp = pl.sets ? (int)(1 + (t + pl.m - 2) % (pl.m - 1)) : (int)((t + pl.m - 1) % pl.m);
-    const size_t cnt = pl.global ? 1 : pl.N / (pl.geom[kp].a * pl.geom[kp].w);
+    const size_t cnt = pl.global ? 1 : pl.island_adaptive ? pl.N / pl.geom[0].a
+                                     : pl.N / (pl.geom[kp].a * pl.geom[kp].w);
     PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[t & 1u], 4 * cnt, cudaMemcpyDeviceToHost, h->stream));
     PF_CUDA(h, cudaStreamSynchronize(h->stream));
   }
@@ -906,7 +923,7 @@ pf_status pf_stage_count(const pf_handle* h, uint64_t* out) {
   DevState st;
   PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
-  *out = h->plan.adaptive ? st.nstages : (uint64_t)st.n * h->plan.sps + st.stage;
+  *out = (h->plan.adaptive || h->plan.island_adaptive) ? st.nstages : (uint64_t)st.n * h->plan.sps + st.stage;
   return PF_OK;
 }
 
@@ -921,6 +938,7 @@ pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
                   ", \"islands\": " + std::to_string(pl.islands ? pl.geom[1].a : 0) +
                   ", \"digit_sets\": " + (pl.sets ? "true" : "false") +
                   ", \"island_resampling\": \"" + (pl.islands ? (pl.island_plain ? "algorithm6" : "algorithm7") : "") +
+                  (pl.island_adaptive ? "+adapted" : "") +
                   "\", \"digits\": [";
   if (pl.global)
     o += "{\"a\": " + std::to_string(pl.N) + ", \"s\": 1, \"kernel\": \"global\", \"scan_tiles\": " +

@@ -36,7 +36,52 @@ __global__ void __launch_bounds__(kIslandThreads) island_stages_kernel(const __g
   }
   __syncthreads();
   const float log2f_ = 0.69314718055994531f;
+  __shared__ float s_red[3][kIslandThreads / 32];
+  __shared__ uint32_t s_stop;
+  uint32_t executed = 0;
   for (uint32_t s = 1; s <= ip.S; ++s) {
+    if (ip.adaptive) {
+      // AIRPF2: ESS of the island weights, (sum W)^2 / (m sum W^2); stop once >= theta
+      const uint32_t lane = tid & 31u, warp = tid >> 5;
+      float mx = -INFINITY;
+      for (uint32_t i = tid; i < ip.islands; i += blockDim.x) mx = fmaxf(mx, V[i]);
+#pragma unroll
+      for (int off = 16; off; off >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      if (lane == 0) s_red[0][warp] = mx;
+      __syncthreads();
+      mx = -INFINITY;
+      for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2) mx = fmaxf(mx, s_red[0][w2]);
+      float a1 = 0.0f, a2 = 0.0f;
+      if (mx != -INFINITY) {
+        for (uint32_t i = tid; i < ip.islands; i += blockDim.x) {
+          const float e = expf(V[i] - mx);
+          a1 += e;
+          a2 = fmaf(e, e, a2);
+        }
+      }
+#pragma unroll
+      for (int off = 16; off; off >>= 1) {
+        a1 += __shfl_xor_sync(0xffffffffu, a1, off);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, off);
+      }
+      if (lane == 0) {
+        s_red[1][warp] = a1;
+        s_red[2][warp] = a2;
+      }
+      __syncthreads();
+      if (tid == 0) {
+        double S1 = 0.0, S2 = 0.0;
+        for (uint32_t w2 = 0; w2 < blockDim.x / 32; ++w2) {
+          S1 += s_red[1][w2];
+          S2 += s_red[2][w2];
+        }
+        const double ess = S1 * S1 / ((double)ip.islands * S2);   // NaN when every weight is zero
+        s_stop = (ess >= (double)ip.theta) ? 1u : 0u;
+      }
+      __syncthreads();
+      if (s_stop) break;
+    }
+    ++executed;
     const uint32_t lb = s - 1, b = 1u << lb;
     for (uint32_t q = tid; q < ip.islands / 2; q += blockDim.x) {
       const uint32_t i0 = ((q >> lb) << (lb + 1)) + (q & (b - 1));   // member 0: bit s-1 clear
@@ -74,7 +119,12 @@ __global__ void __launch_bounds__(kIslandThreads) island_stages_kernel(const __g
     __syncthreads();
   }
   for (uint32_t i = tid; i < ip.islands; i += blockDim.x) ip.src[i] = H[i];
-  for (uint32_t j = tid; j < ip.M; j += blockDim.x) ip.lV_next[j] = V[0];
+  if (ip.adaptive) {        // carried weight of every particle = its island's weight
+    for (uint32_t i = tid; i < ip.islands; i += blockDim.x) ip.lV_next[i] = V[i];
+    if (tid == 0) p.st->nstages += executed;
+  } else {
+    for (uint32_t j = tid; j < ip.M; j += blockDim.x) ip.lV_next[j] = V[0];
+  }
 }
 
 // Gather + mutation: particle (island i, place j) <- particle (src[i], j).

@@ -270,25 +270,38 @@ def check_step_adaptive(filt, model, radices, seed, y_n, n, theta, rotate, start
                   max_inc_err=e_inc, max_mean_err=e_mean, max_ess_err=e_ess), new.start
 
 
-def check_step_islands(filt, model, M, m, seed, y_n, n, modified):
+def check_step_islands(filt, model, M, m, seed, y_n, n, modified, theta=None):
     """GPU AIRPF step n (PF_ISLANDS) against the oracle's AIRPF step from the same
     state.  A particle's new state must match when its within-island draw and
     every island-stage draw on its island's line of holders is decidable (with
-    Algorithm 7 an island's choice also depends on its partner's draw)."""
+    Algorithm 7 an island's choice also depends on its partner's draw).  With
+    ``theta`` (AIRPF2) the number of island stages run must match too, unless an
+    ESS lies within 1e-5 of theta (then the step is reported as ambiguous)."""
     N = M * m
     x0, lv0, sc = filt.state()
     assert sc["n"] == n
+    c0 = filt.stage_count() if theta is not None else 0
     mean, inc, ess = filt.step(y_n)
     x1, lv1, sc1 = filt.state()
-    lV = per_particle_lV(lv0, (M, m), 2 * n).astype(np.float64)
+    if theta is not None:       # one carried weight per island
+        lV = lv0[np.arange(N) // M].astype(np.float64)
+    else:
+        lV = per_particle_lV(lv0, (M, m), 2 * n).astype(np.float64)
     st = bpf.State(x=x0.astype(np.float64), lV=lV, mu=sc["mu"], n=n)
-    new, o = bpf.step_islands(model, M, m, seed, st, y_n, modified, mu_used=sc["mu_used"])
+    new, o = bpf.step_islands(model, M, m, seed, st, y_n, modified, mu_used=sc["mu_used"], theta=theta)
     e_inc = abs(inc - o["inc"]) / max(1.0, abs(o["inc"]))
     e_mean = rel_err(mean, o["mean"])
     e_ess = abs(ess - o["ess"]) / max(o["ess"], 1e-12)
     assert e_inc <= TOL_INC, f"step {n}: likelihood increment error {e_inc}"
     assert e_mean <= TOL_STATE, f"step {n}: mean error {e_mean}"
     assert e_ess <= 1e-4, f"step {n}: ess error {e_ess}"
+    if theta is not None:
+        tested = [i["ess_before"] for i in o["island_info"]]
+        if len(o["island_info"]) < int(np.log2(m)):
+            tested.append(bpf.ess_of(o["lW_final"]))
+        if any(abs(e - theta) <= 1e-5 * theta for e in tested):
+            return Report(ambiguous_steps=1)
+        assert filt.stage_count() - c0 == len(o["island_info"]), f"step {n}: island stages run differ"
     w = o["within"]
     lo, hi = plausible_members(w["q"].reshape(m, M, 1), w["u"].reshape(m, M, 1), axis=1)
     dec_w = (lo == hi).reshape(N)
@@ -307,7 +320,7 @@ def check_step_islands(filt, model, M, m, seed, y_n, n, modified):
     src = o["holder"][np.arange(N) // M] * M + np.arange(N) % M
     ok = line[np.arange(N) // M] & dec_w[src]
     e_x = rel_err(x1[ok], new.x[ok])
-    e_lv = rel_err(lv1, np.full(lv1.shape, new.lV[0]))
+    e_lv = rel_err(lv1, new.lV[::M] if theta is not None else np.full(lv1.shape, new.lV[0]))
     assert e_x <= TOL_STATE, f"step {n}: state error {e_x}"
     assert e_lv <= TOL_STATE, f"step {n}: log-weight error {e_lv}"
     assert abs(sc1["mu"] - new.mu) <= 1e-6 * max(1.0, abs(new.mu))

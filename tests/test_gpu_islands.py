@@ -34,6 +34,35 @@ def test_islands_lockstep(bfpf, name, model, M, m, modified, T):
     assert rep["undecided_particles"] <= max(16, 0.02 * N * T)
 
 
+@pytest.mark.parametrize("name,model,M,m,theta,T", [
+    ("sv_16x64_half", S.sv_model(), 16, 64, 0.5, 6),
+    ("lg4_32x256_09", S.lg_dense(4, seed=3), 32, 256, 0.9, 4),
+    ("lg1_30x16_all", S.lg_scalar(r=0.1), 30, 16, 1.5, 4),
+    ("lg1_64x128_none", S.lg_scalar(r=0.1), 64, 128, 1e-9, 4),
+    ("lg2_8x2048_07", S.lg_dense(2, seed=6), 8, 2048, 0.7, 4),
+])
+def test_airpf2_lockstep(bfpf, name, model, M, m, theta, T):
+    """AIRPF2: the island stages run while the ESS of the island weights is below theta."""
+    N = M * m
+    y = S.simulate(model, T, seed=71)[1]
+    seed = 717
+    f = bfpf.ButterflyFilter(model, N, (M, m), seed, islands="modified", adaptive=True, ess_threshold=theta)
+    assert "adapted" in f.describe()["island_resampling"]
+    rep = LS.Report()
+    for n in range(T):
+        r = LS.check_step_islands(f, model, M, m, seed, y[n], n, True, theta=theta)
+        rep.merge(r)
+        if r.get("ambiguous_steps"):
+            break
+    stages = f.stage_count()
+    f.close()
+    print(name, dict(rep), "island stages", stages)
+    if theta > 1:
+        assert stages == int(np.log2(m)) * T
+    if theta < 1e-6:
+        assert stages == 0
+
+
 def test_islands_graph_equals_steps(bfpf):
     model, M, m = S.sv_model(), 64, 32
     y = S.simulate(model, 30, seed=53)[1]

@@ -100,3 +100,33 @@ def test_airpf_mean_converges_to_kalman():
                         - kf["mean"][:, 0]) ** 2) for r in range(6)]
         mses.append(np.mean(errs))
     assert mses[1] < mses[0] / 6, mses       # 16x the particles: about 16x less error
+
+
+def test_airpf2_theta_limits():
+    """Fully adapted island stages: theta > 1 runs every stage (= AIRPF1), theta = 0
+    none (each island keeps its own sample and its weight)."""
+    model = S.sv_model()
+    M, m = 8, 16
+    y = S.simulate(model, 4, seed=5)[1]
+    a = bpf.init_state(model, M * m, seed=3)
+    b = bpf.init_state(model, M * m, seed=3)
+    c = bpf.init_state(model, M * m, seed=3)
+    for n in range(4):
+        a, oa = bpf.step_islands(model, M, m, 3, a, y[n])
+        b, ob = bpf.step_islands(model, M, m, 3, b, y[n], theta=1.5)
+        np.testing.assert_array_equal(a.x, b.x)
+        assert len(ob["island_info"]) == 4
+        c, oc = bpf.step_islands(model, M, m, 3, c, y[n], theta=0.0)
+        assert oc["island_info"] == [] and np.array_equal(oc["holder"], np.arange(m))
+        np.testing.assert_allclose(c.lV.reshape(m, M), oc["lW"][:, None] * np.ones((1, M)), rtol=0, atol=0)
+
+
+def test_airpf2_stops_at_threshold():
+    rng = np.random.default_rng(3)
+    lW = rng.normal(scale=2.0, size=64)
+    theta = 0.6
+    holder, V, info = bpf.island_stages(lW, 9, 1, True, theta)
+    for st in info:
+        assert st["ess_before"] < theta
+    if len(info) < 6:
+        assert bpf.ess_of(V) >= theta
