@@ -437,7 +437,7 @@ def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
     (sum over steps and components, mean over J runs) and time per step, for
     the one-digit schedule, all stages per step, fully adapted resampling at
     several thresholds (with and without the rotated start), AIRPF with 64 and
-    256 islands, the paper's own stage matrices (64 particles per PE, one stage
+    256 islands, AIRPF2 (fully adapted island stages), the paper's own stage matrices (64 particles per PE, one stage
     per PE bit) and the global filter.  Times are whole-run device times through pf_run (CUDA graphs)."""
     import numpy as np
     import torch
@@ -454,6 +454,8 @@ def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
     scheds.append(("global", None, 0))
     for mi in (64, 256):        # AIRPF (Algorithm 4 with Algorithm 7): mi islands of N / mi particles
         scheds.append((f"airpf_m{mi}", {"islands": "modified"}, mi))
+    # AIRPF2: island stages fully adapted (ESS of the island weights against theta = 0.5)
+    scheds.append(("airpf2_m256_0.5", {"islands": "modified", "adaptive": True, "ess_threshold": 0.5}, 256))
     # Algorithm 3 with eq. (A matrices): 64 particles per PE, N / 64 PEs, one stage per PE bit
     scheds.append(("paper_stages_M64", {"digit_sets": True}, -64))
     curves = []
@@ -469,7 +471,7 @@ def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
                 rad = (N // mi, mi)
             else:
                 rad = _radix16(N)
-            if kw is not None and kw.get("adaptive") and len(rad) == 1 and N > 1024:
+            if kw is not None and kw.get("adaptive") and not kw.get("islands") and len(rad) == 1 and N > 1024:
                 continue
             mses, ts, stages = [], [], []
             for j in range(J):

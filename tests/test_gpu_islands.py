@@ -83,4 +83,4 @@ def test_islands_invalid(bfpf):
     with pytest.raises(bfpf.PFError):
         bfpf.ButterflyFilter(m, 64, (4, 4, 4), 1, islands="modified")          # not (M, m)
     with pytest.raises(bfpf.PFError):
-        bfpf.ButterflyFilter(m, 64, (8, 8), 1, islands="modified", adaptive=True)
+        bfpf.ButterflyFilter(m, 64, (8, 8), 1, islands="modified", all_stages=True)
