@@ -197,6 +197,7 @@ struct DigitGeom {
   // prev_s / w; 1 and prev_s for a plain digit stage
   uint32_t w, prev_sw;
   FastDiv div_w, div_nlw;
+  uint32_t team;      // lanes per group in the tile kernels' group phase (power of two <= 32)
 };
 
 // Geometry of one digit for the register-resident group kernel (power-of-two

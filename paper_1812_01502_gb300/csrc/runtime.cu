@@ -329,8 +329,18 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     g.div_prev_as = make_fastdiv(pl.geom[kp].a * pl.geom[kp].s);
     g.div_prev_s = make_fastdiv(pl.geom[kp].s);
   }
+  // Lanes per group in the tile kernels' group phase: one lane for groups of up
+  // to 32 members (a serial pass is cheapest there), else a power of two <= 32
+  // that leaves each lane at least 8 members.
+  auto team_for = [](uint32_t members) {
+    uint32_t t = 1;
+    if (members <= 32) return t;
+    while (t * 2 <= 32 && t * 2 * 8 <= members) t *= 2;
+    return t;
+  };
   for (int k = 0; k < m; ++k) {
     DigitGeom& g = pl.geom[k];
+    g.team = team_for(g.a);
     g.div_tgroups = make_fastdiv(g.nh * g.nl);
     g.w = 1;
     g.prev_sw = g.prev_s;
@@ -383,6 +393,7 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
       g.div_w = make_fastdiv(w);
       g.div_nlw = make_fastdiv(g.nl / w);
       g.div_tgroups = make_fastdiv(g.nh * (g.nl / w));
+      g.team = team_for(G);
       pl.cap = std::max(pl.cap, g.tile_n);
       pl.max_tiles = std::max(pl.max_tiles, g.ntiles);
       if (g.wide) pl.wide = true;

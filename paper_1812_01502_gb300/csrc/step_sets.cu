@@ -103,27 +103,34 @@ __device__ __forceinline__ void set_tile_steps(const TileCtx& ctx, uint32_t firs
     __syncthreads();
 
     // ---- per group: max, log-sum-exp, integer weights and prefix sums ----
-    for (uint32_t gid = tid; gid < ngroups; gid += kBlock) {
-      const uint32_t hh = fdiv(gid, g.div_nlw);
-      const uint32_t cg = gid - hh * nlw;
-      const uint32_t p0 = hh * a * nl + cg * w;
-      float M = -INFINITY;
-      for (uint32_t rs = 0; rs < a; ++rs)
-        for (uint32_t r0 = 0; r0 < w; ++r0) M = fmaxf(M, s_lw[p0 + rs * nl + r0]);
-      float s1 = 0.0f, s2 = 0.0f, sx[D];
+    // (a team of T lanes per group, as in tile_steps; members rho in order)
+    {
+      const uint32_t T = g.team, lt = tid & (T - 1u);
+      const uint32_t tpb = kBlock / T;
+      const uint32_t C = (G + T - 1u) / T;
+      const uint32_t rb = min(G, lt * C), re = min(G, rb + C);
+      const uint32_t rounds = (ngroups + tpb - 1u) / tpb;
+      for (uint32_t rd = 0; rd < rounds; ++rd) {
+        const uint32_t gid = rd * tpb + tid / T;
+        const bool active = gid < ngroups;
+        uint32_t hh = 0, cg = 0;
+        if (active) {
+          hh = fdiv(gid, g.div_nlw);
+          cg = gid - hh * nlw;
+        }
+        const uint32_t p0 = hh * a * nl + cg * w;
+        float M = -INFINITY;
+        if (active)
+          for (uint32_t rho = rb; rho < re; ++rho) M = fmaxf(M, s_lw[mpos(p0, rho)]);
+        for (uint32_t off = 1; off < T; off <<= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, off));
+        float s1 = 0.0f, s2 = 0.0f, sx[D];
 #pragma unroll
-      for (int t = 0; t < D; ++t) sx[t] = 0.0f;
-      float L;
-      if (M == -INFINITY) {
-        for (uint32_t rs = 0; rs < a; ++rs)
-          for (uint32_t r0 = 0; r0 < w; ++r0) s_P[p0 + rs * nl + r0] = 0;
-        status |= kStatusZeroGroup;
-        L = -INFINITY;
-      } else {
-        PT P = 0;
-        for (uint32_t rs = 0; rs < a; ++rs) {
-          for (uint32_t r0 = 0; r0 < w; ++r0) {
-            const uint32_t pos = p0 + rs * nl + r0;
+        for (int t = 0; t < D; ++t) sx[t] = 0.0f;
+        PT run = 0;
+        const bool live = active && M != -INFINITY;
+        if (live) {
+          for (uint32_t rho = rb; rho < re; ++rho) {
+            const uint32_t pos = mpos(p0, rho);
             const float e = exp_weight(s_lw[pos] - M);
             s1 += e;
             s2 = fmaf(e, e, s2);
@@ -132,14 +139,30 @@ __device__ __forceinline__ void set_tile_steps(const TileCtx& ctx, uint32_t firs
             PT q;
             if (WIDE && wide_digit) q = (PT)__float2ull_rz(e * 4294967296.0f);
             else q = (PT)__float2uint_rz(e * 16777216.0f);
-            P += q;
-            s_P[pos] = P;
+            run += q;
+            s_P[pos] = run;
           }
+        } else if (active) {
+          for (uint32_t rho = rb; rho < re; ++rho) s_P[mpos(p0, rho)] = 0;
         }
-        L = M + logf(s1);
+        PT incl = run;
+        for (uint32_t off = 1; off < T; off <<= 1) {
+          const PT v = __shfl_up_sync(0xffffffffu, incl, off, T);
+          if (lt >= off) incl += v;
+        }
+        const PT excl = incl - run;
+        if (live && excl != 0)
+          for (uint32_t rho = rb; rho < re; ++rho) s_P[mpos(p0, rho)] += excl;
+        // each lane folds its own chunk into its running partial (same max M for the
+        // whole team); only the group's sum of weights is needed here, for L
+        float sg = s1;
+        for (uint32_t off = 1; off < T; off <<= 1) sg += __shfl_xor_sync(0xffffffffu, sg, off);
+        if (live) merge_partial<D>(acc, accx, M, s1, s2, sx);
+        if (!active || lt != 0) continue;
+        if (!live) status |= kStatusZeroGroup;
+        const float L = live ? M + logf(sg) : -INFINITY;
+        lV_out[(h0 + hh) * sw + l0 / w + cg] = L - g.log_a;
       }
-      lV_out[(h0 + hh) * sw + l0 / w + cg] = L - g.log_a;
-      merge_partial<D>(acc, accx, M, s1, s2, sx);
     }
     __syncthreads();
 

@@ -126,47 +126,79 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
     __syncthreads();
 
     // ---- per group: max, log-sum-exp, integer weights and prefix sums ----
-    for (uint32_t gid = tid; gid < ngroups; gid += kBlock) {
-      const uint32_t hh = fdiv(gid, g.div_nl);
-      const uint32_t col = gid - hh * nl;
-      const uint32_t p0 = hh * a * nl + col;
-      float M = -INFINITY;
-      for (uint32_t r = 0; r < a; ++r) M = fmaxf(M, s_lw[p0 + r * nl]);
-      float s1 = 0.0f, s2 = 0.0f, sx[D];
-#pragma unroll
-      for (int t = 0; t < D; ++t) sx[t] = 0.0f;
-      float L;
-      if (M == -INFINITY) {
-        for (uint32_t r = 0; r < a; ++r) s_P[p0 + r * nl] = 0;
-        status |= kStatusZeroGroup;
-        L = -INFINITY;
-      } else {
-        PT P = 0;
-        for (uint32_t r = 0; r < a; ++r) {
-          const uint32_t pos = p0 + r * nl;
-          const float e = exp_weight(s_lw[pos] - M);
-          s1 += e;
-          s2 = fmaf(e, e, s2);
-#pragma unroll
-          for (int t = 0; t < D; ++t) sx[t] = fmaf(e, s_x[t * cap + pos], sx[t]);
-          PT q;
-          if (WIDE && wide_digit) q = (PT)__float2ull_rz(e * 4294967296.0f);
-          else q = (PT)__float2uint_rz(e * 16777216.0f);
-          P += q;
-          s_P[pos] = P;
+    // A team of T lanes (a power of two <= 32, T <= a) shares a group: lane lt
+    // takes members [lt C, lt C + C), C = ceil(a / T); max and sums by xor-shuffle,
+    // the prefix by an in-lane scan plus a shuffle scan over the team.  Every
+    // lane runs the same number of rounds, so the shuffles see the whole warp.
+    {
+      const uint32_t T = g.team, lt = tid & (T - 1u);
+      const uint32_t tpb = kBlock / T;
+      const uint32_t C = (a + T - 1u) / T;
+      const uint32_t rb = min(a, lt * C), re = min(a, rb + C);
+      const uint32_t rounds = (ngroups + tpb - 1u) / tpb;
+      for (uint32_t rd = 0; rd < rounds; ++rd) {
+        const uint32_t gid = rd * tpb + tid / T;
+        const bool active = gid < ngroups;
+        uint32_t hh = 0, col = 0;
+        if (active) {
+          hh = fdiv(gid, g.div_nl);
+          col = gid - hh * nl;
         }
-        L = M + logf(s1);
-      }
-      if constexpr (ADAPT) {
-        const uint32_t ib = base + hh * a * s + col;       // global index of member 0
-        for (uint32_t r = 0; r < a; ++r) lV_out[ib + r * s] = L - g.log_a;
-        float zx[D];
+        const uint32_t p0 = hh * a * nl + col;
+        float M = -INFINITY;
+        if (active)
+          for (uint32_t r = rb; r < re; ++r) M = fmaxf(M, s_lw[p0 + r * nl]);
+        for (uint32_t off = 1; off < T; off <<= 1) M = fmaxf(M, __shfl_xor_sync(0xffffffffu, M, off));
+        float s1 = 0.0f, s2 = 0.0f, sx[D];
 #pragma unroll
-        for (int t = 0; t < D; ++t) zx[t] = 0.0f;
-        merge_partial<D>(acc, accx, L, 1.0f, 1.0f / (float)a, zx);   // sum_i V_i, sum_i V_i^2 of the group
-      } else {
-        lV_out[(h0 + hh) * s + l0 + col] = L - g.log_a;
-        merge_partial<D>(acc, accx, M, s1, s2, sx);
+        for (int t = 0; t < D; ++t) sx[t] = 0.0f;
+        PT run = 0;
+        const bool live = active && M != -INFINITY;
+        if (live) {
+          for (uint32_t r = rb; r < re; ++r) {
+            const uint32_t pos = p0 + r * nl;
+            const float e = exp_weight(s_lw[pos] - M);
+            s1 += e;
+            s2 = fmaf(e, e, s2);
+#pragma unroll
+            for (int t = 0; t < D; ++t) sx[t] = fmaf(e, s_x[t * cap + pos], sx[t]);
+            PT q;
+            if (WIDE && wide_digit) q = (PT)__float2ull_rz(e * 4294967296.0f);
+            else q = (PT)__float2uint_rz(e * 16777216.0f);
+            run += q;
+            s_P[pos] = run;
+          }
+        } else if (active) {
+          for (uint32_t r = rb; r < re; ++r) s_P[p0 + r * nl] = 0;
+        }
+        PT incl = run;
+        for (uint32_t off = 1; off < T; off <<= 1) {
+          const PT v = __shfl_up_sync(0xffffffffu, incl, off, T);
+          if (lt >= off) incl += v;
+        }
+        const PT excl = incl - run;
+        if (live && excl != 0)
+          for (uint32_t r = rb; r < re; ++r) s_P[p0 + r * nl] += excl;
+        // each lane folds its own chunk into its running partial (same max M for the
+        // whole team); only the group's sum of weights is needed here, for L
+        float sg = s1;
+        for (uint32_t off = 1; off < T; off <<= 1) sg += __shfl_xor_sync(0xffffffffu, sg, off);
+        if (!ADAPT && live) merge_partial<D>(acc, accx, M, s1, s2, sx);
+        if (!active) continue;
+        const float L = live ? M + logf(sg) : -INFINITY;
+        if (!live && lt == 0) status |= kStatusZeroGroup;
+        if constexpr (ADAPT) {
+          const uint32_t ib = base + hh * a * s + col;       // global index of member 0
+          for (uint32_t r = rb; r < re; ++r) lV_out[ib + r * s] = L - g.log_a;
+          if (lt == 0) {
+            float zx[D];
+#pragma unroll
+            for (int t = 0; t < D; ++t) zx[t] = 0.0f;
+            merge_partial<D>(acc, accx, L, 1.0f, 1.0f / (float)a, zx);   // sum_i V_i, sum_i V_i^2 of the group
+          }
+        } else if (lt == 0) {
+          lV_out[(h0 + hh) * s + l0 + col] = L - g.log_a;
+        }
       }
     }
     __syncthreads();
