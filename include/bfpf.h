@@ -236,6 +236,24 @@ pf_status pf_get_ancestors(const pf_handle* h, int32_t* anc);
  * global-resampling scan gave up (results invalid).  Synchronises. */
 pf_status pf_get_status(const pf_handle* h, uint32_t* bits);
 
+/*
+ * Checkpoint / resume (no counterpart in the paper).  A checkpoint holds the
+ * filter's whole device workspace (particles, carried weights, normaliser,
+ * FP64 log-likelihood, step counter, pushed observations, output rings) and
+ * its host counters, behind a header naming the model, N, radices, seed and
+ * options.  The random numbers are counter-based (keyed by seed, step and
+ * particle), so a filter resumed from a checkpoint continues bit for bit as
+ * the uninterrupted one.
+ *   pf_checkpoint_size: bytes a checkpoint of h needs.
+ *   pf_save: writes it to buf (host memory, len >= that size); synchronises.
+ *   pf_load: restores h from buf; h must have been created with the same
+ *            model, N, radices, seed and options (else PF_EINVAL, h unchanged).
+ *            Synchronises.
+ */
+pf_status pf_checkpoint_size(const pf_handle* h, size_t* bytes);
+pf_status pf_save(const pf_handle* h, void* buf, size_t len);
+pf_status pf_load(pf_handle* h, const void* buf, size_t len);
+
 /* Number of resampling stages executed so far (PF_ADAPTIVE counts only the
  * stages its ESS test let run; otherwise one per stage launched).  Synchronises. */
 pf_status pf_stage_count(const pf_handle* h, uint64_t* out);

@@ -87,6 +87,9 @@ def load_library(path: str = LIB_PATH):
         "pf_get_ancestors": (i32, [vp, vp]),
         "pf_get_status": (i32, [vp, c.POINTER(u32)]),
         "pf_stage_count": (i32, [vp, c.POINTER(c.c_uint64)]),
+        "pf_checkpoint_size": (i32, [vp, c.POINTER(c.c_size_t)]),
+        "pf_save": (i32, [vp, vp, c.c_size_t]),
+        "pf_load": (i32, [vp, vp, c.c_size_t]),
         "pf_destroy": (i32, [vp]),
         "pf_describe": (i32, [vp, c.c_char_p, c.c_size_t]),
         "pf_last_error": (c.c_char_p, [vp]),
@@ -338,6 +341,24 @@ class ButterflyFilter:
         b = ctypes.c_uint32(0)
         _check(_lib.pf_get_status(self._h, ctypes.byref(b)), self._h)
         return b.value
+
+    def save(self) -> np.ndarray:
+        """Checkpoint (uint8 array): the whole filter state; see pf_save."""
+        n = ctypes.c_size_t(0)
+        _check(_lib.pf_checkpoint_size(self._h, ctypes.byref(n)), self._h)
+        buf = np.empty(int(n.value), dtype=np.uint8)
+        _check(_lib.pf_save(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes), self._h)
+        return buf
+
+    def load(self, buf) -> None:
+        """Restore a checkpoint taken with save() from a filter with the same model,
+        N, radices, seed and options; the run continues bit for bit."""
+        buf = np.ascontiguousarray(buf, dtype=np.uint8)
+        _check(_lib.pf_load(self._h, buf.ctypes.data_as(ctypes.c_void_p), buf.nbytes), self._h)
+        n = ctypes.c_double * 4
+        sc = n()
+        _check(_lib.pf_get_state(self._h, None, None, sc), self._h)
+        self.steps = int(sc[0])
 
     def stage_count(self) -> int:
         """Resampling stages executed so far (with adaptive=True, those the ESS test let run)."""

@@ -19,9 +19,19 @@
 #include "bfpf_device.cuh"
 #include "bfpf_kernels.h"
 
+#include <nvtx3/nvToolsExt.h>
+
 using namespace bfpf;
 
 namespace {
+
+// NVTX range for profilers and tracers (a no-op unless a tool is attached).
+struct Trace {
+  explicit Trace(const char* name) { nvtxRangePushA(name); }
+  ~Trace() { nvtxRangePop(); }
+  Trace(const Trace&) = delete;
+  Trace& operator=(const Trace&) = delete;
+};
 
 thread_local std::string t_error;
 
@@ -97,6 +107,9 @@ struct pf_handle {
   uint32_t launch_j[kMaxDigits] = {};    // stage-launch arguments of the fully adapted schedule
   StepParams Pisl[2]{};                  // AIRPF: step parameters by step parity (states ping-pong)
   IslandParams ipar[2]{};
+  uint32_t flags = 0;                    // pf_options.flags at creation
+  uint64_t seed = 0;
+  int32_t radices[kMaxDigits] = {};
   std::string err;
 };
 
@@ -648,6 +661,9 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   Plan& pl = h->plan;
   cudaGetDevice(&h->device);
   h->stream = opts ? static_cast<cudaStream_t>(opts->stream) : nullptr;
+  h->flags = opts ? opts->flags : 0u;
+  h->seed = seed;
+  for (int32_t k = 0; k < m; ++k) h->radices[k] = radices[k];
   if (workspace) {
     if (workspace_bytes < pl.lay.total) {
       delete h;
@@ -795,6 +811,7 @@ namespace {
 // radix phase t0 mod m, since the kernel depends on the digit) when L is the
 // chunk length, else individual launches.
 pf_status enqueue_steps(pf_handle* h, int32_t L) {
+  Trace tr("bfpf steps");
   const Plan& pl = h->plan;
   const uint64_t lps = pl.islands ? 3 : pl.adaptive ? (uint64_t)pl.m + 1 : pl.sps;   // launches per step
   const uint64_t t0 = h->n_host * lps;
@@ -926,6 +943,95 @@ pf_status pf_get_status(const pf_handle* h, uint32_t* bits) {
   PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   *bits = st.status;
+  return PF_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Checkpoint / resume: the whole device workspace plus the host counters.
+// ---------------------------------------------------------------------------
+namespace {
+
+struct CheckpointHeader {
+  char magic[8];            // "BFPFCKP1"
+  uint32_t version;
+  uint32_t N;
+  int32_t m, d, dy, kind;
+  int32_t radices[kMaxDigits];
+  uint32_t flags, pad;
+  uint64_t seed;
+  uint64_t model_hash;      // FNV-1a of the device model parameters
+  uint64_t ws_bytes;
+  uint64_t n_host, n_pushed;
+};
+
+uint64_t fnv1a(const void* data, size_t n) {
+  const unsigned char* b = static_cast<const unsigned char*>(data);
+  uint64_t hsh = 1469598103934665603ull;
+  for (size_t i = 0; i < n; ++i) {
+    hsh ^= b[i];
+    hsh *= 1099511628211ull;
+  }
+  return hsh;
+}
+
+void fill_header(const pf_handle* h, CheckpointHeader& hd) {
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, "BFPFCKP1", 8);
+  hd.version = 1;
+  hd.N = h->plan.N;
+  hd.m = h->plan.m;
+  hd.d = h->plan.d;
+  hd.dy = h->plan.dy;
+  hd.kind = h->plan.kind;
+  for (int k = 0; k < h->plan.m; ++k) hd.radices[k] = h->radices[k];
+  hd.flags = h->flags;
+  hd.seed = h->seed;
+  hd.model_hash = fnv1a(&h->plan.mp, sizeof(h->plan.mp));
+  hd.ws_bytes = h->plan.lay.total;
+  hd.n_host = h->n_host;
+  hd.n_pushed = h->n_pushed;
+}
+
+}  // namespace
+
+pf_status pf_checkpoint_size(const pf_handle* h, size_t* bytes) {
+  if (!h || !bytes) return fail(h, PF_EINVAL, "NULL argument");
+  *bytes = sizeof(CheckpointHeader) + h->plan.lay.total;
+  return PF_OK;
+}
+
+pf_status pf_save(const pf_handle* h, void* buf, size_t len) {
+  Trace tr("bfpf save");
+  if (!h || !buf) return fail(h, PF_EINVAL, "NULL argument");
+  if (len < sizeof(CheckpointHeader) + h->plan.lay.total) return fail(h, PF_EINVAL, "buffer smaller than pf_checkpoint_size()");
+  CheckpointHeader hd;
+  fill_header(h, hd);
+  std::memcpy(buf, &hd, sizeof(hd));
+  PF_CUDA(h, cudaMemcpyAsync(static_cast<unsigned char*>(buf) + sizeof(hd), h->ws, h->plan.lay.total,
+                             cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+pf_status pf_load(pf_handle* h, const void* buf, size_t len) {
+  Trace tr("bfpf load");
+  if (!h || !buf) return fail(h, PF_EINVAL, "NULL argument");
+  if (len < sizeof(CheckpointHeader)) return fail(h, PF_EINVAL, "buffer too small for a checkpoint");
+  CheckpointHeader hd, mine;
+  std::memcpy(&hd, buf, sizeof(hd));
+  fill_header(h, mine);
+  if (std::memcmp(hd.magic, mine.magic, 8) != 0 || hd.version != mine.version)
+    return fail(h, PF_EINVAL, "not a checkpoint of this library");
+  if (hd.N != mine.N || hd.m != mine.m || hd.d != mine.d || hd.dy != mine.dy || hd.kind != mine.kind ||
+      std::memcmp(hd.radices, mine.radices, sizeof(hd.radices)) != 0 || hd.flags != mine.flags ||
+      hd.seed != mine.seed || hd.model_hash != mine.model_hash || hd.ws_bytes != mine.ws_bytes)
+    return fail(h, PF_EINVAL, "the checkpoint was taken from a filter with another model, N, radices, seed or options");
+  if (len < sizeof(hd) + hd.ws_bytes) return fail(h, PF_EINVAL, "checkpoint truncated");
+  PF_CUDA(h, cudaMemcpyAsync(h->ws, static_cast<const unsigned char*>(buf) + sizeof(hd), hd.ws_bytes,
+                             cudaMemcpyHostToDevice, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  h->n_host = hd.n_host;
+  h->n_pushed = hd.n_pushed;
   return PF_OK;
 }
 
@@ -1350,6 +1456,7 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
 }
 
 pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_incs, float* means, float* ess) {
+  Trace tr("bfpf batch run");
   if (!b) return bfail(nullptr, PF_EINVAL, "batch is NULL");
   if (T < 0 || (T > 0 && !y)) return bfail(b, PF_EINVAL, "need T >= 0 and y != NULL");
   const int R = b->ring, F = b->F;

@@ -10,7 +10,9 @@ against ``memory_budget``) are free.  Every scheduling pass enqueues the next
 chunk of every active request that has one ready, so the chunks of different
 requests overlap on the device; completions are detected with CUDA events.
 
-Latency of a request = completion of its last chunk - its arrival.  The
+Latency of a request = completion of its last chunk - its arrival.  A request
+whose filter reports non-finite weights (a NaN observation, say) is finished
+with ``error`` set; the other requests are not affected.  The
 server reports p50 / p99 request latency, chunk latency and throughput in
 particle-steps/s.  The filtering itself runs in the library's kernels; this
 module only schedules.
@@ -45,6 +47,8 @@ class Request:
     means: Optional[np.ndarray] = None
     incs: Optional[np.ndarray] = None
     loglik: Optional[float] = None
+    status: int = 0                # sticky device status bits of the request's filter
+    error: Optional[str] = None    # set when the filter reported a failure (others keep running)
 
 
 def workspace_bytes(model, N: int, radices: Sequence[int]) -> int:
@@ -134,7 +138,14 @@ class Server:
                 req.finished = now
                 req.means = act.means.cpu().numpy()
                 req.incs = act.incs.cpu().numpy()
-                req.loglik = act.filt.loglik()
+                req.status = act.filt.status()
+                try:
+                    req.loglik = act.filt.loglik()
+                except Exception as ex:      # a failure of this request only
+                    req.loglik = None
+                    req.error = str(ex)
+                if req.status & 1 and req.error is None:
+                    req.error = "non-finite log-weights (e.g. a NaN observation)"
                 act.filt.close()
                 self.in_use -= act.nbytes
                 self.free_streams.append(act.slot)
@@ -174,13 +185,14 @@ class Server:
 
 
 def summarize(done: Sequence[Request], wall: float) -> dict:
+    failed = sum(1 for r in done if r.error)
     lat = np.array([r.finished - r.arrival for r in done])
     clat = np.array([c for r in done for c in r.chunk_latencies])
     ps = sum(r.N * len(r.y) for r in done)
     return {"requests": len(done), "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "p50_chunk_latency_s": float(np.percentile(clat, 50)),
             "p99_chunk_latency_s": float(np.percentile(clat, 99)), "wall_s": wall,
-            "particle_steps_per_s": ps / wall}
+            "particle_steps_per_s": ps / wall, "failed_requests": failed}
 
 
 def requests_from_stream(stream, chunk: int = 50) -> List[Request]:

@@ -60,3 +60,23 @@ def test_request_larger_than_budget_is_refused(bfpf):
     req = _requests(serve, n=1)[0]
     with pytest.raises(MemoryError):
         serve.Server(memory_budget=1024, slots=2).run([req])
+
+
+def test_failed_request_is_isolated(bfpf):
+    """A request with NaN observations finishes with an error; every other request
+    in the mix gets exactly its result alone."""
+    from paper_1812_01502_gb300 import serve
+    mix = _requests(serve, n=8, seed=5)
+    bad = mix[2]
+    bad.y = bad.y.copy()
+    bad.y[40:45] = np.nan
+    done = {r.rid: r for r in serve.Server(memory_budget=8 << 30, slots=6).run(mix)}
+    assert done[2].error is not None and done[2].status & 1
+    for rid in (0, 5):
+        assert done[rid].error is None
+        alone = _requests(serve, n=8, seed=5)[rid]
+        alone.arrival = 0.0
+        one = serve.Server(memory_budget=8 << 30, slots=1).run([alone])[0]
+        assert np.array_equal(one.incs, done[rid].incs)
+    assert serve.summarize(list(done.values()), 1.0)["failed_requests"] == 1
+
