@@ -3,13 +3,13 @@
 //
 // Each filter is the filter of step_butterfly.cu (Algorithm 1 with one stage
 // of Algorithm 3 per step, Heine, Whiteley & Cemgil, arXiv 1812.01502).  One
-// launch covers every filter of the batch: block b runs the whole step of
-// filter order[b] (filters sorted by decreasing work, so the largest start
-// first) with the shared tile code, and finishes that filter's likelihood
-// increment, filter mean and ESS inside the block - a filter never needs
-// another block, so nothing waits.  The last block to finish advances the
-// batch's step counter (last-block-done).  Chunks of steps are replayed from
-// a CUDA graph.
+// launch covers a whole chunk of time steps of every filter of the batch:
+// block b runs filter order[b] (filters sorted by decreasing work, so the
+// largest start first) step after step with the shared tile code, finishing
+// each step's likelihood increment, filter mean and ESS inside the block - a
+// filter never needs another block, so nothing waits and blocks of small
+// filters flow through the chunk without per-step launches.  The last block
+// to finish advances the batch's step counter (last-block-done).
 #include <cfloat>
 #include <type_traits>
 
@@ -99,9 +99,21 @@ __device__ __forceinline__ void batch_filter_step(const BatchParams& bp, BatchFi
   block_finish<D>(bp, f, fid, n, acc, accx, status, ctx.muf);
 }
 
+// Steps n0 .. n0 + steps - 1 of one filter: a filter never depends on another,
+// so its block runs the whole chunk without any grid-wide synchronisation.
+template <int D, int KIND>
+__device__ __forceinline__ void batch_filter_steps(const BatchParams& bp, BatchFilter& f, uint32_t fid, uint32_t n0,
+                                                   uint32_t steps, unsigned char* smem) {
+  for (uint32_t j = 0; j < steps; ++j) {
+    batch_filter_step<D, KIND>(bp, f, fid, n0 + j, smem);
+    __syncthreads();   // this filter's normaliser and weights are in place for the next step
+  }
+}
+
 }  // namespace
 
-__global__ void __launch_bounds__(kBlock) batch_step_kernel(const __grid_constant__ BatchParams bp) {
+// One launch runs `steps` consecutive time steps of every filter (one block per filter).
+__global__ void __launch_bounds__(kBlock) batch_step_kernel(const __grid_constant__ BatchParams bp, uint32_t steps) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ uint32_t s_last;
   const uint32_t n = bp.state->n;
@@ -109,21 +121,20 @@ __global__ void __launch_bounds__(kBlock) batch_step_kernel(const __grid_constan
   BatchFilter& f = bp.filters[fid];
   const int d = f.model.d;
   if (f.model.kind == kStochVol) {
-    batch_filter_step<1, kStochVol>(bp, f, fid, n, smem_raw);
+    batch_filter_steps<1, kStochVol>(bp, f, fid, n, steps, smem_raw);
   } else {
     switch (d) {
-      case 1: batch_filter_step<1, kLinearGaussian>(bp, f, fid, n, smem_raw); break;
-      case 2: batch_filter_step<2, kLinearGaussian>(bp, f, fid, n, smem_raw); break;
-      case 3: batch_filter_step<3, kLinearGaussian>(bp, f, fid, n, smem_raw); break;
-      case 4: batch_filter_step<4, kLinearGaussian>(bp, f, fid, n, smem_raw); break;
-      case 5: batch_filter_step<5, kLinearGaussian>(bp, f, fid, n, smem_raw); break;
-      case 6: batch_filter_step<6, kLinearGaussian>(bp, f, fid, n, smem_raw); break;
-      case 7: batch_filter_step<7, kLinearGaussian>(bp, f, fid, n, smem_raw); break;
-      default: batch_filter_step<8, kLinearGaussian>(bp, f, fid, n, smem_raw); break;
+      case 1: batch_filter_steps<1, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
+      case 2: batch_filter_steps<2, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
+      case 3: batch_filter_steps<3, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
+      case 4: batch_filter_steps<4, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
+      case 5: batch_filter_steps<5, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
+      case 6: batch_filter_steps<6, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
+      case 7: batch_filter_steps<7, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
+      default: batch_filter_steps<8, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
     }
   }
   // the last block to finish advances the batch's step counter
-  __syncthreads();
   if (threadIdx.x == 0) {
     __threadfence();
     const uint32_t prev = atomicAdd(&bp.state->done, 1u);
@@ -133,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) batch_step_kernel(const __grid_constan
   if (s_last && threadIdx.x == 0) {
     bp.state->done = 0;
     __threadfence();
-    bp.state->n = n + 1;
+    bp.state->n = n + steps;
   }
 }
 

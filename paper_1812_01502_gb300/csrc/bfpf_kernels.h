@@ -58,7 +58,8 @@ struct IslandKernels {
 };
 bool select_island_kernels(int d, int kind, IslandKernels& ik);
 
-// Batched filters (batch.cu): batch_step_kernel(BatchParams), batch_init_kernel(BatchParams).
+// Batched filters (batch.cu): batch_step_kernel(BatchParams, uint32_t steps) runs a chunk of
+// steps of every filter; batch_init_kernel(BatchParams).
 const void* batch_step_kernel_ptr();
 const void* batch_init_kernel_ptr();
 

@@ -1460,7 +1460,8 @@ pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_in
   if (!b) return bfail(nullptr, PF_EINVAL, "batch is NULL");
   if (T < 0 || (T > 0 && !y)) return bfail(b, PF_EINVAL, "need T >= 0 and y != NULL");
   const int R = b->ring, F = b->F;
-  void* args[] = {&b->BP};
+  uint32_t chunk_steps = 0;
+  void* args[] = {&b->BP, &chunk_steps};
   int32_t done = 0;
   while (done < T) {
     const uint32_t slot0 = (uint32_t)(b->n_host % (uint64_t)R);
@@ -1472,9 +1473,9 @@ pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_in
       if (!b->graph) {
         cudaGraph_t graph = nullptr;
         PF_BCUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = cudaSuccess;
-        for (int j = 0; j < L && le == cudaSuccess; ++j)
-          le = cudaLaunchKernel(batch_step_kernel_ptr(), dim3(F), dim3(kBlock), args, b->smem, b->cap_stream);
+        chunk_steps = (uint32_t)L;           // one launch runs the whole chunk
+        cudaError_t le = cudaLaunchKernel(batch_step_kernel_ptr(), dim3(F), dim3(kBlock), args, b->smem,
+                                          b->cap_stream);
         cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
         if (le != cudaSuccess) return bfail(b, PF_ECUDA, std::string("capture launch: ") + cudaGetErrorString(le));
         if (ce != cudaSuccess) return bfail(b, PF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
@@ -1487,8 +1488,8 @@ pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_in
       }
       PF_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
     } else {
-      for (int j = 0; j < L; ++j)
-        PF_BCUDA(b, cudaLaunchKernel(batch_step_kernel_ptr(), dim3(F), dim3(kBlock), args, b->smem, b->stream));
+      chunk_steps = (uint32_t)L;
+      PF_BCUDA(b, cudaLaunchKernel(batch_step_kernel_ptr(), dim3(F), dim3(kBlock), args, b->smem, b->stream));
     }
     if (loglik_incs)
       PF_BCUDA(b, cudaMemcpy2DAsync(loglik_incs + done, (size_t)8 * T, b->BP.inc_ring + slot0, (size_t)8 * R,
