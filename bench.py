@@ -633,9 +633,13 @@ def ours_main(a):
         g_ms = _timed_flushed_steps(bf, gfilt, torch.tensor(y[:W + KG], device=dev).contiguous(), KG, W,
                                     flush, gfilt.stream, dev)
         gfilt.close()
+        gbytes = 8 * w.model.d * w.N + 8                 # states read and written; one carried weight
         glob = {"value": job_throughput(world, w.N, KG, sum(g_ms) * 1e-3), "unit": METRIC, "steps": KG,
                 "ms_per_step": sum(g_ms) / KG, "p99_ms": float(np.percentile(g_ms, 99)),
-                "kernels_per_step": 3}
+                "kernels_per_step": 3,
+                "hbm_gbs_algorithmic": gbytes * KG / (sum(g_ms) * 1e-3) / 1e9,
+                "note": "same algorithmic bytes as the butterfly step; the scan arrays and the random "
+                        "gather are the global method's overhead"}
     eq = None
     if not a.no_global and rank == 0 and w.model.kind == "sv" and w.N == (1 << 24):
         eq = equal_error_leg(bf, w, dev)
