@@ -198,6 +198,7 @@ struct DigitGeom {
   uint32_t w, prev_sw;
   FastDiv div_w, div_nlw;
   uint32_t team;      // lanes per group in the tile kernels' group phase (power of two <= 32)
+  FastDiv div_s;      // division by s_k
 };
 
 // Geometry of one digit for the register-resident group kernel (power-of-two

@@ -328,6 +328,7 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     g.wide = a > kNarrowMaxRadix ? 1u : 0u;
     g.div_nl = make_fastdiv(g.nl);
     g.div_a = make_fastdiv(a);
+    g.div_s = make_fastdiv(s);
     g.div_tiles_l = make_fastdiv(g.tiles_l);
     if (!(pl.islands && k == 1)) {
       pl.cap = std::max(pl.cap, g.tile_n);

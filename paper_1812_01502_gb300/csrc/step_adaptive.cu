@@ -88,6 +88,33 @@ __global__ void __launch_bounds__(kBlock) adaptive_stage_kernel(const __grid_con
     // Normals numbered group-major on digit k, as when this launch resamples.
     const DigitGeom& g = p.geom[k];
     const ModelParams& mp = p.model;
+    if ((g.a & 3u) == 0) {
+      // quads of members of one group: one Philox block per 4 normals
+      for (uint32_t q = blockIdx.x * kBlock + threadIdx.x; q < p.N / 4; q += gridDim.x * kBlock) {
+        const uint32_t pi0 = 4 * q;
+        const uint32_t gid = fdiv(pi0, g.div_a), r0 = pi0 - gid * g.a;
+        const uint32_t h = fdiv(gid, g.div_s), l = gid - h * g.s;
+        const uint32_t ib = (h * g.a + r0) * g.s + l;       // particle of member r0
+        float z[4 * D];
+#pragma unroll
+        for (int b = 0; b < D; ++b) {
+          const uint4 w = philox4x32_10(make_uint4(q * D + b, n, kPurposePropagate, 0), p.rk);
+          normals4(w, z + 4 * b);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const uint32_t i = ib + e * g.s;
+          float xh[D], xo[D];
+#pragma unroll
+          for (int t = 0; t < D; ++t) xh[t] = __ldcs(p.x + (size_t)t * p.N + i);
+          mutate<D, KIND>(mp, xh, z + e * D, xo);
+#pragma unroll
+          for (int t = 0; t < D; ++t) __stcs(p.x + (size_t)t * p.N + i, xo[t]);
+        }
+      }
+      if (last_block_done(st)) end_step(p, st, n);
+      return;
+    }
     for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < p.N; i += gridDim.x * kBlock) {
       const uint32_t r = (i / g.s) % g.a;
       const uint32_t gid = (i / (g.a * g.s)) * g.s + i % g.s;
