@@ -26,6 +26,7 @@ import argparse
 import hashlib
 import json
 import os
+import platform
 import re
 import statistics
 import subprocess
@@ -232,6 +233,20 @@ def oracle_rate_main(a):
     print(json.dumps({"value": N * steps / el, "N": N, "radices": radices, "steps": steps, "seconds": el}))
 
 
+def _host_cpu() -> dict:
+    """The host the CPU baseline ran on: logical CPUs and the CPU model."""
+    model = platform.processor() or platform.machine()
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu model", "hardware")):
+                    model = line.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"nproc": os.cpu_count(), "cpu": model, "threads_used": 1}
+
+
 def oracle_rate(workload: str, n: int = 0, seconds: float = 12.0, steps: int = 0):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-rate", "--workload", workload,
@@ -258,7 +273,7 @@ def reference_main(a):
             "ms_per_step": 1000.0 * r["seconds"] / r["steps"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": a.workload, "N": r["N"], "radices": r["radices"]},
-            "cpu_baseline": {"value": r["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+            "cpu_baseline": {"value": r["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "host": _host_cpu(),
                              "sample": sample},
             "e2e": {"value": r["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
@@ -687,7 +702,7 @@ def ours_main(a):
     if not a.no_cpu_baseline:
         try:
             r = oracle_rate(a.workload, seconds=12.0)
-            cpu = {"value": r["value"], "unit": METRIC, "cores": 1, "kind": "oracle",
+            cpu = {"value": r["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "host": _host_cpu(),
                    "sample": f"first {r['steps']} time steps of {a.workload} at full size "
                              f"(N={r['N']}) on the FP64 numpy oracle, 1 thread"}
         except Exception as ex:  # report, never hide
