@@ -272,9 +272,11 @@ def reference_main(a):
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1000.0 * r["seconds"] / r["steps"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": a.workload, "N": r["N"], "radices": r["radices"]},
+            "config": {"workload": a.workload, "N": w.N, "radices": list(w.radices), "d": w.model.d,
+                       "model": w.model.kind, "parallelism": "replicas1"},
             "cpu_baseline": {"value": r["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "host": _host_cpu(),
-                             "sample": sample},
+                             "sample": sample + f" (a bounded sample of the N = {w.N} workload; "
+                                                "the rate is particle-steps/s, as for the GPU arm)"},
             "e2e": {"value": r["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
