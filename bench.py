@@ -263,7 +263,13 @@ def reference_main(a):
         return
     import synthetic as S
     w = S.workload(a.workload)
-    n_sample = 1 << 20 if w.N > (1 << 20) else w.N
+    # sample size chosen so that K steps of the oracle (about 1.5e6 particle-steps/s on
+    # one core) take about 100 s: the whole reference run stays within a few minutes
+    budget = 1.5e6 * 100.0 / max(1, a.steps)
+    n_sample = 1 << 10
+    while n_sample * 2 <= min(budget, 1 << 20):
+        n_sample *= 2
+    n_sample = min(n_sample, w.N)
     # warm-up steps are included in the sample run's start-up; time K steps
     r = oracle_rate(a.workload, n=n_sample, steps=max(1, a.steps))
     sample = (f"first {r['steps']} time steps of {a.workload} with N={r['N']} particles "
