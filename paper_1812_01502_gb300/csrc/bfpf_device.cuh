@@ -210,6 +210,7 @@ struct GroupGeom {
   uint32_t nbatch;    // (N / a_k) / groups per thread block
   uint32_t lv_mul, lv_lmask, lv_mask;
   float log_a;
+  uint32_t j, k, last;   // fully adapted schedule: launch position, digit, last launch of the step
 };
 
 // ModelParams::flags: structure of the linear-Gaussian matrices (lets the

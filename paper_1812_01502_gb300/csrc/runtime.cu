@@ -449,7 +449,11 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     DigitPlan& dp = pl.dp[k];
     const DigitGeom& g = pl.geom[k];
     int G = 0;
-    const void* gk = (pow2 && g.a <= 32 && !pl.adaptive && !pl.sets && !pl.island_adaptive) ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged) : nullptr;
+    // the fully adapted schedule uses group kernels unless rotation makes a launch's digit data-dependent
+    const bool adapt_group = pl.adaptive && !pl.rotate;
+    const void* gk = (pow2 && g.a <= 32 && !(pl.adaptive && pl.rotate) && !pl.sets && !pl.island_adaptive)
+                         ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged, adapt_group)
+                         : nullptr;
     if (gk && G > 0) {
       const uint32_t gpb = kBlock / G;
       const uint32_t ngroups = pl.N / g.a;
@@ -475,6 +479,14 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
           dp.gg.lv_mask = 0xffffffffu;
         }
         dp.gg.log_a = g.log_a;
+        if (adapt_group) {            // per-particle carried weights: index = member's particle index
+          dp.gg.lv_mul = g.s;
+          dp.gg.lv_lmask = g.s - 1;
+          dp.gg.lv_mask = 0xffffffffu;
+          dp.gg.j = (uint32_t)k;
+          dp.gg.k = (uint32_t)k;
+          dp.gg.last = (k == m - 1) ? 1u : 0u;
+        }
       }
     }
   }
@@ -615,6 +627,11 @@ cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
     if (j == 0) {
       void* args[] = {&h->P};
       return cudaLaunchKernel(pl.ak.weight, dim3(pl.max_grid), dim3(kBlock), args, 0, stream);
+    }
+    const DigitPlan& dp = pl.dp[j - 1];
+    if (dp.group) {                 // no rotation: launch j - 1 works on digit j - 1
+      void* args[] = {&h->P, const_cast<GroupGeom*>(&dp.gg)};
+      return cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, 0, stream);
     }
     h->launch_j[j - 1] = j - 1;
     void* args[] = {&h->P, &h->launch_j[j - 1]};

@@ -27,6 +27,7 @@
 #include "bfpf_device.cuh"
 #include "bfpf_epilogue.cuh"
 #include "bfpf_model.cuh"
+#include "step_adaptive.cuh"
 
 namespace bfpf {
 
@@ -34,7 +35,11 @@ namespace bfpf {
 // STAGED = true: the stage schedule of the device state decides both (all
 // stages per step, Sched); a separate instantiation keeps the default path's
 // registers unchanged.
-template <int D, int KIND, int A, int G, bool STAGED>
+// ADAPT = true: stage launch gg.j of the fully adapted schedule without
+// rotation (digit gg.k = gg.j): skipped when the ESS already reached the
+// threshold (the last launch then only mutates), per-particle carried weights
+// in and out, and the ESS of the new stage weights decides the next stage.
+template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
 __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constant__ StepParams p,
                                                            const __grid_constant__ GroupGeom gg) {
   static_assert(A >= 2 && A <= 32 && (A & (A - 1)) == 0, "radix must be a power of two <= 32");
@@ -57,12 +62,21 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
   const uint32_t tg = tid / G, j = tid % G;
   const ModelParams& mp = p.model;
   DevState* st = p.st;
-  const Sched sc = STAGED ? sched_of(p, st) : Sched{st->n, st->n, 0u, true, true};
-  const bool obs = STAGED ? sc.obs : true;
-  const bool mut = STAGED ? sc.mut : true;
+  if constexpr (ADAPT) {
+    if (st->skip) {
+      if (!gg.last) return;                     // nothing to do, nothing to record
+      adaptive_mutate_only<D, KIND>(p, p.geom[gg.k], st->n);
+      return;
+    }
+  }
+  const Sched sc = ADAPT ? Sched{st->n, st->n * (uint32_t)p.m + gg.j, gg.k, false, gg.last != 0}
+                         : STAGED ? sched_of(p, st) : Sched{st->n, st->n, 0u, true, true};
+  const bool obs = (STAGED || ADAPT) ? sc.obs : true;
+  const bool mut = (STAGED || ADAPT) ? sc.mut : true;
   const uint32_t n = sc.n;
-  const float* __restrict__ lV_in = p.lV[sc.t & 1u];
-  float* __restrict__ lV_out = p.lV[(sc.t & 1u) ^ 1u];
+  const uint32_t lvsel = ADAPT ? st->lvp : (sc.t & 1u);
+  const float* __restrict__ lV_in = p.lV[lvsel];
+  float* __restrict__ lV_out = p.lV[lvsel ^ 1u];
   float* __restrict__ X = p.x;
   const float muf = st->mu_f;
   const uint32_t N = p.N;
@@ -205,7 +219,23 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
 #pragma unroll
       for (int t = 0; t < D; ++t) col[(t * A + r) * LD] = __float_as_uint(xv[mm][t]);
     }
-    if (j == 0) {
+    if constexpr (ADAPT) {           // per-particle carried weights; partial of the new stage weights
+      const float lv_new = (Q != 0) ? (mx + logf(s1) - gg.log_a) : -INFINITY;
+      if (contiguous) {
+#pragma unroll
+        for (int q = 0; q < M / 4; ++q)
+          reinterpret_cast<float4*>(lV_out + i0)[q] = make_float4(lv_new, lv_new, lv_new, lv_new);
+      } else {
+#pragma unroll
+        for (int mm = 0; mm < M; ++mm) lV_out[i0 + (mm << log2s)] = lv_new;
+      }
+      if (j == 0 && Q != 0) {
+        float zx[D];
+#pragma unroll
+        for (int t = 0; t < D; ++t) zx[t] = 0.0f;
+        merge_partial<D>(acc, accx, lv_new + gg.log_a, 1.0f, 1.0f / (float)A, zx);
+      }
+    } else if (j == 0) {
       lV_out[g] = (Q != 0) ? (mx + logf(s1) - gg.log_a) : -INFINITY;
       merge_partial<D>(acc, accx, mx, s1, s2, sx);
     }
@@ -319,7 +349,11 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
     }
     __syncwarp();
   }
-  finish_step<D>(p, acc, accx, sc, status, muf);
+  if constexpr (ADAPT) {
+    adaptive_stage_finish<D>(p, acc, accx, status, lvsel, gg.k, gg.last != 0, n);
+  } else {
+    finish_step<D>(p, acc, accx, sc, status, muf);
+  }
 }
 
 // Lanes per group: each lane keeps M = A / G members, M * D <= 16 state values.
@@ -329,29 +363,31 @@ constexpr int group_members_per_lane(int A, int D) {
   return m;
 }
 
-template <int D, int KIND, int A, bool STAGED>
+template <int D, int KIND, int A, bool STAGED, bool ADAPT>
 inline const void* group_kernel_pick(int& G) {
   constexpr int M = group_members_per_lane(A, D);
   constexpr int GG = A / M;
   G = GG;
-  return reinterpret_cast<const void*>(&step_group_kernel<D, KIND, A, GG, STAGED>);
+  return reinterpret_cast<const void*>(&step_group_kernel<D, KIND, A, GG, STAGED, ADAPT>);
 }
 
-template <int D, int KIND, bool STAGED>
+template <int D, int KIND, bool STAGED, bool ADAPT>
 inline const void* group_kernel_for_s(int a, int& G) {
   switch (a) {
-    case 2: return group_kernel_pick<D, KIND, 2, STAGED>(G);
-    case 4: return group_kernel_pick<D, KIND, 4, STAGED>(G);
-    case 8: return group_kernel_pick<D, KIND, 8, STAGED>(G);
-    case 16: return group_kernel_pick<D, KIND, 16, STAGED>(G);
-    case 32: return group_kernel_pick<D, KIND, 32, STAGED>(G);
+    case 2: return group_kernel_pick<D, KIND, 2, STAGED, ADAPT>(G);
+    case 4: return group_kernel_pick<D, KIND, 4, STAGED, ADAPT>(G);
+    case 8: return group_kernel_pick<D, KIND, 8, STAGED, ADAPT>(G);
+    case 16: return group_kernel_pick<D, KIND, 16, STAGED, ADAPT>(G);
+    case 32: return group_kernel_pick<D, KIND, 32, STAGED, ADAPT>(G);
     default: return nullptr;
   }
 }
 
+// staged: all stages per step; adapt: the fully adapted schedule (no rotation)
 template <int D, int KIND>
-inline const void* group_kernel_for(int a, int& G, bool staged) {
-  return staged ? group_kernel_for_s<D, KIND, true>(a, G) : group_kernel_for_s<D, KIND, false>(a, G);
+inline const void* group_kernel_for(int a, int& G, bool staged, bool adapt) {
+  if (adapt) return group_kernel_for_s<D, KIND, false, true>(a, G);
+  return staged ? group_kernel_for_s<D, KIND, true, false>(a, G) : group_kernel_for_s<D, KIND, false, false>(a, G);
 }
 
 }  // namespace bfpf

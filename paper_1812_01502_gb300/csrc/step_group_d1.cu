@@ -4,10 +4,10 @@
 
 namespace bfpf {
 
-const void* group_kernel_d1(int kind, int a, int* G, bool staged) {
-  if (kind == kStochVol) return group_kernel_for<1, kStochVol>(a, *G, staged);
+const void* group_kernel_d1(int kind, int a, int* G, bool staged, bool adapt) {
+  if (kind == kStochVol) return group_kernel_for<1, kStochVol>(a, *G, staged, adapt);
   if (kind != kLinearGaussian) return nullptr;
-  return group_kernel_for<1, kLinearGaussian>(a, *G, staged);
+  return group_kernel_for<1, kLinearGaussian>(a, *G, staged, adapt);
 }
 
 }  // namespace bfpf

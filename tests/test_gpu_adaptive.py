@@ -23,6 +23,10 @@ def _informative_lg(d, seed):
     ("lg2_all", _informative_lg(2, 5), (32, 32), 1.5, False, 4),
     ("lg1_none", S.lg_scalar(), (16, 16), 1e-9, True, 4),
     ("sv_wide", S.sv_model(), (300, 4), 0.9, True, 4),
+    # sizes at which every digit runs on the register-resident group kernel (no rotation)
+    ("sv_group_half", S.sv_model(), (16, 16, 16), 0.5, False, 5),
+    ("sv_group_all", S.sv_model(), (16, 16, 16), 1.5, False, 3),
+    ("lg4_group_09", _informative_lg(4, 3), (8, 8, 8, 8), 0.9, False, 4),
 ])
 def test_adaptive_lockstep(bfpf, name, model, radices, theta, rotate, T):
     N = int(np.prod(radices))
@@ -31,6 +35,8 @@ def test_adaptive_lockstep(bfpf, name, model, radices, theta, rotate, T):
     f = bfpf.ButterflyFilter(model, N, radices, seed, adaptive=True, ess_threshold=theta, rotate=rotate)
     desc = f.describe()
     assert desc["adaptive"] and desc["rotate"] == rotate
+    if name.startswith(("sv_group", "lg4_group")):
+        assert all(dg["kernel"] == "group" for dg in desc["digits"])
     rep = LS.Report()
     start = 0
     for n in range(T):
