@@ -135,46 +135,64 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
   const unsigned long long warp_excl = (warp == 0) ? 0ull : s_warp[warp - 1];
   const unsigned long long thread_excl = warp_excl + incl - tot;
   const unsigned long long tile_total = s_warp[kBlock / 32 - 1];
-  // decoupled look-back (thread 0)
-  if (tid == 0) {
+  // decoupled look-back by warp 0, 32 predecessor tiles per round: every lane
+  // waits (bounded) for its tile's aggregate or inclusive prefix; the nearest
+  // tile with an inclusive prefix ends the walk
+  if (warp == 0) {
     const uint32_t f_agg = 2u * n + 1u, f_pre = 2u * n + 2u;
     unsigned long long prefix = 0;
     if (tile == 0) {
-      gp.incl[0] = tile_total;
-      __threadfence();
-      atomicExch(gp.flag, f_pre);
+      if (lane == 0) {
+        gp.incl[0] = tile_total;
+        __threadfence();
+        atomicExch(gp.flag, f_pre);
+      }
     } else {
-      gp.agg[tile] = tile_total;
-      __threadfence();
-      atomicExch(gp.flag + tile, f_agg);
-      int32_t t = (int32_t)tile - 1;
-      uint32_t spins = 0;
+      if (lane == 0) {
+        gp.agg[tile] = tile_total;
+        __threadfence();
+        atomicExch(gp.flag + tile, f_agg);
+      }
       // test hook: the stalled tile recognises no flag, so its wait runs out
       const bool stall = gp.stall_tile != 0 && tile == gp.stall_tile;
-      while (t >= 0) {
-        const uint32_t f = stall ? 0u : ld_volatile_u32(gp.flag + t);
-        if (f == f_pre) {
+      bool timed_out = false;
+      int32_t base = (int32_t)tile - 1;
+      while (true) {
+        const int32_t t = base - (int32_t)lane;
+        uint32_t f = f_pre;                       // before tile 0: an inclusive prefix of 0
+        unsigned long long v = 0;
+        if (t >= 0) {
+          uint32_t spins = 0;
+          f = stall ? 0u : ld_volatile_u32(gp.flag + t);
+          while (f != f_agg && f != f_pre) {
+            if (++spins > kSpinLimit) {
+              timed_out = true;                   // counted as an aggregate of 0
+              break;
+            }
+            __nanosleep(32);
+            f = stall ? 0u : ld_volatile_u32(gp.flag + t);
+          }
           __threadfence();
-          prefix += ld_volatile_u64(gp.incl + t);
-          break;
+          if (f == f_pre) v = ld_volatile_u64(gp.incl + t);
+          else if (f == f_agg) v = ld_volatile_u64(gp.agg + t);
         }
-        if (f == f_agg) {
-          __threadfence();
-          prefix += ld_volatile_u64(gp.agg + t);
-          --t;
-          continue;
-        }
-        if (++spins > kSpinLimit) {
-          atomicOr(&st->status, kStatusTimeout);
-          break;
-        }
-        __nanosleep(32);
+        const unsigned ready = __ballot_sync(0xffffffffu, f == f_pre);
+        const int first = ready ? __ffs(ready) - 1 : 32;   // nearest tile with a prefix
+        unsigned long long c = ((int)lane <= first) ? v : 0ull;
+#pragma unroll
+        for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
+        prefix += c;
+        if (ready) break;
+        base -= 32;
       }
-      gp.incl[tile] = prefix + tile_total;
-      __threadfence();
-      atomicExch(gp.flag + tile, f_pre);
+      if (__any_sync(0xffffffffu, timed_out) && lane == 0) atomicOr(&st->status, kStatusTimeout);
+      if (lane == 0) {
+        gp.incl[tile] = prefix + tile_total;
+        __threadfence();
+        atomicExch(gp.flag + tile, f_pre);
+      }
     }
-    s_prefix = prefix;
+    if (lane == 0) s_prefix = prefix;
   }
   __syncthreads();
   const unsigned long long off0 = s_prefix + thread_excl;
@@ -210,12 +228,15 @@ __global__ void __launch_bounds__(kBlock) global_draw_kernel(const __grid_consta
   const uint32_t seg = 1u << gp.top_shift;
   uint32_t fsteps = 1;
   while (fsteps < seg) fsteps <<= 1;
-  auto search = [&](unsigned long long u) -> uint32_t {
-    // top table: number of entries <= u (binary lifting over ntop - 1 candidates)
+  // top table: number of its first ntop - 1 entries <= u (binary lifting in shared memory)
+  auto top_count = [&](unsigned long long u) -> uint32_t {
     uint32_t c = 0;
     for (uint32_t stp = lsteps >> 1; stp; stp >>= 1)
       if (c + stp <= ntop - 1 && s_top[c + stp - 1] <= u) c += stp;
-    const uint32_t lo = c << gp.top_shift;
+    return c;
+  };
+  auto search = [&](unsigned long long u) -> uint32_t {
+    const uint32_t lo = top_count(u) << gp.top_shift;
     const uint32_t len = min(seg, N - lo);
     uint32_t f = 0;   // number of P_j <= u inside the segment (< len)
     for (uint32_t stp = fsteps >> 1; stp; stp >>= 1)
