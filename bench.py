@@ -383,10 +383,10 @@ def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
     import synthetic as S
     y = S.simulate(w.model, T, w.data_seed)[1].astype(np.float32)
 
-    def run(N, radices, seed):
-        f = bf.ButterflyFilter(w.model, N, radices, seed, device=dev)
+    def run(N, radices, seed, **kw):
+        f = bf.ButterflyFilter(w.model, N, radices, seed, device=dev, **kw)
         f.run(y[:4])                                  # graph capture / first touch
-        g = bf.ButterflyFilter(w.model, N, radices, seed, device=dev)
+        g = bf.ButterflyFilter(w.model, N, radices, seed, device=dev, **kw)
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         yd = torch.tensor(y, device=dev)
         torch.cuda.synchronize(dev)
@@ -404,14 +404,17 @@ def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
     ref_mean = 0.5 * (ref[0] + ref[1])
     ref_mse = 0.25 * float(np.sum((ref[0] - ref[1]) ** 2))     # error of the averaged reference
     out = {}
-    for name, Ns, rad in (("butterfly", [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24], _radix16),
-                          ("global", [1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22], lambda N: (N,))):
+    for name, Ns, rad, kw in (("butterfly", [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24], _radix16, {}),
+                              ("butterfly_all_stages", [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24], _radix16,
+                               {"all_stages": True}),
+                              ("global", [1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24],
+                               lambda N: (N,), {})):
         mses, times = [], []
         for N in Ns:
             J = 4 if N <= (1 << 20) else 2
             errs, ts = [], []
             for j in range(J):
-                mean, ms = run(N, rad(N), seed0 + 100 * j + N % 97)
+                mean, ms = run(N, rad(N), seed0 + 100 * j + N % 97, **kw)
                 errs.append(float(np.sum((mean - ref_mean) ** 2)) - ref_mse)
                 ts.append(ms)
             mses.append(max(float(np.mean(errs)), 1e-30))
@@ -428,8 +431,21 @@ def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
                                  left=None, right=None))) if logN_eq <= np.log(gN[-1]) else \
         float(np.exp(np.polyval(np.polyfit(np.log(gN[-3:]), np.log(gt[-3:]), 1), logN_eq)))
     t_b = bt[-1]
+
+    def global_ms_at(mse):                     # the global filter's time per step at a given MSE
+        lN = (np.log(mse) - fit_g[1]) / fit_g[0]
+        if lN <= np.log(gN[-1]):
+            return float(np.exp(np.interp(lN, np.log(gN), np.log(gt))))
+        return float(np.exp(np.polyval(np.polyfit(np.log(gN[-3:]), np.log(gt[-3:]), 1), lN)))
+    aN, am, at = (out["butterfly_all_stages"][k] for k in ("N", "mse", "ms_per_step"))
+    fit_a = np.polyfit(np.log(aN), np.log(am), 1)
+    target_a = float(np.exp(np.polyval(fit_a, np.log(aN[-1]))))
+    all_stages = {"N": aN[-1], "mse": target_a, "ms_per_step": at[-1], "mse_slope": float(fit_a[0]),
+                  "global_ms_per_step_at_equal_mse": global_ms_at(target_a),
+                  "speedup_at_equal_error": global_ms_at(target_a) / at[-1]}
     return {"T": T, "reference": "mean of 2 global runs at N=2^25, their spread subtracted",
             "butterfly": out["butterfly"], "global": out["global"],
+            "butterfly_all_stages": out["butterfly_all_stages"], "all_stages_at_equal_error": all_stages,
             "mse_slope": {"butterfly": float(fit_b[0]), "global": float(fit_g[0])},
             "butterfly_N": bN[-1], "butterfly_mse": target, "global_N_at_equal_mse": float(np.exp(logN_eq)),
             "butterfly_ms_per_step": t_b, "global_ms_per_step_at_equal_mse": t_g,
