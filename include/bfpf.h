@@ -214,12 +214,18 @@ pf_status pf_loglik(const pf_handle* h, double* out);
 
 /*
  * Copy the filter state to host memory (synchronises; any pointer may be NULL):
- *   x        N*d floats, state-major: x[t*N + i] = component t of particle i;
+ *   x        N*d floats, state-major: x[t*N + i] = component t of particle i
+ *            (the prediction particles of the next step);
  *   lV       N / a_{k'} floats: carried log stage weights, one per group of the
  *            digit k' of the last stage run (k' = (n-1) mod m; m-1 with
  *            PF_ALL_STAGES; all zero before the first step), group index
  *            (i / (a_{k'} s_{k'})) * s_{k'} + i % s_{k'}, s_{k'} = a_0 ... a_{k'-1};
  *            with PF_ADAPTIVE: N floats, one per particle;
+ *            with PF_DIGIT_SETS: N / (a_0 a_{m-1}) floats, one per group of the
+ *            last set {0, m-1} (index (i / (a_{m-1} s_{m-1})) (s_{m-1} / a_0)
+ *            + (i % s_{m-1}) / a_0);
+ *            with PF_ISLANDS: M floats, all equal (radices (M, m)); with
+ *            PF_ISLANDS | PF_ADAPTIVE: m floats, one per island;
  *   scalars  4 doubles: { n, loglik, mu, mu_used }, where mu is the carried
  *            normaliser subtracted from the log-weights at the next step (FP64)
  *            and mu_used its FP32 value the kernels subtract.
