@@ -534,6 +534,43 @@ def paper_workload_leg(bf, dev, J=3, Ns=(1 << 12, 1 << 14, 1 << 16, 1 << 18)):
             "raw_observation_mse": raw, "curves": curves}
 
 
+def lg8d_kalman_leg(bf, dev):
+    """The 8-dimensional linear-Gaussian workload at full size (N = 2^20, T = 1000)
+    against the exact Kalman filter (measurement reference, a few lines below):
+    log-likelihood error and filter-mean MSE (sum over steps and components)
+    for the one-digit schedule, all stages per step and the global filter."""
+    import numpy as np
+    import torch
+    import synthetic as S
+    w = S.workload("lg8d_n1m")
+    y = w.observations()
+    A, H = w.model.A, w.model.H
+    Q, R = w.model.Lq @ w.model.Lq.T, w.model.Lr @ w.model.Lr.T
+    m, P = w.model.m0.copy(), w.model.L0 @ w.model.L0.T
+    kmean = np.empty((len(y), w.model.d))
+    kll = 0.0
+    for n in range(len(y)):                       # Kalman filter (prediction, then update)
+        if n > 0:
+            m, P = A @ m, A @ P @ A.T + Q
+        Sv = H @ P @ H.T + R
+        r = y[n] - H @ m
+        kll += -0.5 * (r @ np.linalg.solve(Sv, r) + np.linalg.slogdet(2 * np.pi * Sv)[1])
+        K = P @ H.T @ np.linalg.inv(Sv)
+        m, P = m + K @ r, (np.eye(len(m)) - K @ H) @ P
+        kmean[n] = m
+    yd = torch.tensor(y.astype(np.float32), device=dev)
+    out = {"N": w.N, "T": len(y), "kalman_loglik": kll}
+    for name, rad, kw in (("one_digit", w.radices, {}), ("all_stages", w.radices, {"all_stages": True}),
+                          ("global", (w.N,), {})):
+        f = bf.ButterflyFilter(w.model, w.N, rad, w.filter_seed, device=dev, **kw)
+        r = f.run(yd)
+        ll = f.loglik()
+        f.close()
+        out[name] = {"loglik_error": ll - kll,
+                     "mse": float(np.sum((r["mean"].double().cpu().numpy() - kmean) ** 2))}
+    return out
+
+
 def schedules_leg(bf, w, dev, flush, K=30, W=3):
     """The paper's schedules on the main workload at full size: all stages per
     step and fully adapted resampling (theta = 0.5, and theta > 1, which runs
@@ -698,6 +735,9 @@ def ours_main(a):
     scheds = None
     if not a.no_schedules and rank == 0:
         scheds = schedules_leg(bf, w, dev, flush)
+    lg8 = None
+    if not a.no_schedules and rank == 0:
+        lg8 = lg8d_kalman_leg(bf, dev)
 
     total_ms, e2e_s, resident_ms = max_over_ranks([total_ms, e2e_s, resident_ms], world, dev)
     value = job_throughput(world, w.N, K, total_ms * 1e-3)
@@ -761,6 +801,7 @@ def ours_main(a):
         "serving": serving,
         "paper_workload": paper,
         "schedules": scheds,
+        "lg8d_against_kalman": lg8,
     }
     print(json.dumps(line))
     filt.close()
