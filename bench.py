@@ -51,6 +51,7 @@ def _args():
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-global", action="store_true", help="skip the global-resampling comparator legs")
     p.add_argument("--global-steps", type=int, default=200)
+    p.add_argument("--no-equal-error", action="store_true", help="skip the equal-error sweep")
     p.add_argument("--no-batched", action="store_true", help="skip the batched-filters leg")
     p.add_argument("--batched-filters", type=int, default=4096)
     p.add_argument("--batched-steps", type=int, default=500)
@@ -716,12 +717,13 @@ def ours_main(a):
         gbytes = 8 * w.model.d * w.N + 8                 # states read and written; one carried weight
         glob = {"value": job_throughput(world, w.N, KG, sum(g_ms) * 1e-3), "unit": METRIC, "steps": KG,
                 "ms_per_step": sum(g_ms) / KG, "p99_ms": float(np.percentile(g_ms, 99)),
-                "kernels_per_step": 3,
+                "kernels_per_step": 4,
                 "hbm_gbs_algorithmic": gbytes * KG / (sum(g_ms) * 1e-3) / 1e9,
-                "note": "same algorithmic bytes as the butterfly step; the scan arrays and the random "
-                        "gather are the global method's overhead"}
+                "note": "same algorithmic bytes as the butterfly step; the log-weight, prefix-sum and "
+                        "bucket arrays and the scattered writes of the new states are the global "
+                        "method's overhead"}
     eq = None
-    if not a.no_global and rank == 0 and w.model.kind == "sv" and w.N == (1 << 24):
+    if not a.no_global and not a.no_equal_error and rank == 0 and w.model.kind == "sv" and w.N == (1 << 24):
         eq = equal_error_leg(bf, w, dev)
     batched = None
     if not a.no_batched and rank == 0:

@@ -130,6 +130,11 @@ typedef struct {
  * runs out (well under a second) every step, status bit 2 is set and
  * pf_loglik returns PF_ETIMEOUT.  The results of such a filter are invalid. */
 #define PF_TEST_SCAN_TIMEOUT 0x80000000u
+/* Test hook for the global-resampling draws (radices = {N}, N > 1024): every
+ * bucket of draws holds 16 particles and stages at most 64 indices, so most
+ * draws go through the overflow list and most buckets search P in global
+ * memory.  Results are those of the normal path; only slower. */
+#define PF_TEST_SMALL_BUCKETS 0x40000000u
 
 typedef struct {
     int32_t tile;        /* target particles per thread-block tile; 0 = automatic            */
@@ -148,7 +153,10 @@ typedef struct pf_handle pf_handle;
  * Device workspace needed by pf_create for this problem: particle states
  * (4*d*N bytes), carried log-weights (2 * 4N/min(a) bytes), optional
  * ancestors (4N), per-block partial sums and small rings for observations
- * and per-step outputs.  opts may be NULL.
+ * and per-step outputs; global resampling (radices = {N}, N > 1024) adds a
+ * second state buffer (4dN), log-weights (4N), prefix sums (8N), the draws
+ * filed by bucket with their uniforms (about 16N) and an overflow list
+ * (12N).  opts may be NULL.
  * Errors: PF_EINVAL (bad model / N / radices, see pf_create).
  */
 pf_status pf_workspace_size(const pf_model* model, int64_t N, const int32_t* radices,

@@ -35,6 +35,7 @@ PF_ROTATE = 8
 PF_ISLANDS = 16
 PF_ISLANDS_PLAIN = 32
 PF_TEST_SCAN_TIMEOUT = 0x80000000
+PF_TEST_SMALL_BUCKETS = 0x40000000
 PF_DIGIT_SETS = 64
 STATUS_NAMES = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",
                 PF_ETIMEOUT: "PF_ETIMEOUT", PF_ESTATE: "PF_ESTATE"}

@@ -37,7 +37,10 @@ const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt);
 struct GlobalKernels {
   const void* weight;
   const void* scan;
-  const void* draw;
+  const void* refine;
+  const void* bounds;
+  const void* resolve;
+  const void* advance;
 };
 bool select_global_kernels(int d, int kind, GlobalKernels& gk);
 

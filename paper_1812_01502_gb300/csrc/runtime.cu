@@ -41,7 +41,8 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t st, x, lv0, lv1, anc, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
-  size_t x2, lw, P, top, agg, incl, flag;   // global resampling only (x2: also AIRPF)
+  size_t x2, lw, P, agg, incl, flag;        // global resampling only (x2: also AIRPF)
+  size_t slot, cnt, ovf, jb, cslot, ccnt, covf;   // global resampling: draws filed by coarse bin, then bucket
   size_t src;                               // AIRPF: island sources
 };
 
@@ -84,8 +85,11 @@ struct Plan {
   int max_grid = 0;
   bool global = false;        // radices = {N} with N > kMaxCtaRadix: global resampling kernels
   GlobalKernels gk{};
-  int grid_weight = 0, grid_draw = 0;
-  uint32_t nscan = 0, ntop = 0, top_shift = 0;
+  int grid_weight = 0;
+  uint32_t nscan = 0;
+  uint32_t log2b = 0, buckets = 1, bucket_cap = 0, stage_cap = 0;   // bucketed draws
+  uint32_t cbits = 0, ccap = 0, nseg = 1;                            // coarse bins
+  size_t smem_resolve = 0, smem_weight = 0, smem_refine = 0;
   Layout lay{};
 };
 
@@ -287,10 +291,31 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     if (!select_global_kernels(d, pl.kind, pl.gk)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
     if (!select_kernels(d, pl.kind, true, pl.ks)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
     pl.nscan = (pl.N + kScanTile - 1) / kScanTile;
-    uint32_t lg = 0;
-    while ((1ull << lg) < pl.N) ++lg;
-    pl.top_shift = lg > 12 ? lg - 12 : 0;
-    pl.ntop = (pl.N + (1u << pl.top_shift) - 1) >> pl.top_shift;
+    // Draws are resolved per bucket of their uniform: about stage_cap / 4 to
+    // stage_cap / 2 draws per bucket, so that a bucket's index range normally
+    // fits the shared-memory staging buffer (8 + 4 d bytes per index).
+    const bool small_buckets = opts && (opts->flags & PF_TEST_SMALL_BUCKETS);
+    pl.stage_cap = global_stage_alloc(d);
+    uint32_t lgN = 0, lgc = 0;
+    while ((2ull << lgN) <= pl.N) ++lgN;            // floor(log2 N)
+    while ((2u << lgc) <= pl.stage_cap) ++lgc;      // log2 stage_cap
+    pl.log2b = lgN > lgc - 2 ? std::min<uint32_t>(lgN - (lgc - 2), 24u) : 0u;
+    pl.buckets = 1u << pl.log2b;
+    const uint32_t mu = (uint32_t)((pl.N + pl.buckets - 1) / pl.buckets);
+    const uint32_t sd = (uint32_t)std::ceil(std::sqrt((double)mu));
+    // 8 standard deviations of the binomial fill above its mean; the rare
+    // excess goes to the overflow list.  The test hook forces overflow.
+    pl.bucket_cap = small_buckets ? 16u : std::min<uint32_t>(pl.N, mu + 8u * sd + 64u);
+    if (small_buckets) pl.stage_cap = 64u;          // most buckets then search in global memory
+    // Coarse bins: the top half of the bucket bits, filed first
+    pl.cbits = (pl.log2b + 1u) / 2u;
+    const uint32_t muc = (uint32_t)((pl.N + (1u << pl.cbits) - 1) >> pl.cbits);
+    const uint32_t sdc = (uint32_t)std::ceil(std::sqrt((double)muc));
+    pl.ccap = small_buckets ? 64u : std::min<uint32_t>(pl.N, muc + 8u * sdc + 64u);
+    pl.nseg = (pl.ccap + kRefineSeg - 1) / kRefineSeg;
+    pl.smem_weight = (size_t)16 * kBlock * global_weight_vec(d) + (size_t)8 * (1u << pl.cbits);
+    pl.smem_refine = (size_t)16 * kRefineSeg + (size_t)8 * (1u << (pl.log2b - pl.cbits));
+    pl.smem_resolve = (size_t)8 * global_stage_alloc(d) + (size_t)4 * d * (global_stage_alloc(d) + 1u);
     DigitGeom& g = pl.geom[0];
     g.a = pl.N;
     g.s = 1;
@@ -500,15 +525,17 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
 
 // Needs a CUDA device: occupancy decides the persistent grid size.
 pf_status finish_plan_global(Plan& pl, const pf_options* opts, int sms, std::string& msg) {
-  int nw = 0, nd = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nw, pl.gk.weight, kBlock, 0);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nd, pl.gk.draw, kBlock, 0);
+  int nw = 0;
+  cudaError_t e = cudaFuncSetAttribute(pl.gk.resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_resolve);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pl.gk.weight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_weight);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(pl.gk.refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_refine);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nw, pl.gk.weight, kBlock, pl.smem_weight);
   if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
   const int units = (int)((pl.N + kBlock - 1) / kBlock);
   int gw = (opts && opts->grid > 0) ? opts->grid : std::max(1, nw) * sms;
-  int gd = (opts && opts->grid > 0) ? opts->grid : std::max(1, nd) * sms;
   pl.grid_weight = std::max(1, std::min(gw, units));
-  pl.grid_draw = std::max(1, std::min(gd, units));
   pl.max_grid = pl.grid_weight;
   pl.grid = pl.grid_weight;
   Layout& L = pl.lay;
@@ -527,7 +554,13 @@ pf_status finish_plan_global(Plan& pl, const pf_options* opts, int sms, std::str
   L.ess_ring = take((size_t)4 * kRing);
   L.lw = take((size_t)4 * pl.N);
   L.P = take((size_t)8 * pl.N);
-  L.top = take((size_t)8 * kTopMax);
+  L.slot = take((size_t)16 * pl.buckets * pl.bucket_cap);
+  L.cnt = take((size_t)4 * (pl.buckets + 1u));
+  L.cslot = take((size_t)16 * (1u << pl.cbits) * pl.ccap);
+  L.ccnt = take((size_t)4 * ((1u << pl.cbits) + 1u));
+  L.covf = take((size_t)16 * pl.N);
+  L.ovf = take((size_t)16 * pl.N);
+  L.jb = take((size_t)4 * (pl.buckets + 1u));
   L.agg = take((size_t)8 * pl.nscan);
   L.incl = take((size_t)8 * pl.nscan);
   L.flag = take((size_t)4 * pl.nscan);
@@ -598,9 +631,17 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
 cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
   if (h->plan.global) {
     void* args[] = {&h->P, &h->GP};
-    cudaError_t e = cudaLaunchKernel(h->plan.gk.weight, dim3(h->plan.grid_weight), dim3(kBlock), args, 0, stream);
+    cudaError_t e = cudaLaunchKernel(h->plan.gk.weight, dim3(h->plan.grid_weight), dim3(kBlock), args,
+                                     h->plan.smem_weight, stream);
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel(h->plan.gk.refine, dim3((1u << h->plan.cbits) * h->plan.nseg), dim3(kBlock), args,
+                           h->plan.smem_refine, stream);
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.scan, dim3(h->plan.nscan), dim3(kBlock), args, 0, stream);
-    if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.draw, dim3(h->plan.grid_draw), dim3(kBlock), args, 0, stream);
+    const uint32_t nbw = (uint32_t)(((uint64_t)(h->plan.buckets + 1u) * 32u + kBlock - 1) / kBlock);
+    if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.bounds, dim3(nbw), dim3(kBlock), args, 0, stream);
+    if (e == cudaSuccess)
+      e = cudaLaunchKernel(h->plan.gk.resolve, dim3(h->plan.buckets), dim3(kBlock), args, h->plan.smem_resolve, stream);
+    if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.advance, dim3(1), dim3(32), args, 0, stream);
     return e;
   }
   if (h->plan.islands) {    // within-island stage, island stages, gather + mutation
@@ -758,13 +799,24 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
     G.xbuf[1] = reinterpret_cast<float*>(h->ws + L.x2);
     G.lw = reinterpret_cast<float*>(h->ws + L.lw);
     G.P = reinterpret_cast<unsigned long long*>(h->ws + L.P);
-    G.top = reinterpret_cast<unsigned long long*>(h->ws + L.top);
     G.agg = reinterpret_cast<unsigned long long*>(h->ws + L.agg);
     G.incl = reinterpret_cast<unsigned long long*>(h->ws + L.incl);
     G.flag = reinterpret_cast<uint32_t*>(h->ws + L.flag);
+    G.slot = reinterpret_cast<uint4*>(h->ws + L.slot);
+    G.cnt = reinterpret_cast<uint32_t*>(h->ws + L.cnt);
+    G.ovf = reinterpret_cast<uint4*>(h->ws + L.ovf);
+    G.cslot = reinterpret_cast<uint4*>(h->ws + L.cslot);
+    G.ccnt = reinterpret_cast<uint32_t*>(h->ws + L.ccnt);
+    G.covf = reinterpret_cast<uint4*>(h->ws + L.covf);
+    G.jb = reinterpret_cast<uint32_t*>(h->ws + L.jb);
+    G.cbits = pl.cbits;
+    G.ccap = pl.ccap;
+    G.nseg = pl.nseg;
     G.nscan = pl.nscan;
-    G.ntop = pl.ntop;
-    G.top_shift = pl.top_shift;
+    G.log2b = pl.log2b;
+    G.buckets = pl.buckets;
+    G.cap = pl.bucket_cap;
+    G.stage_cap = pl.stage_cap;
     G.stall_tile = (opts && (opts->flags & PF_TEST_SCAN_TIMEOUT) && pl.nscan > 1) ? 1u : 0u;
   }
 
@@ -783,6 +835,8 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
   if (pl.global) {
     e = cudaMemsetAsync(h->ws + L.flag, 0, (size_t)4 * pl.nscan, h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.cnt, 0, (size_t)4 * (pl.buckets + 1u), h->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.ccnt, 0, (size_t)4 * ((1u << pl.cbits) + 1u), h->stream);
     if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
   }
   int sms = 0;
@@ -1077,7 +1131,10 @@ pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
                   "\", \"digits\": [";
   if (pl.global)
     o += "{\"a\": " + std::to_string(pl.N) + ", \"s\": 1, \"kernel\": \"global\", \"scan_tiles\": " +
-         std::to_string(pl.nscan) + ", \"grid\": " + std::to_string(pl.grid_draw) + "}";
+         std::to_string(pl.nscan) + ", \"grid\": " + std::to_string(pl.grid_weight) + ", \"buckets\": " +
+         std::to_string(pl.buckets) + ", \"bucket_cap\": " + std::to_string(pl.bucket_cap) +
+         ", \"stage_cap\": " + std::to_string(pl.stage_cap) + ", \"coarse_bins\": " +
+         std::to_string(1u << pl.cbits) + ", \"coarse_cap\": " + std::to_string(pl.ccap) + "}";
   else
   for (int k = 0; k < pl.m; ++k) {
     const DigitPlan& dp = pl.dp[k];

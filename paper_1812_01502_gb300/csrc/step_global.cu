@@ -7,16 +7,32 @@
 // The draw follows the same integer rule as the butterfly kernels with one
 // group of N members: q_i = floor(fp32 exp(lw_i - max lw) 2^32), P = inclusive
 // prefix (64-bit), u_i = floor(r_i Q / 2^64) with a 64-bit uniform r_i from
-// counter (i/2, n, 3, 0), ancestor = #{j : P_j <= u_i}.  Three kernels:
+// counter (i/2, n, 3, 0), ancestor = #{j : P_j <= u_i}.  Six kernels:
 //   1. weights: lw_i to memory, block partials -> last block: likelihood
 //      increment, mean, ESS, the global maximum and the one group's weight;
-//   2. scan: single-pass decoupled look-back prefix sum of q (tiles handed
+//      every draw (i, r_i) is also filed under its coarse bin (the top cbits
+//      bits of r_i), counted per chunk of particles in shared memory so that
+//      one global atomic reserves a run of slots per bin and chunk;
+//   2. refine: the same per coarse bin, filing every draw under its bucket
+//      b = top log2b bits of r_i (fixed capacity per bucket, an overflow list
+//      behind it);
+//   3. scan: single-pass decoupled look-back prefix sum of q (tiles handed
 //      out by an atomic ticket so a tile only waits on tiles already running;
-//      waits are bounded and report kStatusTimeout); also records P at every
-//      2^top_shift-th index (the top table of the search);
-//   3. draws: top table in shared memory, binary search there, then inside
-//      one segment of P in global memory; gather the ancestor's state (random
-//      access), mutate, write the other state buffer; the last block advances n.
+//      waits are bounded and report kStatusTimeout), loads and stores staged
+//      through shared memory so that both are coalesced;
+//   4. bounds: u is monotone in r, so bucket b covers the u interval from
+//      floor(b 2^(64-log2b) Q / 2^64) to the next bucket's start; one warp per
+//      bucket edge finds jb[b] = #{j : P_j <= that u} by a 32-ary search;
+//   5. resolve: one block per bucket stages P[jb[b] .. jb[b+1]) and the
+//      states x[jb[b] .. jb[b+1]] in shared memory, counts P_j <= u_i there for
+//      every particle of the bucket (its index and uniform were filed by
+//      kernels 1 and 2), gathers and mutates, and writes the particle's new
+//      state; a
+//      bucket whose index range is longer than the staging buffer, and the
+//      overflow list, search P in global memory;
+//   6. advance: one thread clears the overflow counts and advances n.
+// Every particle's ancestor is #{j : P_j <= u_i} whatever the bucket layout:
+// bucketing only decides where the count is taken.
 #include <cfloat>
 
 #include "bfpf_device.cuh"
@@ -39,9 +55,110 @@ __device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
 
 }  // namespace
 
+// Bucket of a uniform: its top log2b bits.
+__device__ __forceinline__ uint32_t bucket_of(unsigned long long r, uint32_t log2b) {
+  return log2b ? (uint32_t)(r >> (64u - log2b)) : 0u;
+}
+
+// A filed draw: {i, payload (unused, 0), low and high words of r_i}.
+__device__ __forceinline__ uint4 draw_entry(uint32_t i, uint32_t payload, unsigned long long r) {
+  return make_uint4(i, payload, (uint32_t)r, (uint32_t)(r >> 32));
+}
+__device__ __forceinline__ unsigned long long entry_r(uint4 e) {
+  return ((unsigned long long)e.w << 32) | e.z;
+}
+
+// File draw (i, r) straight into its bucket (or the overflow list): the path
+// of the rare draws whose coarse bin was full.
+__device__ __forceinline__ void file_direct(const GlobalParams& gp, uint4 e) {
+  const uint32_t b = bucket_of(entry_r(e), gp.log2b);
+  const uint32_t pos = atomicAdd(gp.cnt + b, 1u);
+  if (pos < gp.cap) gp.slot[(size_t)b * gp.cap + pos] = e;
+  else gp.ovf[atomicAdd(gp.cnt + gp.buckets, 1u)] = e;
+}
+
+// File one block's chunk of draws (thread t holds V of them: index i, payload,
+// uniform r, bin = bin_of(r), valid) into nbins bins of capacity cap: dst[bin * cap + pos], pos
+// reserved from gcnt[bin]; a draw whose bin is full goes to ovf[*ovf_cnt++].
+// The chunk is counted per bin in shared memory, each non-empty bin reserves
+// its run with one global atomic, and the draws are ordered by bin in shared
+// memory first so that consecutive threads write consecutive slots.
+// Shared memory: s_cnt[nbins], s_off[nbins], s_buf[kBlock * V].
+template <int V, class BinOf>
+__device__ __forceinline__ void file_chunk(const uint32_t (&i)[V], const uint32_t (&pay)[V],
+                                           const unsigned long long (&r)[V], const uint32_t (&bin)[V],
+                                           const bool (&valid)[V], BinOf bin_of, uint32_t nbins, uint32_t* gcnt,
+                                           uint4* dst, uint32_t cap, uint32_t* ovf_cnt, uint4* ovf, uint32_t* s_cnt,
+                                           uint32_t* s_off, uint4* s_buf) {
+  constexpr int NW = kBlock / 32;
+  __shared__ uint32_t s_wsum[NW];
+  __shared__ uint32_t s_total;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  for (uint32_t k = tid; k < nbins; k += kBlock) s_cnt[k] = 0;
+  __syncthreads();
+  uint32_t rank[V];
+#pragma unroll
+  for (int j = 0; j < V; ++j) rank[j] = valid[j] ? atomicAdd(s_cnt + bin[j], 1u) : 0u;
+  __syncthreads();
+  // exclusive scan of the counts (E consecutive bins per thread) and one
+  // global reservation per non-empty bin
+  const uint32_t E = (nbins + kBlock - 1u) / kBlock;
+  const uint32_t k0 = min(tid * E, nbins), k1 = min(k0 + E, nbins);
+  uint32_t sum = 0;
+  for (uint32_t k = k0; k < k1; ++k) sum += s_cnt[k];
+  uint32_t incl = sum;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+    if ((int)lane >= off) incl += v;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    uint32_t v = (lane < NW) ? s_wsum[lane] : 0u;
+#pragma unroll
+    for (int off = 1; off < NW; off <<= 1) {
+      const uint32_t o = __shfl_up_sync(0xffffffffu, v, off);
+      if ((int)lane >= off) v += o;
+    }
+    if (lane < NW) s_wsum[lane] = v;
+    if (lane == NW - 1) s_total = v;
+  }
+  __syncthreads();
+  uint32_t run = (warp ? s_wsum[warp - 1] : 0u) + incl - sum;
+  for (uint32_t k = k0; k < k1; ++k) {
+    const uint32_t c = s_cnt[k];
+    s_off[k] = run;
+    run += c;
+    s_cnt[k] = c ? atomicAdd(gcnt + k, c) : 0u;   // the run's first slot in the bin
+  }
+  __syncthreads();
+#pragma unroll
+  for (int j = 0; j < V; ++j)
+    if (valid[j]) s_buf[s_off[bin[j]] + rank[j]] = draw_entry(i[j], pay[j], r[j]);
+  __syncthreads();
+  const uint32_t total = s_total;
+  for (uint32_t k = tid; k < total; k += kBlock) {
+    const uint4 e = s_buf[k];
+    const uint32_t b = bin_of(entry_r(e));
+    const uint32_t pos = s_cnt[b] + (k - s_off[b]);
+    if (pos < cap) dst[(size_t)b * cap + pos] = e;
+    else ovf[atomicAdd(ovf_cnt, 1u)] = e;
+  }
+  __syncthreads();                                 // the caller reuses the shared buffers
+}
+
+// Weights and the coarse filing.  The particles are taken in chunks of
+// kBlock * V consecutive indices (V per thread); every draw of a chunk is
+// filed under its coarse bin, the top cbits bits of r_i.
 template <int D, int KIND>
 __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_constant__ StepParams p,
                                                               const __grid_constant__ GlobalParams gp) {
+  constexpr int V = global_weight_vec(D);
+  constexpr uint32_t CH = kBlock * V;
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  uint4* const s_buf = reinterpret_cast<uint4*>(s_dyn);                 // [CH]
+  uint32_t* const s_cnt = reinterpret_cast<uint32_t*>(s_buf + CH);      // [2^cbits]
   const ModelParams& mp = p.model;
   DevState* st = p.st;
   const uint32_t n = st->n;
@@ -49,6 +166,7 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
   const float lv = p.lV[n & 1u][0];            // one group: one carried weight
   const float muf = st->mu_f;
   const uint32_t N = p.N;
+  const uint32_t tid = threadIdx.x;
   float y[kMaxDim];
 #pragma unroll
   for (int q = 0; q < kMaxDim; ++q) y[q] = (q < mp.dy) ? p.y_ring[(n % kRing) * mp.dy + q] : 0.0f;
@@ -57,25 +175,130 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
   float accx[D];
 #pragma unroll
   for (int t = 0; t < D; ++t) accx[t] = 0.0f;
-  for (uint32_t i = blockIdx.x * kBlock + threadIdx.x; i < N; i += gridDim.x * kBlock) {
-    float xv[D];
+  const uint32_t cbits = gp.cbits, nbins = 1u << cbits;
+  uint32_t* const s_off = s_cnt + nbins;                                 // [2^cbits]
+  const bool vec = (N % 4u) == 0u;
+  const uint32_t nchunk = (N + CH - 1u) / CH;
+  for (uint32_t ch = blockIdx.x; ch < nchunk; ch += gridDim.x) {   // block-uniform loop
+    const uint32_t i0 = ch * CH + tid * V;
+    const bool full = vec && i0 + V <= N;
+    float xv[V][D];
+    float lw[V];
+    if (full) {
 #pragma unroll
-    for (int t = 0; t < D; ++t) xv[t] = __ldcs(X + (size_t)t * N + i);
-    const float lw = sanitize_logweight(lv + obs_log_term<D, KIND>(mp, y, xv) - muf, status);
-    gp.lw[i] = lw;
-    if (lw != -INFINITY) {
-      float one[D];
+      for (int t = 0; t < D; ++t) {
 #pragma unroll
-      for (int t = 0; t < D; ++t) one[t] = xv[t];
-      merge_partial<D>(acc, accx, lw, 1.0f, 1.0f, one);
+        for (int h = 0; h < V / 4; ++h) {
+          const float4 v = __ldcs(reinterpret_cast<const float4*>(X + (size_t)t * N + i0) + h);
+          xv[4 * h][t] = v.x; xv[4 * h + 1][t] = v.y; xv[4 * h + 2][t] = v.z; xv[4 * h + 3][t] = v.w;
+        }
+      }
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+#pragma unroll
+        for (int t = 0; t < D; ++t) xv[j][t] = (i0 + j < N) ? __ldcs(X + (size_t)t * N + i0 + j) : 0.0f;
     }
+#pragma unroll
+    for (int j = 0; j < V; ++j)
+      lw[j] = (i0 + j < N) ? sanitize_logweight(lv + obs_log_term<D, KIND>(mp, y, xv[j]) - muf, status) : -INFINITY;
+    if (full) {
+#pragma unroll
+      for (int h = 0; h < V / 4; ++h)
+        reinterpret_cast<float4*>(gp.lw + i0)[h] = make_float4(lw[4 * h], lw[4 * h + 1], lw[4 * h + 2], lw[4 * h + 3]);
+    } else {
+#pragma unroll
+      for (int j = 0; j < V; ++j)
+        if (i0 + j < N) gp.lw[i0 + j] = lw[j];
+    }
+#pragma unroll
+    for (int h = 0; h < V / 4; ++h) {            // one partial merge per four particles
+      const float m4 = fmaxf(fmaxf(lw[4 * h], lw[4 * h + 1]), fmaxf(lw[4 * h + 2], lw[4 * h + 3]));
+      if (m4 != -INFINITY) {
+        float s1 = 0.0f, s2 = 0.0f, sx[D];
+#pragma unroll
+        for (int t = 0; t < D; ++t) sx[t] = 0.0f;
+#pragma unroll
+        for (int j = 4 * h; j < 4 * h + 4; ++j) {
+          const float e = exp_weight(lw[j] - m4);   // 0 for a log-weight of -inf
+          s1 += e;
+          s2 = fmaf(e, e, s2);
+#pragma unroll
+          for (int t = 0; t < D; ++t) sx[t] = fmaf(e, xv[j][t], sx[t]);
+        }
+        merge_partial<D>(acc, accx, m4, s1, s2, sx);
+      }
+    }
+    // uniforms (pairs of particles share a Philox block) and their coarse bins
+    uint32_t ii[V], cb[V], pay[V];
+    unsigned long long r[V];
+    bool valid[V];
+#pragma unroll
+    for (int j = 0; j < V; ++j) pay[j] = 0;
+#pragma unroll
+    for (int h = 0; h < V / 2; ++h) {
+      const uint4 w = philox4x32_10(make_uint4(i0 / 2u + h, n, kPurposeResampleWide, 0), p.rk);
+      r[2 * h] = ((unsigned long long)w.y << 32) | w.x;
+      r[2 * h + 1] = ((unsigned long long)w.w << 32) | w.z;
+    }
+#pragma unroll
+    for (int j = 0; j < V; ++j) {
+      ii[j] = i0 + j;
+      cb[j] = bucket_of(r[j], cbits);
+      valid[j] = i0 + j < N;
+    }
+    file_chunk<V>(ii, pay, r, cb, valid, [cbits](unsigned long long rr) { return bucket_of(rr, cbits); }, nbins,
+                  gp.ccnt, gp.cslot, gp.ccap, gp.ccnt + nbins, gp.covf, s_cnt, s_off, s_buf);
   }
   const Sched sc{n, n, 0u, true, true};   // one digit (m = 1): every step is one whole stage
   finish_step<D, false>(p, acc, accx, sc, status, muf, p.lV[(n & 1u) ^ 1u]);
 }
 
+// Fine filing: block (coarse bin cb, segment sg) takes kRefineSeg entries of
+// the bin and files each under its bucket (the next log2b - cbits bits of r),
+// the same way.  Draws of the coarse overflow list are filed one by one.
+__global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_constant__ StepParams p,
+                                                              const __grid_constant__ GlobalParams gp) {
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  uint4* const s_buf = reinterpret_cast<uint4*>(s_dyn);                 // [kRefineSeg]
+  uint32_t* const s_cnt = reinterpret_cast<uint32_t*>(s_buf + kRefineSeg);
+  const uint32_t tid = threadIdx.x;
+  const uint32_t cbits = gp.cbits, fbits = gp.log2b - cbits, nfine = 1u << fbits;
+  uint32_t* const s_off = s_cnt + nfine;
+  const uint32_t cb = blockIdx.x / gp.nseg, sg = blockIdx.x % gp.nseg;
+  const uint32_t cfill = min(__ldcg(gp.ccnt + cb), gp.ccap);
+  const uint32_t e0 = sg * kRefineSeg;
+  if (e0 < cfill) {                                // block-uniform
+    const size_t cbase = (size_t)cb * gp.ccap;
+    uint32_t ii[kRefineItems], pay[kRefineItems], fb[kRefineItems];
+    unsigned long long rr[kRefineItems];
+    bool valid[kRefineItems];
+#pragma unroll
+    for (int q = 0; q < kRefineItems; ++q) {
+      const uint32_t e = e0 + q * kBlock + tid;
+      valid[q] = e < cfill;
+      const uint4 en = valid[q] ? __ldcs(gp.cslot + cbase + e) : make_uint4(0, 0, 0, 0);
+      ii[q] = en.x;
+      pay[q] = en.y;
+      rr[q] = entry_r(en);
+      fb[q] = bucket_of(rr[q], gp.log2b) & (nfine - 1u);
+    }
+    const size_t b0 = (size_t)cb << fbits;         // this coarse bin's first bucket
+    const uint32_t log2b = gp.log2b, fmask = nfine - 1u;
+    file_chunk<kRefineItems>(ii, pay, rr, fb, valid,
+                             [log2b, fmask](unsigned long long r) { return bucket_of(r, log2b) & fmask; }, nfine,
+                             gp.cnt + b0, gp.slot + b0 * gp.cap, gp.cap, gp.cnt + gp.buckets, gp.ovf, s_cnt, s_off,
+                             s_buf);
+  }
+  const uint32_t nco = __ldcg(gp.ccnt + (1u << cbits));
+  for (uint32_t e = blockIdx.x * kBlock + tid; e < nco; e += gridDim.x * kBlock) file_direct(gp, __ldcg(gp.covf + e));
+}
+
 __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_constant__ StepParams p,
                                                             const __grid_constant__ GlobalParams gp) {
+  // the tile's log-weights, then its prefix sums, one padding word every 32
+  // floats / 16 doubles so that thread-contiguous accesses hit distinct banks
+  __shared__ unsigned long long s_buf[kScanTile + kScanTile / 16];
   __shared__ unsigned long long s_warp[kBlock / 32];
   __shared__ unsigned long long s_prefix;
   __shared__ uint32_t s_tile;
@@ -87,27 +310,25 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
   if (tid == 0) s_tile = (uint32_t)(atomicAdd(&st->ticket, 1ull) - (unsigned long long)n * gp.nscan);
   __syncthreads();
   const uint32_t tile = s_tile;
-  const uint32_t base = tile * kScanTile + tid * kScanItems;
-  // integer weights of my 16 particles and their running sums
+  const uint32_t tbase = tile * kScanTile;
+  float* const s_f = reinterpret_cast<float*>(s_buf);
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {          // coalesced load of the tile
+    const uint32_t idx = k * kBlock + tid;
+    s_f[idx + (idx >> 5)] = (tbase + idx < N) ? __ldcs(gp.lw + tbase + idx) : -INFINITY;
+  }
+  __syncthreads();
+  // integer weights of my 16 consecutive particles and their running sums
   unsigned long long run[kScanItems];
   unsigned long long tot = 0;
-  float lwv[kScanItems];
-  if (base + kScanItems <= N) {
-#pragma unroll
-    for (int q = 0; q < kScanItems / 4; ++q) {
-      const float4 v = __ldcs(reinterpret_cast<const float4*>(gp.lw + base) + q);
-      lwv[4 * q] = v.x; lwv[4 * q + 1] = v.y; lwv[4 * q + 2] = v.z; lwv[4 * q + 3] = v.w;
-    }
-  } else {
-#pragma unroll
-    for (int q = 0; q < kScanItems; ++q) lwv[q] = (base + q < N) ? gp.lw[base + q] : -INFINITY;
-  }
   if (tid == 0 && tile == 0 && gmax == -INFINITY) atomicOr(&st->status, kStatusZeroGroup);
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
+    const uint32_t idx = tid * kScanItems + q;
+    const float lw = s_f[idx + (idx >> 5)];
     unsigned long long w = 0;
     if (gmax != -INFINITY) {
-      const float e = exp_weight(lwv[q] - gmax);
+      const float e = exp_weight(lw - gmax);
       w = __float2ull_rz(e * 4294967296.0f);
     }
     tot += w;
@@ -196,125 +417,172 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
   }
   __syncthreads();
   const unsigned long long off0 = s_prefix + thread_excl;
-  const uint32_t seg_mask = (1u << gp.top_shift) - 1u;
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
-    const uint32_t i = base + q;
-    if (i < N) {
-      const unsigned long long P = off0 + run[q];
-      gp.P[i] = P;
-      if (((i + 1u) & seg_mask) == 0u || i == N - 1u) gp.top[i >> gp.top_shift] = P;
-    }
+    const uint32_t idx = tid * kScanItems + q;
+    s_buf[idx + (idx >> 4)] = off0 + run[q];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int k = 0; k < kScanItems; ++k) {          // coalesced store of the tile
+    const uint32_t idx = k * kBlock + tid;
+    if (tbase + idx < N) gp.P[tbase + idx] = s_buf[idx + (idx >> 4)];
   }
 }
 
+// jb[b] = #{j : P_j <= u_b} for every bucket edge b = 0 .. buckets, with u_b
+// the smallest u of bucket b (u_buckets = Q - 1, the largest u of all): one
+// warp per edge, 32 probes per round (P is non-decreasing, so the probes at or
+// below u form a prefix of the warp).
+__global__ void __launch_bounds__(kBlock) global_bounds_kernel(const __grid_constant__ StepParams p,
+                                                              const __grid_constant__ GlobalParams gp) {
+  const uint32_t lane = threadIdx.x & 31u;
+  const uint32_t b = (blockIdx.x * kBlock + threadIdx.x) >> 5;
+  if (b > gp.buckets) return;                     // whole warps
+  const uint32_t N = p.N;
+  const unsigned long long Q = __ldcg(gp.P + (N - 1u));
+  uint32_t lo = 0;
+  if (Q != 0) {
+    unsigned long long u = 0;
+    if (b == gp.buckets) u = Q - 1u;
+    else if (gp.log2b) u = __umul64hi((unsigned long long)b << (64u - gp.log2b), Q);
+    // invariant: P_j <= u for j < lo, P_j > u for j >= lo + span
+    uint32_t span = N;
+    while (span) {
+      const uint32_t s = (span - 1u) / 32u + 1u;
+      const unsigned long long off = (unsigned long long)(lane + 1u) * s;
+      const bool le = off <= span && __ldcg(gp.P + lo + (uint32_t)(off - 1u)) <= u;
+      const uint32_t c = __popc(__ballot_sync(0xffffffffu, le));
+      const uint32_t nlo = lo + c * s;
+      span = min(s - 1u, lo + span - nlo);
+      lo = nlo;
+    }
+  }
+  if (lane == 0) gp.jb[b] = lo;
+}
+
+// Ancestor, gather and mutation of particle i with uniform r.  Its ancestor
+// lies in [lo, lo + len]: ancestor = lo + #{j in [lo, lo + len) : P_j <= u},
+// counted in the staged copy (sP; states sX with row stride SC + 1) or in
+// global memory.
 template <int D, int KIND>
-__global__ void __launch_bounds__(kBlock) global_draw_kernel(const __grid_constant__ StepParams p,
-                                                            const __grid_constant__ GlobalParams gp) {
-  __shared__ unsigned long long s_top[kTopMax];
-  __shared__ uint32_t s_last;
-  const ModelParams& mp = p.model;
+__device__ __forceinline__ void resolve_draw(const StepParams& p, const GlobalParams& gp, const float* __restrict__ Xin,
+                                             float* __restrict__ Xout, unsigned long long Q, uint32_t n, uint4 en,
+                                             bool staged, uint32_t lo, uint32_t len,
+                                             const unsigned long long* sP, const float* sX) {
+  constexpr uint32_t SC = global_stage_alloc(D);
+  static_assert((SC & (SC - 1)) == 0, "staging buffer must hold a power of two of indices");
+  const uint32_t N = p.N;
+  const uint32_t i = en.x;
+  const unsigned long long r = entry_r(en);
+  uint32_t anc = i;                                // an all-zero population keeps its particles
+  float xh[D];
+  if (Q != 0) {
+    const unsigned long long u = __umul64hi(r, Q);
+    uint32_t c = 0;
+    if (staged) {                                  // sP padded with 2^64 - 1 up to the power of two above len
+      for (uint32_t stp = (1u << (32 - __clz(len))) >> 1; stp; stp >>= 1) c += (sP[c + stp - 1u] <= u) ? stp : 0u;
+#pragma unroll
+      for (int t = 0; t < D; ++t) xh[t] = sX[t * (SC + 1u) + c];
+    } else {
+      const unsigned long long* Pg = gp.P + lo;
+      for (uint32_t stp = len ? (1u << (31 - __clz(len))) : 0u; stp; stp >>= 1)
+        if (c + stp <= len && __ldcg(Pg + c + stp - 1u) <= u) c += stp;
+#pragma unroll
+      for (int t = 0; t < D; ++t) xh[t] = __ldg(Xin + (size_t)t * N + lo + c);
+    }
+    anc = lo + c;
+  } else {
+#pragma unroll
+    for (int t = 0; t < D; ++t) xh[t] = __ldg(Xin + (size_t)t * N + i);
+  }
+  // propagation normals nu = i d + t: Philox block nu / 4, Box-Muller pairs of its words
+  float z[D];
+  {
+    uint4 w = make_uint4(0, 0, 0, 0);
+    float z0 = 0.0f, z1 = 0.0f;
+    const uint32_t nu0 = i * D;
+#pragma unroll
+    for (int t = 0; t < D; ++t) {
+      const uint32_t nu = nu0 + t;
+      if (t == 0 || (nu & 3u) == 0u) w = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
+      if (t == 0 || (nu & 1u) == 0u) box_muller_fast((nu & 2u) ? w.z : w.x, (nu & 2u) ? w.w : w.y, z0, z1);
+      z[t] = (nu & 1u) ? z1 : z0;
+    }
+  }
+  float xo[D];
+  mutate<D, KIND>(p.model, xh, z, xo);
+#pragma unroll
+  for (int t = 0; t < D; ++t) Xout[(size_t)t * N + i] = xo[t];
+  if (p.anc) p.anc[i] = (int32_t)anc;
+}
+
+// One block per bucket (grid = buckets), then the overflow list grid-stride.
+template <int D, int KIND>
+__global__ void __launch_bounds__(kBlock) global_resolve_kernel(const __grid_constant__ StepParams p,
+                                                               const __grid_constant__ GlobalParams gp) {
+  constexpr uint32_t SC = global_stage_alloc(D);
+  extern __shared__ __align__(16) unsigned char s_dyn[];
+  unsigned long long* const sP = reinterpret_cast<unsigned long long*>(s_dyn);   // [SC]
+  float* const sX = reinterpret_cast<float*>(sP + SC);                            // [D][SC + 1]
   DevState* st = p.st;
   const uint32_t n = st->n;
   const uint32_t N = p.N;
+  const uint32_t tid = threadIdx.x, b = blockIdx.x;
   const float* __restrict__ Xin = gp.xbuf[n & 1u];
   float* __restrict__ Xout = gp.xbuf[(n & 1u) ^ 1u];
-  const uint32_t ntop = gp.ntop;
-  for (uint32_t j = threadIdx.x; j < ntop; j += kBlock) s_top[j] = __ldcg(gp.top + j);
-  __syncthreads();
-  const unsigned long long Q = s_top[ntop - 1];
-  uint32_t lsteps = 1;   // power of two > ntop / 2 for binary lifting over the table
-  while (lsteps < ntop) lsteps <<= 1;
-  const uint32_t seg = 1u << gp.top_shift;
-  uint32_t fsteps = 1;
-  while (fsteps < seg) fsteps <<= 1;
-  // top table: number of its first ntop - 1 entries <= u (binary lifting in shared memory)
-  auto top_count = [&](unsigned long long u) -> uint32_t {
-    uint32_t c = 0;
-    for (uint32_t stp = lsteps >> 1; stp; stp >>= 1)
-      if (c + stp <= ntop - 1 && s_top[c + stp - 1] <= u) c += stp;
-    return c;
-  };
-  auto search = [&](unsigned long long u) -> uint32_t {
-    const uint32_t lo = top_count(u) << gp.top_shift;
-    const uint32_t len = min(seg, N - lo);
-    uint32_t f = 0;   // number of P_j <= u inside the segment (< len)
-    for (uint32_t stp = fsteps >> 1; stp; stp >>= 1)
-      if (f + stp <= len - 1 && __ldcg(gp.P + lo + f + stp - 1) <= u) f += stp;
-    return lo + f;
-  };
-  // quads of consecutive particles share their Philox blocks
-  const uint32_t nquad = (N % 4u == 0u) ? N / 4u : 0u;
-  for (uint32_t q = blockIdx.x * kBlock + threadIdx.x; q < nquad; q += gridDim.x * kBlock) {
-    const uint32_t i0 = 4u * q;
-    const uint4 w0 = philox4x32_10(make_uint4(i0 >> 1, n, kPurposeResampleWide, 0), p.rk);
-    const uint4 w1 = philox4x32_10(make_uint4((i0 >> 1) + 1, n, kPurposeResampleWide, 0), p.rk);
-    const unsigned long long r64[4] = {((unsigned long long)w0.y << 32) | w0.x,
-                                       ((unsigned long long)w0.w << 32) | w0.z,
-                                       ((unsigned long long)w1.y << 32) | w1.x,
-                                       ((unsigned long long)w1.w << 32) | w1.z};
-    float z[4 * D];
-#pragma unroll
-    for (int b = 0; b < D; ++b) {
-      const uint4 wz = philox4x32_10(make_uint4(q * D + b, n, kPurposePropagate, 0), p.rk);
-      normals4(wz, z + 4 * b);
-    }
-    float xo[D][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const uint32_t anc = (Q != 0) ? search(__umul64hi(r64[j], Q)) : i0 + j;
-      float xh[D], o[D];
-#pragma unroll
-      for (int t = 0; t < D; ++t) xh[t] = __ldg(Xin + (size_t)t * N + anc);
-      mutate<D, KIND>(mp, xh, z + j * D, o);
-#pragma unroll
-      for (int t = 0; t < D; ++t) xo[t][j] = o[t];
-      if (p.anc) p.anc[i0 + j] = (int32_t)anc;
-    }
+  const unsigned long long Q = __ldcg(gp.P + (N - 1u));
+  const uint32_t filled = min(__ldcg(gp.cnt + b), gp.cap);
+  const uint32_t lo = __ldcg(gp.jb + b);
+  const uint32_t len = __ldcg(gp.jb + b + 1u) - lo;
+  const bool staged = Q != 0 && len < gp.stage_cap;
+  const size_t s0 = (size_t)b * gp.cap;
+  // the first draw of every thread is loaded before the staging, so that the
+  // two latencies overlap
+  const bool first = tid < filled;
+  const uint4 e_first = first ? __ldcs(gp.slot + s0 + tid) : make_uint4(0, 0, 0, 0);
+  if (staged) {
+    const uint32_t p2 = 1u << (32 - __clz(len));   // power of two above len (<= SC)
+    for (uint32_t j = tid; j < p2; j += kBlock) sP[j] = (j < len) ? __ldcg(gp.P + lo + j) : ~0ull;
 #pragma unroll
     for (int t = 0; t < D; ++t)
-      __stcs(reinterpret_cast<float4*>(Xout + (size_t)t * N + i0), make_float4(xo[t][0], xo[t][1], xo[t][2], xo[t][3]));
-  }
-  for (uint32_t i = 4u * nquad + blockIdx.x * kBlock + threadIdx.x; i < N; i += gridDim.x * kBlock) {
-    const uint4 w = philox4x32_10(make_uint4(i >> 1, n, kPurposeResampleWide, 0), p.rk);
-    const unsigned long long r64 = (i & 1u) ? (((unsigned long long)w.w << 32) | w.z)
-                                             : (((unsigned long long)w.y << 32) | w.x);
-    const uint32_t anc = (Q != 0) ? search(__umul64hi(r64, Q)) : i;
-    float xh[D], xo[D], z[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t) {
-      xh[t] = __ldg(Xin + (size_t)t * N + anc);
-      const uint32_t nu = i * D + t;
-      const uint4 wz = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
-      float zz[4];
-      normals4(wz, zz);
-      z[t] = zz[nu & 3u];
-    }
-    mutate<D, KIND>(mp, xh, z, xo);
-#pragma unroll
-    for (int t = 0; t < D; ++t) __stcs(Xout + (size_t)t * N + i, xo[t]);
-    if (p.anc) p.anc[i] = (int32_t)anc;
-  }
-  // the last block to finish advances the step counter
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const uint32_t prev = atomicAdd(&st->done2, 1u);
-    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
+      for (uint32_t j = tid; j <= len; j += kBlock) sX[t * (SC + 1u) + j] = __ldg(Xin + (size_t)t * N + lo + j);
   }
   __syncthreads();
-  if (s_last && threadIdx.x == 0) {
-    st->done2 = 0;
-    __threadfence();
-    st->n = n + 1;
+  if (tid == 0) {                                  // zero the counters for the next step
+    gp.cnt[b] = 0;                                 // (read above by every thread)
+    if (b < (1u << gp.cbits)) gp.ccnt[b] = 0;
   }
+  if (first) resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, e_first, staged, lo, len, sP, sX);
+  for (uint32_t e = tid + kBlock; e < filled; e += kBlock) {
+    const uint4 en = __ldcs(gp.slot + s0 + e);
+    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, en, staged, lo, len, sP, sX);
+  }
+  const uint32_t nov = __ldcg(gp.cnt + gp.buckets);
+  for (uint32_t e = b * kBlock + tid; e < nov; e += gridDim.x * kBlock) {
+    const uint4 en = __ldcg(gp.ovf + e);
+    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, en, false, 0u, N, sP, sX);
+  }
+}
+
+// End of the step (one thread, after the resolve kernel): clear the overflow
+// counts and advance the step counter.  A separate launch, so that no resolve
+// block waits for its scattered stores before it retires.
+__global__ void global_advance_kernel(const __grid_constant__ StepParams p, const __grid_constant__ GlobalParams gp) {
+  if (threadIdx.x != 0 || blockIdx.x != 0) return;
+  gp.cnt[gp.buckets] = 0;
+  gp.ccnt[1u << gp.cbits] = 0;
+  p.st->n = p.st->n + 1;
 }
 
 template <int D, int KIND>
 static void fill_global(GlobalKernels& gk) {
   gk.weight = reinterpret_cast<const void*>(&global_weight_kernel<D, KIND>);
   gk.scan = reinterpret_cast<const void*>(&global_scan_kernel);
-  gk.draw = reinterpret_cast<const void*>(&global_draw_kernel<D, KIND>);
+  gk.refine = reinterpret_cast<const void*>(&global_refine_kernel);
+  gk.bounds = reinterpret_cast<const void*>(&global_bounds_kernel);
+  gk.resolve = reinterpret_cast<const void*>(&global_resolve_kernel<D, KIND>);
+  gk.advance = reinterpret_cast<const void*>(&global_advance_kernel);
 }
 
 bool select_global_kernels(int d, int kind, GlobalKernels& gk) {

@@ -96,7 +96,7 @@ def test_lockstep_sv_group_kernel(bfpf):
 
 @pytest.mark.parametrize("d,N,T", [(1, 4096, 5), (1, 1 << 16, 3), (4, 5000, 3), (8, 1 << 14, 2), (0, 1 << 15, 4)])
 def test_lockstep_global_resampling(bfpf, d, N, T):
-    """radices = {N} above one block: the three-kernel global path (d = 0 means SV)."""
+    """radices = {N} above one block: the four-kernel global path (d = 0 means SV)."""
     model = S.sv_model() if d == 0 else (S.lg_scalar() if d == 1 else S.lg_dense(d, seed=d))
     y = S.simulate(model, T, seed=41)[1]
     f = _filter(bfpf, model, (N,), 606)
@@ -110,6 +110,38 @@ def test_lockstep_global_resampling(bfpf, d, N, T):
     # With one group of N members the worst-case margin (ETA times a cumulative sum)
     # spans several boundary spacings, so most draws count as undecidable; the
     # actual FP32/FP64 differences are far smaller: nearly all draws agree exactly.
+    assert rep["mismatched_undecidable"] <= 0.001 * rep["draws"]
+
+
+@pytest.mark.parametrize("d,N,T,small,outlier", [
+    (1, 4099, 3, False, False),        # N not a multiple of 4: scalar weight loop, ragged scan tile
+    (1, 1 << 15, 3, False, True),      # one far observation: most integer weights tiny or zero
+    (2, 1 << 15, 2, True, False),      # 16 draws per bucket: the overflow list and global searches
+    (0, 1 << 16, 2, True, False),
+    (8, 5000, 2, True, True),
+    (1, 1025, 2, False, False),        # one bucket
+])
+def test_lockstep_global_bucket_paths(bfpf, d, N, T, small, outlier):
+    """The global draws are resolved per bucket of their uniform; every layout
+    of buckets (staged in shared memory, searched in global memory, overflow)
+    must give the oracle's ancestors."""
+    model = S.sv_model() if d == 0 else (S.lg_scalar() if d == 1 else S.lg_dense(d, seed=d))
+    y = S.simulate(model, T, seed=43)[1]
+    if outlier:
+        y = y.copy()
+        y[0] = 8.0
+    flags = bfpf.PF_TEST_SMALL_BUCKETS if small else 0
+    f = _filter(bfpf, model, (N,), 607, extra_flags=flags)
+    dg = f.describe()["digits"][0]
+    assert dg["kernel"] == "global"
+    if small:
+        assert dg["bucket_cap"] == 16 and dg["stage_cap"] == 64
+    rep = LS.Report()
+    for n in range(T):
+        rep.merge(LS.check_step_full(f, model, (N,), 607, y[n], n))
+    assert f.status() == 0
+    f.close()
+    print("global buckets", d, N, small, outlier, dict(rep))
     assert rep["mismatched_undecidable"] <= 0.001 * rep["draws"]
 
 
