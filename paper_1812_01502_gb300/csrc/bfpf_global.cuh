@@ -1,0 +1,52 @@
+// bfpf_global.cuh - buffers and sizes of the global-resampling path
+// (radices = {N}, N above one thread block): Algorithm 2 of Heine, Whiteley &
+// Cemgil, arXiv 1812.01502, over all N particles.
+#pragma once
+
+#include <cstdint>
+
+#include "bfpf_device.cuh"
+
+namespace bfpf {
+
+// Buffers of the global-resampling path (m = 1, N > kMaxCtaRadix).
+// The draws are resolved by bucket: particle i goes to bucket b = the top
+// log2b bits of its 64-bit uniform r_i, so every bucket covers one interval of
+// u = floor(r Q / 2^64) and hence one index range [jb[b], jb[b+1]] of
+// ancestors, which is staged in shared memory.
+struct GlobalParams {
+  float* xbuf[2];                 // states, ping-pong by time-step parity (gather is random)
+  float* lw;                      // [N] log-weights of the step
+  unsigned long long* P;          // [N] inclusive prefix sums of the integer weights
+  unsigned long long* agg;        // [nscan] scan tile aggregates
+  unsigned long long* incl;       // [nscan] scan tile inclusive prefixes
+  uint32_t* flag;                 // [nscan] 2n+1: aggregate ready, 2n+2: prefix ready (step n)
+  // A filed draw is one 16-byte entry {i, 0, low and high words of r_i}.
+  uint4* slot;                    // [buckets][cap] draws filed by bucket
+  uint32_t* cnt;                  // [buckets + 1] fill counts (zero between steps); last: overflow count
+  uint4* cslot;                   // [2^cbits][ccap] draws filed by coarse bin (top cbits bits of r)
+  uint32_t* ccnt;                 // [2^cbits + 1] coarse fill counts (zero between steps); last: overflow count
+  uint4* covf;                    // [N] draws whose coarse bin was full
+  uint4* ovf;                     // [N] draws whose bucket was full
+  uint32_t* jb;                   // [buckets + 1] jb[b] = #{j : P_j <= lowest u of bucket b}
+  uint32_t nscan;                 // scan tiles of kScanTile particles
+  uint32_t log2b, buckets;        // buckets = 2^log2b
+  uint32_t cbits, ccap, nseg;     // coarse bins 2^cbits (cbits <= 12, log2b - cbits <= 12), their
+                                  // capacity, refine blocks per coarse bin
+  uint32_t cap;                   // slots per bucket
+  uint32_t stage_cap;             // longest index range staged in shared memory (<= global_stage_alloc(d))
+  uint32_t stall_tile;            // test hook (0 = off): this scan tile waits on a flag nothing sets
+};
+
+// Consecutive particles per thread of the global weight kernel.
+__host__ __device__ constexpr int global_weight_vec(int d) { return d <= 2 ? 8 : 4; }
+// Indices of P (and states) the resolve kernel's shared-memory buffer holds.
+__host__ __device__ constexpr uint32_t global_stage_alloc(int d) { return d <= 2 ? 2048u : 1024u; }
+
+constexpr int kScanItems = 16;
+constexpr uint32_t kMaxCoarse = 4096;                          // coarse bins and buckets per coarse bin
+constexpr int kRefineItems = 8;                                // draws per thread of a refine block
+constexpr uint32_t kRefineSeg = kBlock * kRefineItems;        // draws per refine block
+constexpr uint32_t kScanTile = kBlock * kScanItems;   // 4096 particles
+
+}  // namespace bfpf

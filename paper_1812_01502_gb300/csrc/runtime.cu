@@ -17,6 +17,7 @@
 #include "bfpf.h"
 #include "bfpf_batch.cuh"
 #include "bfpf_device.cuh"
+#include "bfpf_global.cuh"
 #include "bfpf_kernels.h"
 
 #include <nvtx3/nvToolsExt.h>

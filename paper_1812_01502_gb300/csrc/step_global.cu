@@ -37,6 +37,7 @@
 
 #include "bfpf_device.cuh"
 #include "bfpf_epilogue.cuh"
+#include "bfpf_global.cuh"
 #include "bfpf_kernels.h"
 #include "bfpf_model.cuh"
 
