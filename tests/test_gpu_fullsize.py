@@ -60,7 +60,7 @@ def test_headline_over_the_full_horizon_against_the_grid_filter(bfpf):
 
 def test_lg8d_full_size_against_kalman(bfpf):
     """The 8-dimensional linear-Gaussian workload at full size (N = 2^20, T = 1000)
-    against the exact Kalman filter (measured: global resampling -0.4 in
+    against the exact Kalman filter (measured: global resampling -0.4 to -0.8 in
     log-likelihood, all stages per step -3.9 -- staged interaction has the larger
     estimator variance, and the log of an unbiased estimate sits about half its
     variance low; summed squared mean error about 4 for both).  The one-digit
