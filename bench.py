@@ -376,9 +376,9 @@ def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
     """Filter-mean MSE (Section 6.1: sum over steps and components, mean over runs)
     against the number of particles, for the butterfly (radix 16) and the global-
     resampling filter on the same observations, and the time per step of each.
-    Reference mean: average of two independent global runs at N = 2^25; the
-    reference's own error (half the squared spread of the two runs, halved again
-    for their average) is subtracted."""
+    Reference mean: average of R = 4 independent global runs at N = 2^25; the
+    reference's own error (the runs' squared spread / (R - 1), divided by R for
+    their average) is subtracted.  Four runs per N for both methods."""
     import numpy as np
     import torch
     import synthetic as S
@@ -401,9 +401,10 @@ def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
         g.close()
         return mean, ms
 
-    ref = [run(1 << 25, (1 << 25,), seed0 + 1 + j)[0] for j in range(2)]
-    ref_mean = 0.5 * (ref[0] + ref[1])
-    ref_mse = 0.25 * float(np.sum((ref[0] - ref[1]) ** 2))     # error of the averaged reference
+    R = 4
+    ref = [run(1 << 25, (1 << 25,), seed0 + 1 + j)[0] for j in range(R)]
+    ref_mean = sum(ref) / R
+    ref_mse = sum(float(np.sum((rk - ref_mean) ** 2)) for rk in ref) / (R - 1) / R   # error of the averaged reference
     out = {}
     for name, Ns, rad, kw in (("butterfly", [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24], _radix16, {}),
                               ("butterfly_all_stages", [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24], _radix16,
@@ -412,7 +413,7 @@ def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
                                lambda N: (N,), {})):
         mses, times = [], []
         for N in Ns:
-            J = 4 if N <= (1 << 20) else 2
+            J = 4
             errs, ts = [], []
             for j in range(J):
                 mean, ms = run(N, rad(N), seed0 + 100 * j + N % 97, **kw)
@@ -444,7 +445,7 @@ def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
     all_stages = {"N": aN[-1], "mse": target_a, "ms_per_step": at[-1], "mse_slope": float(fit_a[0]),
                   "global_ms_per_step_at_equal_mse": global_ms_at(target_a),
                   "speedup_at_equal_error": global_ms_at(target_a) / at[-1]}
-    return {"T": T, "reference": "mean of 2 global runs at N=2^25, their spread subtracted",
+    return {"T": T, "reference": "mean of 4 global runs at N=2^25, their spread subtracted", "runs_per_N": 4,
             "butterfly": out["butterfly"], "global": out["global"],
             "butterfly_all_stages": out["butterfly_all_stages"], "all_stages_at_equal_error": all_stages,
             "mse_slope": {"butterfly": float(fit_b[0]), "global": float(fit_g[0])},

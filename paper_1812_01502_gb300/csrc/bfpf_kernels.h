@@ -22,15 +22,15 @@ const void* select_sets_kernel(int d, int kind, bool wide);
 
 // Register-resident group kernel step_group_kernel<d, kind, a, G, staged>(StepParams,
 // GroupGeom) for a power-of-two radix a <= 32; sets *G (lanes per group).  nullptr if none.
-const void* select_group_kernel(int d, int kind, int a, int* G, bool staged, bool adapt = false);
-const void* group_kernel_d1(int kind, int a, int* G, bool staged, bool adapt);
-const void* group_kernel_d2(int kind, int a, int* G, bool staged, bool adapt);
-const void* group_kernel_d3(int kind, int a, int* G, bool staged, bool adapt);
-const void* group_kernel_d4(int kind, int a, int* G, bool staged, bool adapt);
-const void* group_kernel_d5(int kind, int a, int* G, bool staged, bool adapt);
-const void* group_kernel_d6(int kind, int a, int* G, bool staged, bool adapt);
-const void* group_kernel_d7(int kind, int a, int* G, bool staged, bool adapt);
-const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt);
+const void* select_group_kernel(int d, int kind, int a, int* G, bool staged, bool adapt = false, bool small = false);
+const void* group_kernel_d1(int kind, int a, int* G, bool staged, bool adapt, bool small);
+const void* group_kernel_d2(int kind, int a, int* G, bool staged, bool adapt, bool small);
+const void* group_kernel_d3(int kind, int a, int* G, bool staged, bool adapt, bool small);
+const void* group_kernel_d4(int kind, int a, int* G, bool staged, bool adapt, bool small);
+const void* group_kernel_d5(int kind, int a, int* G, bool staged, bool adapt, bool small);
+const void* group_kernel_d6(int kind, int a, int* G, bool staged, bool adapt, bool small);
+const void* group_kernel_d7(int kind, int a, int* G, bool staged, bool adapt, bool small);
+const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt, bool small);
 
 // Global-resampling comparator (radices = {N}, N > 1024): three kernels per step,
 // each taking (StepParams, GlobalParams).

@@ -467,6 +467,7 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     if (!select_adaptive_kernels(d, pl.kind, pl.wide, pl.ak)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
   }
   const bool staged = pl.sps > 1;
+  constexpr uint32_t kSmallBatches = 128;
   // Register-resident group kernel: every radix a power of two, a_k <= 32, and the
   // groups of digit k fill whole thread-block iterations.
   bool pow2 = true;
@@ -481,8 +482,19 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
                          ? select_group_kernel(pl.d, pl.kind, (int)g.a, &G, staged, adapt_group)
                          : nullptr;
     if (gk && G > 0) {
-      const uint32_t gpb = kBlock / G;
+      uint32_t gpb = kBlock / G;
       const uint32_t ngroups = pl.N / g.a;
+      // A population whose groups fill fewer than kSmallBatches thread-block
+      // iterations takes the two-members-per-lane split: more blocks, shorter chains.
+      if (!adapt_group && ngroups % gpb == 0 && ngroups / gpb < kSmallBatches) {
+        int Gs = 0;
+        const void* gks = select_group_kernel(pl.d, pl.kind, (int)g.a, &Gs, staged, false, true);
+        if (gks && Gs > 0 && ngroups % (kBlock / Gs) == 0) {
+          gk = gks;
+          G = Gs;
+          gpb = kBlock / G;
+        }
+      }
       if (ngroups % gpb == 0) {
         dp.kernel = gk;
         dp.group = true;

@@ -108,16 +108,16 @@ bool select_kernels(int d, int kind, bool wide, KernelSet& ks) {
 #undef BFPF_CASE
 }
 
-const void* select_group_kernel(int d, int kind, int a, int* G, bool staged, bool adapt) {
+const void* select_group_kernel(int d, int kind, int a, int* G, bool staged, bool adapt, bool small) {
   switch (d) {
-    case 1: return group_kernel_d1(kind, a, G, staged, adapt);
-    case 2: return group_kernel_d2(kind, a, G, staged, adapt);
-    case 3: return group_kernel_d3(kind, a, G, staged, adapt);
-    case 4: return group_kernel_d4(kind, a, G, staged, adapt);
-    case 5: return group_kernel_d5(kind, a, G, staged, adapt);
-    case 6: return group_kernel_d6(kind, a, G, staged, adapt);
-    case 7: return group_kernel_d7(kind, a, G, staged, adapt);
-    case 8: return group_kernel_d8(kind, a, G, staged, adapt);
+    case 1: return group_kernel_d1(kind, a, G, staged, adapt, small);
+    case 2: return group_kernel_d2(kind, a, G, staged, adapt, small);
+    case 3: return group_kernel_d3(kind, a, G, staged, adapt, small);
+    case 4: return group_kernel_d4(kind, a, G, staged, adapt, small);
+    case 5: return group_kernel_d5(kind, a, G, staged, adapt, small);
+    case 6: return group_kernel_d6(kind, a, G, staged, adapt, small);
+    case 7: return group_kernel_d7(kind, a, G, staged, adapt, small);
+    case 8: return group_kernel_d8(kind, a, G, staged, adapt, small);
     default: return nullptr;
   }
 }

@@ -363,31 +363,39 @@ constexpr int group_members_per_lane(int A, int D) {
   return m;
 }
 
-template <int D, int KIND, int A, bool STAGED, bool ADAPT>
+// SMALL: at most two members per lane, for populations too small to fill the
+// GPU with the default split (shorter per-thread chains, more thread blocks).
+template <int D, int KIND, int A, bool STAGED, bool ADAPT, bool SMALL>
 inline const void* group_kernel_pick(int& G) {
-  constexpr int M = group_members_per_lane(A, D);
+  constexpr int MD = group_members_per_lane(A, D);
+  constexpr int M = (SMALL && MD > 2) ? 2 : MD;
   constexpr int GG = A / M;
   G = GG;
   return reinterpret_cast<const void*>(&step_group_kernel<D, KIND, A, GG, STAGED, ADAPT>);
 }
 
-template <int D, int KIND, bool STAGED, bool ADAPT>
+template <int D, int KIND, bool STAGED, bool ADAPT, bool SMALL>
 inline const void* group_kernel_for_s(int a, int& G) {
   switch (a) {
-    case 2: return group_kernel_pick<D, KIND, 2, STAGED, ADAPT>(G);
-    case 4: return group_kernel_pick<D, KIND, 4, STAGED, ADAPT>(G);
-    case 8: return group_kernel_pick<D, KIND, 8, STAGED, ADAPT>(G);
-    case 16: return group_kernel_pick<D, KIND, 16, STAGED, ADAPT>(G);
-    case 32: return group_kernel_pick<D, KIND, 32, STAGED, ADAPT>(G);
+    case 2: return group_kernel_pick<D, KIND, 2, STAGED, ADAPT, SMALL>(G);
+    case 4: return group_kernel_pick<D, KIND, 4, STAGED, ADAPT, SMALL>(G);
+    case 8: return group_kernel_pick<D, KIND, 8, STAGED, ADAPT, SMALL>(G);
+    case 16: return group_kernel_pick<D, KIND, 16, STAGED, ADAPT, SMALL>(G);
+    case 32: return group_kernel_pick<D, KIND, 32, STAGED, ADAPT, SMALL>(G);
     default: return nullptr;
   }
 }
 
-// staged: all stages per step; adapt: the fully adapted schedule (no rotation)
+// staged: all stages per step; adapt: the fully adapted schedule (no rotation);
+// small: the two-members-per-lane split (not for the adapted schedule)
 template <int D, int KIND>
-inline const void* group_kernel_for(int a, int& G, bool staged, bool adapt) {
-  if (adapt) return group_kernel_for_s<D, KIND, false, true>(a, G);
-  return staged ? group_kernel_for_s<D, KIND, true, false>(a, G) : group_kernel_for_s<D, KIND, false, false>(a, G);
+inline const void* group_kernel_for(int a, int& G, bool staged, bool adapt, bool small) {
+  if (adapt) return group_kernel_for_s<D, KIND, false, true, false>(a, G);
+  if (small)
+    return staged ? group_kernel_for_s<D, KIND, true, false, true>(a, G)
+                  : group_kernel_for_s<D, KIND, false, false, true>(a, G);
+  return staged ? group_kernel_for_s<D, KIND, true, false, false>(a, G)
+                : group_kernel_for_s<D, KIND, false, false, false>(a, G);
 }
 
 }  // namespace bfpf

@@ -4,10 +4,10 @@
 
 namespace bfpf {
 
-const void* group_kernel_d1(int kind, int a, int* G, bool staged, bool adapt) {
-  if (kind == kStochVol) return group_kernel_for<1, kStochVol>(a, *G, staged, adapt);
+const void* group_kernel_d1(int kind, int a, int* G, bool staged, bool adapt, bool small) {
+  if (kind == kStochVol) return group_kernel_for<1, kStochVol>(a, *G, staged, adapt, small);
   if (kind != kLinearGaussian) return nullptr;
-  return group_kernel_for<1, kLinearGaussian>(a, *G, staged, adapt);
+  return group_kernel_for<1, kLinearGaussian>(a, *G, staged, adapt, small);
 }
 
 }  // namespace bfpf

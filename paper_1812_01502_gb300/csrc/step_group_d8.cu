@@ -4,10 +4,10 @@
 
 namespace bfpf {
 
-const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt) {
+const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt, bool small) {
 
   if (kind != kLinearGaussian) return nullptr;
-  return group_kernel_for<8, kLinearGaussian>(a, *G, staged, adapt);
+  return group_kernel_for<8, kLinearGaussian>(a, *G, staged, adapt, small);
 }
 
 }  // namespace bfpf

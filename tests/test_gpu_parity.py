@@ -86,12 +86,37 @@ def test_lockstep_sv_group_kernel(bfpf):
     radices = (16, 16, 16, 4)
     y = S.simulate(model, 6, seed=23)[1]
     f = _filter(bfpf, model, radices, 7)
-    assert all(dg["kernel"] == "group" for dg in f.describe()["digits"])
+    digits = f.describe()["digits"]
+    assert all(dg["kernel"] == "group" for dg in digits)
+    # 16384 particles fill few thread blocks: two members per lane (8 lanes per radix-16 group)
+    assert [dg["lanes"] for dg in digits] == [8, 8, 8, 2]
     rep = LS.Report()
     for n in range(len(y)):
         rep.merge(LS.check_step_full(f, model, radices, 7, y[n], n))
     f.close()
     print("sv group", dict(rep))
+
+
+@pytest.mark.parametrize("all_stages", [False, True])
+def test_lockstep_sv_group_kernel_default_split(bfpf, all_stages):
+    """2^20 particles: the default split (a whole radix-16 group in one lane), every
+    step checked in full against the oracle."""
+    model = S.sv_model()
+    radices = (16,) * 5
+    y = S.simulate(model, 5 if not all_stages else 2, seed=29)[1]
+    N = int(np.prod(radices))
+    f = (bfpf.ButterflyFilter(model, N, radices, 17, all_stages=True) if all_stages
+         else _filter(bfpf, model, radices, 17))
+    digits = f.describe()["digits"]
+    assert all(dg["kernel"] == "group" and dg["lanes"] == 1 for dg in digits)
+    rep = LS.Report()
+    for n in range(len(y)):
+        if all_stages:
+            rep.merge(LS.check_step_all_stages(f, model, radices, 17, y[n], n))
+        else:
+            rep.merge(LS.check_step_full(f, model, radices, 17, y[n], n))
+    f.close()
+    print("sv group default split", all_stages, dict(rep))
 
 
 @pytest.mark.parametrize("d,N,T", [(1, 4096, 5), (1, 1 << 16, 3), (4, 5000, 3), (8, 1 << 14, 2), (0, 1 << 15, 4)])
