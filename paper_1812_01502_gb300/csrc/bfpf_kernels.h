@@ -32,8 +32,9 @@ const void* group_kernel_d6(int kind, int a, int* G, bool staged, bool adapt, bo
 const void* group_kernel_d7(int kind, int a, int* G, bool staged, bool adapt, bool small);
 const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt, bool small);
 
-// Global-resampling comparator (radices = {N}, N > 1024): three kernels per step,
-// each taking (StepParams, GlobalParams).
+// Global-resampling comparator (radices = {N}, N > 1024): six kernels per step,
+// launched in the order weight, refine, scan, bounds, resolve, advance, each
+// taking (StepParams, GlobalParams).
 struct GlobalKernels {
   const void* weight;
   const void* scan;
