@@ -61,9 +61,9 @@ __device__ __forceinline__ uint32_t bucket_of(unsigned long long r, uint32_t log
   return log2b ? (uint32_t)(r >> (64u - log2b)) : 0u;
 }
 
-// A filed draw: {i, payload (unused, 0), low and high words of r_i}.
-__device__ __forceinline__ uint4 draw_entry(uint32_t i, uint32_t payload, unsigned long long r) {
-  return make_uint4(i, payload, (uint32_t)r, (uint32_t)(r >> 32));
+// A filed draw: one 16-byte entry {i, 0, low and high words of r_i}.
+__device__ __forceinline__ uint4 draw_entry(uint32_t i, unsigned long long r) {
+  return make_uint4(i, 0u, (uint32_t)r, (uint32_t)(r >> 32));
 }
 __device__ __forceinline__ unsigned long long entry_r(uint4 e) {
   return ((unsigned long long)e.w << 32) | e.z;
@@ -78,19 +78,20 @@ __device__ __forceinline__ void file_direct(const GlobalParams& gp, uint4 e) {
   else gp.ovf[atomicAdd(gp.cnt + gp.buckets, 1u)] = e;
 }
 
-// File one block's chunk of draws (thread t holds V of them: index i, payload,
-// uniform r, bin = bin_of(r), valid) into nbins bins of capacity cap: dst[bin * cap + pos], pos
-// reserved from gcnt[bin]; a draw whose bin is full goes to ovf[*ovf_cnt++].
+// File one block's chunk of draws (thread t holds V of them: index i, uniform
+// r, bin = bin_of(r), valid) into nbins bins of capacity cap: dst[bin * cap +
+// pos], pos reserved from gcnt[bin]; a draw whose bin is full goes to
+// ovf[*ovf_cnt++].
 // The chunk is counted per bin in shared memory, each non-empty bin reserves
 // its run with one global atomic, and the draws are ordered by bin in shared
 // memory first so that consecutive threads write consecutive slots.
 // Shared memory: s_cnt[nbins], s_off[nbins], s_buf[kBlock * V].
 template <int V, class BinOf>
-__device__ __forceinline__ void file_chunk(const uint32_t (&i)[V], const uint32_t (&pay)[V],
-                                           const unsigned long long (&r)[V], const uint32_t (&bin)[V],
-                                           const bool (&valid)[V], BinOf bin_of, uint32_t nbins, uint32_t* gcnt,
-                                           uint4* dst, uint32_t cap, uint32_t* ovf_cnt, uint4* ovf, uint32_t* s_cnt,
-                                           uint32_t* s_off, uint4* s_buf) {
+__device__ __forceinline__ void file_chunk(const uint32_t (&i)[V], const unsigned long long (&r)[V],
+                                           const uint32_t (&bin)[V], const bool (&valid)[V], BinOf bin_of,
+                                           uint32_t nbins, uint32_t* gcnt, uint4* dst, uint32_t cap,
+                                           uint32_t* ovf_cnt, uint4* ovf, uint32_t* s_cnt, uint32_t* s_off,
+                                           uint4* s_buf) {
   constexpr int NW = kBlock / 32;
   __shared__ uint32_t s_wsum[NW];
   __shared__ uint32_t s_total;
@@ -136,7 +137,7 @@ __device__ __forceinline__ void file_chunk(const uint32_t (&i)[V], const uint32_
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < V; ++j)
-    if (valid[j]) s_buf[s_off[bin[j]] + rank[j]] = draw_entry(i[j], pay[j], r[j]);
+    if (valid[j]) s_buf[s_off[bin[j]] + rank[j]] = draw_entry(i[j], r[j]);
   __syncthreads();
   const uint32_t total = s_total;
   for (uint32_t k = tid; k < total; k += kBlock) {
@@ -231,11 +232,9 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
       }
     }
     // uniforms (pairs of particles share a Philox block) and their coarse bins
-    uint32_t ii[V], cb[V], pay[V];
+    uint32_t ii[V], cb[V];
     unsigned long long r[V];
     bool valid[V];
-#pragma unroll
-    for (int j = 0; j < V; ++j) pay[j] = 0;
 #pragma unroll
     for (int h = 0; h < V / 2; ++h) {
       const uint4 w = philox4x32_10(make_uint4(i0 / 2u + h, n, kPurposeResampleWide, 0), p.rk);
@@ -248,7 +247,7 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
       cb[j] = bucket_of(r[j], cbits);
       valid[j] = i0 + j < N;
     }
-    file_chunk<V>(ii, pay, r, cb, valid, [cbits](unsigned long long rr) { return bucket_of(rr, cbits); }, nbins,
+    file_chunk<V>(ii, r, cb, valid, [cbits](unsigned long long rr) { return bucket_of(rr, cbits); }, nbins,
                   gp.ccnt, gp.cslot, gp.ccap, gp.ccnt + nbins, gp.covf, s_cnt, s_off, s_buf);
   }
   const Sched sc{n, n, 0u, true, true};   // one digit (m = 1): every step is one whole stage
@@ -271,7 +270,7 @@ __global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_cons
   const uint32_t e0 = sg * kRefineSeg;
   if (e0 < cfill) {                                // block-uniform
     const size_t cbase = (size_t)cb * gp.ccap;
-    uint32_t ii[kRefineItems], pay[kRefineItems], fb[kRefineItems];
+    uint32_t ii[kRefineItems], fb[kRefineItems];
     unsigned long long rr[kRefineItems];
     bool valid[kRefineItems];
 #pragma unroll
@@ -280,13 +279,12 @@ __global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_cons
       valid[q] = e < cfill;
       const uint4 en = valid[q] ? __ldcs(gp.cslot + cbase + e) : make_uint4(0, 0, 0, 0);
       ii[q] = en.x;
-      pay[q] = en.y;
       rr[q] = entry_r(en);
       fb[q] = bucket_of(rr[q], gp.log2b) & (nfine - 1u);
     }
     const size_t b0 = (size_t)cb << fbits;         // this coarse bin's first bucket
     const uint32_t log2b = gp.log2b, fmask = nfine - 1u;
-    file_chunk<kRefineItems>(ii, pay, rr, fb, valid,
+    file_chunk<kRefineItems>(ii, rr, fb, valid,
                              [log2b, fmask](unsigned long long r) { return bucket_of(r, log2b) & fmask; }, nfine,
                              gp.cnt + b0, gp.slot + b0 * gp.cap, gp.cap, gp.cnt + gp.buckets, gp.ovf, s_cnt, s_off,
                              s_buf);
