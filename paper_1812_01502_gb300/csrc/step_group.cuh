@@ -40,8 +40,7 @@ namespace bfpf {
 // threshold (the last launch then only mutates), per-particle carried weights
 // in and out, and the ESS of the new stage weights decides the next stage.
 template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
-__global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constant__ StepParams p,
-                                                           const __grid_constant__ GroupGeom gg) {
+__device__ __forceinline__ void step_group_body(const StepParams& p, const GroupGeom& gg) {
   static_assert(A >= 2 && A <= 32 && (A & (A - 1)) == 0, "radix must be a power of two <= 32");
   static_assert(G >= 1 && G <= A && A % G == 0, "bad lanes per group");
   constexpr int M = A / G;                 // members per lane
@@ -356,6 +355,23 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
   }
 }
 
+template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
+__global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constant__ StepParams p,
+                                                           const __grid_constant__ GroupGeom gg) {
+  step_group_body<D, KIND, A, G, STAGED, ADAPT>(p, gg);
+}
+
+// The same for d >= 5 and one stage per launch, with at most 85 registers so
+// that three blocks share an SM (a few bytes of spills; with two blocks per SM
+// the 8-D step was short of warps to hide its latencies).  The staged
+// instantiations keep the unbounded build: bounded, they spill hundreds of
+// bytes per thread.
+template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
+__global__ void __launch_bounds__(kBlock, 3) step_group_kernel_d5(const __grid_constant__ StepParams p,
+                                                                  const __grid_constant__ GroupGeom gg) {
+  step_group_body<D, KIND, A, G, STAGED, ADAPT>(p, gg);
+}
+
 // Lanes per group: each lane keeps M = A / G members, M * D <= 16 state values.
 constexpr int group_members_per_lane(int A, int D) {
   int m = 1;
@@ -371,6 +387,8 @@ inline const void* group_kernel_pick(int& G) {
   constexpr int M = (SMALL && MD > 2) ? 2 : MD;
   constexpr int GG = A / M;
   G = GG;
+  if constexpr (D >= 5 && !STAGED)
+    return reinterpret_cast<const void*>(&step_group_kernel_d5<D, KIND, A, GG, STAGED, ADAPT>);
   return reinterpret_cast<const void*>(&step_group_kernel<D, KIND, A, GG, STAGED, ADAPT>);
 }
 
