@@ -63,3 +63,17 @@ def test_null_arguments(bfpf):
     assert lib.pf_destroy(None) == bfpf.PF_OK
     assert lib.pf_loglik(None, None) == bfpf.PF_EINVAL
     assert lib.pf_step(None, None, None, None, None) == bfpf.PF_EINVAL
+
+
+def test_binding_flags_match_the_header(bfpf):
+    """Every PF_* flag and status code the header defines has the same value in the binding."""
+    text = open(HEADER).read()
+    defines = {name: int(val.rstrip("uU"), 0)
+               for name, val in re.findall(r"#define\s+(PF_[A-Z0-9_]+)\s+(0x[0-9a-fA-F]+u?|\d+u?)\b", text)}
+    assert "PF_ALL_STAGES" in defines and "PF_TEST_SMALL_BUCKETS" in defines
+    for name, val in defines.items():
+        if hasattr(bfpf, name):
+            assert getattr(bfpf, name) == val, name
+    for name in ("PF_RECORD_ANCESTORS", "PF_ALL_STAGES", "PF_ADAPTIVE", "PF_ROTATE", "PF_ISLANDS",
+                 "PF_ISLANDS_PLAIN", "PF_DIGIT_SETS", "PF_TEST_SCAN_TIMEOUT", "PF_TEST_SMALL_BUCKETS"):
+        assert getattr(bfpf, name) == defines[name], name
