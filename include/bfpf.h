@@ -339,8 +339,9 @@ const char* pf_batch_last_error(const pf_batch* b);
  * The step's temporary data (the device state block, per-block partial sums
  * and the per-step outputs) lives in a fixed scratch area compiled into the
  * library: 192 KiB of device memory per GPU that loads the library, held until
- * the process exits.  The step runs at most 2048 thread blocks; pf_step_noalloc
- * caps its grid there, so N and d stay limited only as for pf_create.
+ * the process exits.  The step runs at most 2048 thread blocks (the grid is
+ * capped there; a larger problem only takes more iterations per block), so N
+ * and d stay limited only as for pf_create.
  *
  * Arguments: model, N, radices, m, seed as for pf_create; n = index of this
  * time step (digit n mod m interacts; it keys the random draws); mu = carried
@@ -350,7 +351,12 @@ const char* pf_batch_last_error(const pf_batch* b);
  * floats, all zero at n = 0) the carried log stage weights; lV_out
  * (N / a_{n mod m} floats) receives the new ones.  y_n: dy floats, host.
  * Host outputs: out[3] = { log-likelihood increment, mu for step n + 1, ESS };
- * mean_out (d floats, may be NULL) = the filtering mean.  Synchronises `stream`.
+ * mean_out (d floats, may be NULL) = the filtering mean; status_out (1 uint32,
+ * may be NULL) = this step's status bits as pf_get_status reports them (bit 0:
+ * a non-finite log-weight was treated as weight zero; bit 1: a group had zero
+ * total weight and kept its particles).  Synchronises `stream`, which must
+ * belong to the current device (NULL = the legacy default stream of the
+ * current device; another device's stream: PF_EINVAL).
  *
  * The first call on a device resolves the scratch area's device address
  * (cudaGetSymbolAddress) with that device current, so make that first call
@@ -363,7 +369,7 @@ const char* pf_batch_last_error(const pf_batch* b);
 pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int32_t* radices, int32_t m,
                           uint64_t seed, uint32_t n, double mu, float* x, const float* lV_in,
                           float* lV_out, const float* y_n, double* out, float* mean_out,
-                          void* stream);
+                          uint32_t* status_out, void* stream);
 
 #ifdef __cplusplus
 }

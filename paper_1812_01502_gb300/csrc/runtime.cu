@@ -1263,8 +1263,16 @@ __global__ void noalloc_start_kernel(DevState* st, float* y_ring, NoAllocStart s
 extern "C" pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int32_t* radices, int32_t m,
                                      uint64_t seed, uint32_t n, double mu, float* x, const float* lV_in,
                                      float* lV_out, const float* y_n, double* out, float* mean_out,
-                                     void* stream) {
+                                     uint32_t* status_out, void* stream) {
   if (!x || !lV_in || !lV_out || !y_n || !out) return fail(nullptr, PF_EINVAL, "NULL argument");
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  if (st) {   // the scratch address and the launch plan belong to the current device
+    int cur = 0, sdev = 0;
+    cudaError_t e0 = cudaGetDevice(&cur);
+    if (e0 == cudaSuccess) e0 = cudaStreamGetDevice(st, &sdev);
+    if (e0 != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("stream device: ") + cudaGetErrorString(e0));
+    if (sdev != cur) return fail(nullptr, PF_EINVAL, "the stream belongs to another device than the current one");
+  }
   Plan pl;
   std::string msg;
   pf_status s = make_plan(model, N, radices, m, nullptr, pl, msg);
@@ -1274,12 +1282,9 @@ extern "C" pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int
   }
   if (s == PF_OK) s = finish_plan(pl, nullptr, msg);
   if (s != PF_OK) return fail(nullptr, s, msg);
-  if (pl.max_grid > kNoAllocMaxBlocks)
-    return fail(nullptr, PF_EINVAL, "this device would run more than 2048 thread blocks, the scratch area's limit");
   unsigned char* scratch = nullptr;
   cudaError_t e = noalloc_scratch(&scratch);
   if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
 
   StepParams P{};
   P.rk = make_round_keys(seed);
@@ -1312,12 +1317,16 @@ extern "C" pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int
   e = cudaGetLastError();
   if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("start kernel: ") + cudaGetErrorString(e));
   DigitPlan& dp = pl.dp[n % (uint32_t)pl.m];
+  // The scratch area holds the partial sums of at most kNoAllocMaxBlocks blocks.
+  // The step kernels stride over their units by gridDim and the fold of the
+  // partials runs over gridDim, so a smaller grid only takes more iterations.
+  const int grid = std::min(dp.grid, kNoAllocMaxBlocks);
   if (dp.group) {
     void* args[] = {&P, &dp.gg};
-    e = cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, 0, st);
+    e = cudaLaunchKernel(dp.kernel, dim3(grid), dim3(kBlock), args, 0, st);
   } else {
     void* args[] = {&P};
-    e = cudaLaunchKernel(dp.kernel, dim3(dp.grid), dim3(kBlock), args, dp.smem, st);
+    e = cudaLaunchKernel(dp.kernel, dim3(grid), dim3(kBlock), args, dp.smem, st);
   }
   if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("step kernel: ") + cudaGetErrorString(e));
   const uint32_t slot = n % kRing;
@@ -1332,6 +1341,7 @@ extern "C" pf_status pf_step_noalloc(const pf_model* model, int64_t N, const int
   if (e != cudaSuccess) return fail(nullptr, PF_ECUDA, std::string("copy back: ") + cudaGetErrorString(e));
   out[1] = dst.mu;
   out[2] = (double)ess;
+  if (status_out) *status_out = dst.status;
   return PF_OK;
 }
 
