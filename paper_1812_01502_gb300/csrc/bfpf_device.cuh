@@ -103,15 +103,47 @@ __device__ __forceinline__ void normals4(uint4 w, float z[4]) {
   box_muller(w.z, w.w, z[2], z[3]);
 }
 
+// Special-function-unit approximations with flush-to-zero.  The arguments
+// the kernels pass are never subnormal (uniforms >= 2^-24, radii^2 >= 2^-23,
+// angles and weight exponents of normal size or zero), and there the .ftz
+// forms return the same values as the plain forms without their subnormal
+// scaling steps.
+__device__ __forceinline__ float lg2_ftz(float x) {
+  float r;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float ex2_ftz(float x) {
+  float r;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float rsqrt_ftz(float x) {
+  float r;
+  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float sin_ftz(float x) {
+  float r;
+  asm("sin.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ float cos_ftz(float x) {
+  float r;
+  asm("cos.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+
 // The same transform on the special-function units: -2 ln u from lg2.approx
 // (absolute error about 2^-22 in log2 u), except for u > 63/64 where
 // -ln u = t + t^2/2 + ... + t^6/6 with t = 1 - u (exact in FP32; truncation
 // below 4e-13 relative) keeps the small radii accurate; the angle is taken in
 // [-pi, pi) where sin/cos.approx have absolute error about 2^-21:
 // cos(2 pi v) = -cos(2 pi (v - 1/2)).  Normals differ from the full-precision
-// transform by < 4e-6 absolute.
+// transform by < 4e-6 absolute.  u = (2 floor(w0 / 2^9) + 1) 2^-24 is built
+// from its bits: 1 + floor(w0 / 2^9) 2^-23 minus (1 - 2^-24), exact in FP32.
 __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float& z0, float& z1) {
-  const float u = __uint2float_rn(((wa >> 9) << 1) | 1u) * 0x1p-24f;
+  const float u = __uint_as_float((wa >> 9) | 0x3f800000u) - 0.99999994039535522f;
   const float v = __uint2float_rn(wb >> 8) * 0x1p-24f;
   float r2;
   if (u > 0.984375f) {
@@ -119,13 +151,12 @@ __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float&
     const float poly = fmaf(fmaf(fmaf(fmaf(fmaf(t, 1.0f / 6.0f, 0.2f), t, 0.25f), t, 1.0f / 3.0f), t, 0.5f), t, 1.0f);
     r2 = 2.0f * t * poly;
   } else {
-    r2 = -1.3862943611198906f * __log2f(u);   // -2 ln 2 log2 u
+    r2 = -1.3862943611198906f * lg2_ftz(u);   // -2 ln 2 log2 u
   }
-  const float rad = r2 * rsqrtf(r2);
-  float s, c;
-  __sincosf(6.283185307179586f * (v - 0.5f), &s, &c);
-  z0 = -rad * c;
-  z1 = -rad * s;
+  const float rad = r2 * rsqrt_ftz(r2);
+  const float ang = 6.283185307179586f * (v - 0.5f);
+  z0 = -rad * cos_ftz(ang);
+  z1 = -rad * sin_ftz(ang);
 }
 
 __device__ __forceinline__ void normals4_fast(uint4 w, float z[4]) {
@@ -137,9 +168,7 @@ __device__ __forceinline__ void normals4_fast(uint4 w, float z[4]) {
 // x log2(e).  The PTX ISA specifies ex2.approx(+-0) = +1, and 0 * log2(e) is
 // exactly 0, so the group maximum always weighs exactly 1 (q = 2^B).
 __device__ __forceinline__ float exp_weight(float x) {
-  float r;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x * 1.4426950408889634f));
-  return r;
+  return ex2_ftz(x * 1.4426950408889634f);
 }
 
 // ---------------------------------------------------------------------------

@@ -55,9 +55,28 @@ __device__ __forceinline__ void shfl_merge(Partial& acc, float* accx, int off) {
   merge_partial<D>(acc, accx, o.m, o.s1, o.s2, ox);
 }
 
+// Floats as order-preserving signed integers (for redux.sync max): a
+// non-negative float keeps its bits, a negative one flips its magnitude bits.
+__device__ __forceinline__ int float_order(float f) {
+  const int i = __float_as_int(f);
+  return i >= 0 ? i : (i ^ 0x7fffffff);
+}
+__device__ __forceinline__ float order_float(int i) { return __int_as_float(i >= 0 ? i : (i ^ 0x7fffffff)); }
+
+// Natural log of a positive double x to about 1e-7 absolute: the exponent part
+// exactly in FP64, log of the mantissa in [1, 2) by logf.
+__device__ __forceinline__ double log_split(double x) {
+  const long long b = __double_as_longlong(x);
+  const int e = (int)((b >> 52) & 0x7ff) - 1023;
+  const double m = __longlong_as_double((b & 0x000fffffffffffffLL) | 0x3ff0000000000000LL);
+  return (double)e * 0.6931471805599453 + (double)logf((float)m);
+}
+
 // Grid-wide fold of the per-thread partials, called by every thread of every
-// block exactly once.  Each block writes its partial; the last block to
-// arrive (last-block-done) folds all block partials in a fixed order with
+// block exactly once.  Each block takes the largest of its threads' maxima
+// (redux.sync), rescales every thread's sums to it (one exp per thread), sums
+// them by shuffles and writes the block partial; the last block to arrive
+// (last-block-done) folds all block partials in a fixed order with
 // compensated FP32 sums.  Returns true in thread 0 of the last block only,
 // with S[0] = sum e^{lw - Mx}, S[1] = sum e^{2(lw - Mx)}, S[2 + t] = sum
 // e^{lw - Mx} x_t (FP64) and Mx the global maximum.
@@ -66,6 +85,8 @@ __device__ __forceinline__ bool fold_partials(const StepParams& p, Partial acc, 
                                               double* S, float& Mx_out) {
   constexpr int NP = 3 + D;
   constexpr int NW = kBlock / 32;
+  constexpr unsigned FULL = 0xffffffffu;
+  __shared__ int s_max[NW];
   __shared__ float s_red[NW][NP];
   __shared__ float s_redlo[NW][NP];
   __shared__ uint32_t s_last;
@@ -73,28 +94,40 @@ __device__ __forceinline__ bool fold_partials(const StepParams& p, Partial acc, 
   const uint32_t tid = threadIdx.x;
   if (status) atomicOr(&st->status, status);
   const uint32_t lane = tid & 31u, warp = tid >> 5;
+
+  // ---- block partial: max, then rescaled sums ----
+  int mi = __reduce_max_sync(FULL, float_order(acc.m));
+  if (lane == 0) s_max[warp] = mi;
+  __syncthreads();
+  mi = s_max[0];
 #pragma unroll
-  for (int off = 16; off; off >>= 1) shfl_merge<D>(acc, accx, off);
+  for (int w = 1; w < NW; ++w) mi = max(mi, s_max[w]);
+  const float bm = order_float(mi);
+  const float sc = (acc.m == -INFINITY) ? 0.0f : expf(acc.m - bm);
+  float v[NP - 1];
+  v[0] = acc.s1 * sc;
+  v[1] = acc.s2 * (sc * sc);
+#pragma unroll
+  for (int t = 0; t < D; ++t) v[2 + t] = accx[t] * sc;
+#pragma unroll
+  for (int off = 16; off; off >>= 1) {
+#pragma unroll
+    for (int k = 0; k < NP - 1; ++k) v[k] += __shfl_xor_sync(FULL, v[k], off);
+  }
   if (lane == 0) {
-    s_red[warp][0] = acc.m;
-    s_red[warp][1] = acc.s1;
-    s_red[warp][2] = acc.s2;
 #pragma unroll
-    for (int t = 0; t < D; ++t) s_red[warp][3 + t] = accx[t];
+    for (int k = 0; k < NP - 1; ++k) s_red[warp][k] = v[k];
   }
   __syncthreads();
   if (tid == 0) {
-    Partial b{-INFINITY, 0.0f, 0.0f};
-    float bx[D];
-#pragma unroll
-    for (int t = 0; t < D; ++t) bx[t] = 0.0f;
-    for (int w = 0; w < NW; ++w) merge_partial<D>(b, bx, s_red[w][0], s_red[w][1], s_red[w][2], &s_red[w][3]);
     float* out = p.partials + (size_t)blockIdx.x * NP;
-    out[0] = b.m;
-    out[1] = b.s1;
-    out[2] = b.s2;
+    out[0] = bm;
 #pragma unroll
-    for (int t = 0; t < D; ++t) out[3 + t] = bx[t];
+    for (int k = 0; k < NP - 1; ++k) {
+      float a = s_red[0][k];
+      for (int w = 1; w < NW; ++w) a += s_red[w][k];
+      out[1 + k] = a;
+    }
     __threadfence();
     const uint32_t prev = atomicAdd(&st->done, 1u);
     s_last = (prev == gridDim.x - 1) ? 1u : 0u;
@@ -103,22 +136,22 @@ __device__ __forceinline__ bool fold_partials(const StepParams& p, Partial acc, 
   if (!s_last) return false;
   __threadfence();
 
-  // Last block: fold all block partials (fixed order, compensated FP32), finish in FP64.
+  // ---- last block: fold all block partials (fixed order, compensated FP32) ----
   const uint32_t G = gridDim.x;
-  float Mx = -INFINITY;
-  for (uint32_t b = tid; b < G; b += kBlock) Mx = fmaxf(Mx, __ldcg(p.partials + (size_t)b * NP));
+  int gi = float_order(-INFINITY);
+  for (uint32_t b = tid; b < G; b += kBlock) gi = max(gi, float_order(__ldcg(p.partials + (size_t)b * NP)));
+  gi = __reduce_max_sync(FULL, gi);
+  __syncthreads();
+  if (lane == 0) s_max[warp] = gi;
+  __syncthreads();
+  gi = s_max[0];
 #pragma unroll
-  for (int off = 16; off; off >>= 1) Mx = fmaxf(Mx, __shfl_xor_sync(0xffffffffu, Mx, off));
-  __syncthreads();
-  if (lane == 0) s_red[warp][0] = Mx;
-  __syncthreads();
-  Mx = s_red[0][0];
-  for (int w = 1; w < NW; ++w) Mx = fmaxf(Mx, s_red[w][0]);
-  __syncthreads();
+  for (int w = 1; w < NW; ++w) gi = max(gi, s_max[w]);
+  const float Mx = order_float(gi);
 
   float hi[NP - 1], lo[NP - 1];
 #pragma unroll
-  for (int v = 0; v < NP - 1; ++v) hi[v] = lo[v] = 0.0f;
+  for (int k = 0; k < NP - 1; ++k) hi[k] = lo[k] = 0.0f;
   if (Mx != -INFINITY) {
     for (uint32_t b = tid; b < G; b += kBlock) {
       const float* pb = p.partials + (size_t)b * NP;
@@ -134,29 +167,30 @@ __device__ __forceinline__ bool fold_partials(const StepParams& p, Partial acc, 
 #pragma unroll
   for (int off = 16; off; off >>= 1) {
 #pragma unroll
-    for (int v = 0; v < NP - 1; ++v) {
-      const float oh = __shfl_down_sync(0xffffffffu, hi[v], off);
-      const float ol = __shfl_down_sync(0xffffffffu, lo[v], off);
-      ff_add(hi[v], lo[v], oh);
-      lo[v] += ol;
+    for (int k = 0; k < NP - 1; ++k) {
+      const float oh = __shfl_down_sync(FULL, hi[k], off);
+      const float ol = __shfl_down_sync(FULL, lo[k], off);
+      ff_add(hi[k], lo[k], oh);
+      lo[k] += ol;
     }
   }
   if (lane == 0) {
 #pragma unroll
-    for (int v = 0; v < NP - 1; ++v) {
-      s_red[warp][v] = hi[v];
-      s_redlo[warp][v] = lo[v];
+    for (int k = 0; k < NP - 1; ++k) {
+      s_red[warp][k] = hi[k];
+      s_redlo[warp][k] = lo[k];
     }
   }
   __syncthreads();
   if (tid != 0) return false;
-  for (int v = 0; v < NP - 1; ++v) {
+#pragma unroll
+  for (int k = 0; k < NP - 1; ++k) {
     float h = 0.0f, l = 0.0f;
     for (int w = 0; w < NW; ++w) {
-      ff_add(h, l, s_red[w][v]);
-      l += s_redlo[w][v];
+      ff_add(h, l, s_red[w][k]);
+      l += s_redlo[w][k];
     }
-    S[v] = (double)h + (double)l;
+    S[k] = (double)h + (double)l;
   }
   Mx_out = Mx;
   return true;
@@ -164,27 +198,32 @@ __device__ __forceinline__ bool fold_partials(const StepParams& p, Partial acc, 
 
 // Writes the step's summaries from the folded sums (thread 0 of the last block):
 // likelihood increment, filter mean and ESS into the output rings, the
-// cumulative log-likelihood and the next normaliser.  Returns the ESS.
+// cumulative log-likelihood (FP64) and the next normaliser.  Returns the ESS.
+// The log of the weight sum is taken as exponent (FP64) plus log of the
+// mantissa (FP32), about 1e-7 absolute; mean and ESS are FP32 outputs.
 template <int D>
 __device__ __forceinline__ double write_summaries(const StepParams& p, const double* S, float Mx, uint32_t n,
                                                   float muf, double* lme_out = nullptr) {
   DevState* st = p.st;
   const ModelParams& mp = p.model;
   const uint32_t slot = n % kRing;
+  const double mu_prev = st->mu;
+  const double ll_prev = st->loglik;
   double lme, inc, ess;
   if (Mx == -INFINITY || !(S[0] > 0.0)) {
     lme = -INFINITY;
     inc = -INFINITY;
     ess = 0.0;
   } else {
-    lme = (double)Mx + log(S[0] * (double)p.inv_N);
-    inc = lme + ((double)muf - st->mu) + mp.c_obs;
+    lme = (double)Mx + (log_split(S[0]) - log_split((double)p.N));
+    inc = lme + ((double)muf - mu_prev) + mp.c_obs;
     ess = S[0] * S[0] / ((double)p.N * S[1]);
   }
   p.inc_ring[slot] = inc;
   p.ess_ring[slot] = (float)ess;
-  for (int t = 0; t < D; ++t) p.mean_ring[slot * mp.d + t] = (float)(S[2 + t] / S[0]);
-  st->loglik += inc;
+  const float inv_s0 = 1.0f / (float)S[0];
+  for (int t = 0; t < D; ++t) p.mean_ring[slot * mp.d + t] = (float)S[2 + t] * inv_s0;
+  st->loglik = ll_prev + inc;
   st->mu = lme;
   st->mu_f = (float)lme;
   if (lme_out) *lme_out = lme;

@@ -14,7 +14,7 @@ namespace bfpf {
 template <int D, int KIND>
 __device__ __forceinline__ float obs_log_term(const ModelParams& mp, const float* y, const float* x) {
   if constexpr (KIND == kStochVol) {
-    return fmaf(-0.5f, x[0], -(y[0] * y[0] * mp.inv2b2) * __expf(-x[0]));
+    return fmaf(-0.5f, x[0], -(y[0] * y[0] * mp.inv2b2) * ex2_ftz(x[0] * -1.4426950408889634f));
   } else {
     float r[kMaxDim];
 #pragma unroll

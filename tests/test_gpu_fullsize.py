@@ -60,25 +60,33 @@ def test_headline_over_the_full_horizon_against_the_grid_filter(bfpf):
 
 def test_lg8d_full_size_against_kalman(bfpf):
     """The 8-dimensional linear-Gaussian workload at full size (N = 2^20, T = 1000)
-    against the exact Kalman filter (measured: global resampling -0.4 to -0.8 in
-    log-likelihood, all stages per step -3.9 -- staged interaction has the larger
-    estimator variance, and the log of an unbiased estimate sits about half its
-    variance low; summed squared mean error about 4 for both).  The one-digit
-    schedule's error is reported, not bounded: it carries weights between steps,
-    and sharp 8-dimensional likelihoods make them degenerate (-73, 182)."""
+    against the exact Kalman filter.  The likelihood estimate is unbiased in p^,
+    so over independent filter seeds the error of log p^ has mean about -Var/2
+    (measured: standard deviation about 1.5 for global resampling and 1.7 for all
+    stages per step, means -1.3 to -1.8); checked over six seeds, with the summed
+    squared error of the filtering means (about 4) bounded per run.  The
+    one-digit schedule's error is reported, not bounded: it carries weights
+    between steps, and sharp 8-dimensional likelihoods make them degenerate
+    (about -75 in log-likelihood)."""
     from oracle import kalman
     w = S.workload("lg8d_n1m")
     y = w.observations()
     kf = kalman.kalman_filter(w.model, y)
     res = {}
-    for name, rad, kw in (("one_digit", w.radices, {}), ("all_stages", w.radices, {"all_stages": True}),
-                          ("global", (w.N,), {})):
-        f = bfpf.ButterflyFilter(w.model, w.N, rad, w.filter_seed, **kw)
-        r = f.run(y)
-        res[name] = (f.loglik() - kf["loglik"], float(np.sum((r["mean"] - kf["mean"]) ** 2)))
-        f.close()
-    print("lg8d vs Kalman (loglik error, summed squared mean error)", res)
-    assert abs(res["global"][0]) < 3.0, res
-    assert abs(res["all_stages"][0]) < 12.0, res
+    for name, rad, kw, seeds in (("one_digit", w.radices, {}, 1), ("all_stages", w.radices, {"all_stages": True}, 6),
+                                 ("global", (w.N,), {}, 6)):
+        errs, mse = [], []
+        for r in range(seeds):
+            f = bfpf.ButterflyFilter(w.model, w.N, rad, w.filter_seed + 101 * r, **kw)
+            out = f.run(y)
+            errs.append(f.loglik() - kf["loglik"])
+            mse.append(float(np.sum((out["mean"] - kf["mean"]) ** 2)))
+            f.close()
+        res[name] = (np.array(errs), np.array(mse))
+    print("lg8d vs Kalman (loglik errors, summed squared mean errors)", res)
     for name in ("all_stages", "global"):
-        assert res[name][1] < 8.0, (name, res[name])
+        err, mse = res[name]
+        se = err.std(ddof=1) / np.sqrt(len(err))
+        assert abs(err.mean() + 0.5 * err.var(ddof=1)) < 4 * se + 0.1, (name, err)
+        assert err.std(ddof=1) < 4.0, (name, err)
+        assert np.all(mse < 8.0), (name, mse)
