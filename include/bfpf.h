@@ -125,6 +125,12 @@ typedef struct {
  * m >= 2 and a_0 a_s <= 1024; m - 1 launches per step.  Cannot be combined
  * with the other schedule flags or PF_RECORD_ANCESTORS. */
 #define PF_DIGIT_SETS 64u
+/* Parity output: also keep, for every particle, the inclusive prefix sum P of
+ * the integer weights within its group at the last step (the numbers the
+ * integer draw of Algorithm 2 / Algorithm 3's sampling line compares its
+ * uniform with; read by pf_get_draw_prefix).  Implies PF_RECORD_ANCESTORS and
+ * its limits.  Adds 8N bytes of workspace. */
+#define PF_RECORD_DRAWS 128u
 /* Test hook for failure reporting (global resampling with N > 4096 only):
  * the second scan tile waits on a flag that nothing sets, so its bounded wait
  * runs out (well under a second) every step, status bit 2 is set and
@@ -167,7 +173,7 @@ pf_status pf_workspace_size(const pf_model* model, int64_t N, const int32_t* rad
  * particles (Assumption A1 of the paper with paper-m = N / M generalised to
  * mixed radix).  Every radix must be >= 2 and <= 1024, except that m == 1
  * (radices = {N}: the global-resampling bootstrap filter of Algorithm 2) allows
- * any N.  N < 2^31.  `seed` keys the counter-based random stream (Philox4x32-10),
+ * any N.  N < 2^31.  `seed` keys the counter-based random stream (Philox4x32 with seven rounds),
  * so a run is reproducible given (model, N, radices, seed, observations).
  *
  * workspace: device memory of at least pf_workspace_size() bytes, 256-byte
@@ -244,6 +250,20 @@ pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars)
  * needs PF_RECORD_ANCESTORS.  anc: N int32, host.  Synchronises. */
 pf_status pf_get_ancestors(const pf_handle* h, int32_t* anc);
 
+/*
+ * The integer prefix sums behind the last step's draws (Algorithm 2; the
+ * sampling line of Algorithm 3): prefix[i] = q_0 + ... + q_r for particle i =
+ * member r (its digit k) of its group, q_j = floor(e_j 2^B) the quantised
+ * weight of member j (B = 24 for groups of at most 256 members, else 32).
+ * With the group's total Q and the particle's uniform word(s) r, its ancestor
+ * is member #{j : prefix_j <= floor(r Q / 2^W)} (W = 32 or 64), so a checker
+ * that is given these integers can redo every draw exactly.  prefix: N
+ * uint64, host.  Available with PF_RECORD_DRAWS, and always for global
+ * resampling (radices = {N}, N > 1024), whose single group is all N
+ * particles.  Synchronises.  Errors: PF_ESTATE when not recorded.
+ */
+pf_status pf_get_draw_prefix(const pf_handle* h, uint64_t* prefix);
+
 /* Sticky device-side status bits of the handle (0 = none): bit 0 = a
  * non-finite log-weight was seen and treated as weight zero; bit 1 = a group
  * had zero total weight and kept its particles; bit 2 = a bounded wait of the
@@ -290,8 +310,8 @@ pf_status pf_destroy(pf_handle* h);
 const char* pf_last_error(const pf_handle* h);
 
 /*
- * Philox4x32-10 blocks, for checking the device generator against an
- * independent implementation: out[4*j + w] = word w of Philox4x32-10 with
+ * Philox4x32-7 blocks, for checking the device generator against an
+ * independent implementation: out[4*j + w] = word w of Philox4x32-7 with
  * key (seed mod 2^32, seed div 2^32) and counter (c0 + j, c1, c2, c3),
  * j = 0..count-1.  out: device pointer to 4*count uint32.  Runs on `stream`
  * (cudaStream_t, may be NULL) and is asynchronous.

@@ -10,7 +10,7 @@ Contents (each function cites the passage of Heine, Whiteley & Cemgil,
 "Parallelising particle filters with butterfly interactions", arXiv
 1812.01502, that it follows):
 
-* ``philox``      Philox4x32-10 counter-based generator (Salmon et al., SC'11)
+* ``philox``      Philox4x32-7 counter-based generator (Salmon et al., SC'11)
                   and Box-Muller normals; the counter layout of the filter.
 * ``butterfly``   the mixed-radix butterfly matrices A_s of Section 1.2 and
                   Lemmas 1-3, as dense matrices for small N, and the group

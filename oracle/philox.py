@@ -1,11 +1,13 @@
-"""Philox4x32-10 and Box-Muller normals for the oracle (numpy, vectorised).
+"""Philox4x32-7 and Box-Muller normals for the oracle (numpy, vectorised).
 
 Philox4x32 is defined in Salmon, Moraes, Dror & Shaw, "Parallel random
 numbers: as easy as 1, 2, 3" (SC'11), Section 3: a 4x32-bit counter is mixed
 by R rounds of two 32x32->64 multiplications whose high halves are xor-ed
 with the other two words and a round key; the key is bumped by the Weyl
 constants between rounds.  This file is written from that description and
-shares nothing with the CUDA implementation.
+shares nothing with the CUDA implementation.  The filter uses R = 7 rounds:
+Salmon et al. report Philox4x32 free of TestU01 BigCrush failures from seven
+rounds on (ten being their choice with a safety margin).
 
 The paper being implemented is silent on random numbers.  The filter's
 counter layout (a reading of this library, used identically by the CUDA
@@ -44,6 +46,8 @@ PHILOX_M1 = np.uint64(0xCD9E8D57)
 PHILOX_W0 = 0x9E3779B9
 PHILOX_W1 = 0xBB67AE85
 
+ROUNDS = 7          # rounds of Philox4x32 in the filter's random stream
+
 PURPOSE_INIT = 0
 PURPOSE_PROPAGATE = 1
 PURPOSE_RESAMPLE = 2
@@ -51,7 +55,7 @@ PURPOSE_RESAMPLE_WIDE = 3
 PURPOSE_ISLAND = 4
 
 
-def philox4x32(c0, c1, c2, c3, key, rounds: int = 10):
+def philox4x32(c0, c1, c2, c3, key, rounds: int = ROUNDS):
     """Philox4x32-R on arrays of counters.  Returns four uint32 arrays.
 
     c0..c3: array-likes broadcastable to a common shape (values < 2^32).

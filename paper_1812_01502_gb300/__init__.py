@@ -37,6 +37,7 @@ PF_ISLANDS_PLAIN = 32
 PF_TEST_SCAN_TIMEOUT = 0x80000000
 PF_TEST_SMALL_BUCKETS = 0x40000000
 PF_DIGIT_SETS = 64
+PF_RECORD_DRAWS = 128
 STATUS_NAMES = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",
                 PF_ETIMEOUT: "PF_ETIMEOUT", PF_ESTATE: "PF_ESTATE"}
 
@@ -87,6 +88,7 @@ def load_library(path: str = LIB_PATH):
         "pf_get_state": (i32, [vp, vp, vp, vp]),
         "pf_get_ancestors": (i32, [vp, vp]),
         "pf_get_status": (i32, [vp, c.POINTER(u32)]),
+        "pf_get_draw_prefix": (i32, [vp, vp]),
         "pf_stage_count": (i32, [vp, c.POINTER(c.c_uint64)]),
         "pf_checkpoint_size": (i32, [vp, c.POINTER(c.c_size_t)]),
         "pf_save": (i32, [vp, vp, c.c_size_t]),
@@ -338,6 +340,12 @@ class ButterflyFilter:
         _check(_lib.pf_get_ancestors(self._h, anc.ctypes.data_as(ctypes.c_void_p)), self._h)
         return anc
 
+    def draw_prefix(self) -> np.ndarray:
+        """Integer prefix sums of the last step's draws (pf_get_draw_prefix), uint64 (N,)."""
+        out = np.empty(self.N, dtype=np.uint64)
+        _check(_lib.pf_get_draw_prefix(self._h, out.ctypes.data_as(ctypes.c_void_p)), self._h)
+        return out
+
     def status(self) -> int:
         b = ctypes.c_uint32(0)
         _check(_lib.pf_get_status(self._h, ctypes.byref(b)), self._h)
@@ -475,7 +483,7 @@ class FilterBatch:
 
 
 def philox_blocks(seed: int, counter, count: int, device=None):
-    """Philox4x32-10 words for counters (c0 + j, c1, c2, c3), j < count: a (count, 4) int64
+    """Philox4x32-7 words for counters (c0 + j, c1, c2, c3), j < count: a (count, 4) int64
     tensor of uint32 values (computed on the GPU by the library)."""
     torch = _torch()
     lib = load_library()

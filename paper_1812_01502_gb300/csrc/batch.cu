@@ -81,6 +81,7 @@ __device__ __forceinline__ void batch_filter_step(const BatchParams& bp, BatchFi
   ctx.lV_in = f.lV[n & 1u];
   ctx.lV_out = f.lV[(n & 1u) ^ 1u];
   ctx.anc = nullptr;
+  ctx.prec = nullptr;
   ctx.rk = &f.rk;
   ctx.mp = &f.model;
   ctx.g = &f.geom[k];
@@ -157,7 +158,7 @@ __global__ void __launch_bounds__(kBlock) batch_init_kernel(const __grid_constan
     float z[kMaxDim];
     for (uint32_t t = 0; t < d; ++t) {
       const uint32_t nu = i * d + t;
-      const uint4 w = philox4x32_10(make_uint4(nu >> 2, 0, kPurposeInit, 0), f.rk);
+      const uint4 w = philox4x32(make_uint4(nu >> 2, 0, kPurposeInit, 0), f.rk);
       float zz[4];
       normals4(w, zz);
       z[t] = zz[nu & 3u];

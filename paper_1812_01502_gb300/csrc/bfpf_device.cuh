@@ -1,6 +1,6 @@
 // bfpf_device.cuh - device-side building blocks of the butterfly particle filter.
 //
-// Philox4x32-10 (Salmon, Moraes, Dror & Shaw, SC'11), Box-Muller normals,
+// Philox4x32-7 (Salmon, Moraes, Dror & Shaw, SC'11), Box-Muller normals,
 // division by run-time invariant integers (Granlund & Montgomery, PLDI'94),
 // float-float compensated sums (Knuth's TwoSum), and the parameter blocks the
 // kernels receive.  The random-stream layout (which counter feeds which
@@ -44,18 +44,22 @@ constexpr uint32_t kStatusTimeout = 4u;    // a bounded wait gave up (global sca
 enum ModelKind : int { kLinearGaussian = 1, kStochVol = 2 };
 
 // ---------------------------------------------------------------------------
-// Philox4x32-10.  The ten round keys (k0 + r W0, k1 + r W1) depend only on the
-// seed; kernels take them precomputed from their parameter block so that the
-// xor with the round key reads a constant operand.
-// ---------------------------------------------------------------------------
+// Philox4x32 with seven rounds.  Salmon et al. report Philox4x32 free of
+// TestU01 BigCrush failures from seven rounds on and use ten as a safety
+// margin; this library takes seven (the oracle implements the same count).
+// The round keys (k0 + r W0, k1 + r W1) depend only on the seed; kernels take
+// them precomputed from their parameter block so that the xor with the round
+// key reads a constant operand.
+constexpr int kPhiloxRounds = 7;
+
 struct RoundKeys {
-  uint32_t k[20];   // k[2r], k[2r+1]: round r
+  uint32_t k[2 * kPhiloxRounds];   // k[2r], k[2r+1]: round r
 };
 
 inline RoundKeys make_round_keys(uint64_t seed) {
   RoundKeys rk;
   uint32_t k0 = (uint32_t)seed, k1 = (uint32_t)(seed >> 32);
-  for (int r = 0; r < 10; ++r) {
+  for (int r = 0; r < kPhiloxRounds; ++r) {
     rk.k[2 * r] = k0;
     rk.k[2 * r + 1] = k1;
     k0 += 0x9E3779B9u;
@@ -70,15 +74,15 @@ __device__ __forceinline__ uint4 philox_round(uint4 c, uint32_t k0, uint32_t k1)
   return make_uint4((uint32_t)(p1 >> 32) ^ c.y ^ k0, (uint32_t)p1, (uint32_t)(p0 >> 32) ^ c.w ^ k1, (uint32_t)p0);
 }
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, const RoundKeys& rk) {
+__device__ __forceinline__ uint4 philox4x32(uint4 c, const RoundKeys& rk) {
 #pragma unroll
-  for (int r = 0; r < 10; ++r) c = philox_round(c, rk.k[2 * r], rk.k[2 * r + 1]);
+  for (int r = 0; r < kPhiloxRounds; ++r) c = philox_round(c, rk.k[2 * r], rk.k[2 * r + 1]);
   return c;
 }
 
-__device__ __forceinline__ uint4 philox4x32_10(uint4 c, uint32_t k0, uint32_t k1) {
+__device__ __forceinline__ uint4 philox4x32(uint4 c, uint32_t k0, uint32_t k1) {
 #pragma unroll
-  for (int r = 0; r < 10; ++r) {
+  for (int r = 0; r < kPhiloxRounds; ++r) {
     c = philox_round(c, k0, k1);
     k0 += 0x9E3779B9u;
     k1 += 0xBB67AE85u;
@@ -284,6 +288,8 @@ struct StepParams {
   float* x;            // [d][N] particle states (updated in place)
   float* lV[2];        // carried log stage weights, ping-pong by stage-counter parity
   int32_t* anc;        // [N] ancestors of the last step (nullptr = not recorded)
+  unsigned long long* prec;   // [N] inclusive prefix sums of the integer weights within each
+                              // particle's group at the last step (nullptr = not recorded)
   DevState* st;
   float* partials;     // [grid][3 + d] per-block partial sums
   const float* y_ring; // [kRing][dy]

@@ -41,7 +41,7 @@ constexpr size_t kAlign = 256;
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t st, x, lv0, lv1, anc, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
+  size_t st, x, lv0, lv1, anc, prec, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
   size_t x2, lw, P, agg, incl, flag;        // global resampling only (x2: also AIRPF)
   size_t slot, cnt, ovf, jb, cslot, ccnt, covf;   // global resampling: draws filed by coarse bin, then bucket
   size_t src;                               // AIRPF: island sources
@@ -67,6 +67,7 @@ struct Plan {
   int grid = 0;
   size_t smem = 0;
   bool record = false;
+  bool record_draws = false;  // PF_RECORD_DRAWS: integer prefix sums of the step's draws (test output)
   uint32_t sps = 1;           // resampling stages per time step (1, or m with PF_ALL_STAGES)
   bool adaptive = false;      // PF_ADAPTIVE: m + 1 launches per step, per-particle carried weights
   bool rotate = false;
@@ -240,6 +241,13 @@ uint32_t largest_divisor_at_most(uint32_t n, uint32_t limit) {
 
 pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, int32_t m,
                     const pf_options* opts, Plan& pl, std::string& msg) {
+  pf_options opts_rec;
+  if (opts && (opts->flags & PF_RECORD_DRAWS)) {   // records the ancestors too, with the same limits
+    opts_rec = *opts;
+    opts_rec.flags |= PF_RECORD_ANCESTORS;
+    opts = &opts_rec;
+    pl.record_draws = true;
+  }
   const pf_status bs = build_model(model, pl.mp, msg);
   if (bs != PF_OK) return bs;
   pl.d = pl.mp.d;
@@ -624,6 +632,7 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
   L.lv0 = take((size_t)4 * nlv);
   L.lv1 = take((size_t)4 * nlv);
   L.anc = pl.record ? take((size_t)4 * pl.N) : 0;
+  L.prec = pl.record_draws ? take((size_t)8 * pl.N) : 0;
   L.partials = take((size_t)4 * (3 + pl.d) * grid);
   L.y_ring = take((size_t)4 * kRing * pl.dy);
   L.inc_ring = take((size_t)8 * kRing);
@@ -768,6 +777,8 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
   P.lV[0] = reinterpret_cast<float*>(h->ws + L.lv0);
   P.lV[1] = reinterpret_cast<float*>(h->ws + L.lv1);
   P.anc = pl.record ? reinterpret_cast<int32_t*>(h->ws + L.anc) : nullptr;
+  // the global path keeps its prefix sums in L.P; the others record them on request
+  P.prec = (pl.record_draws && !pl.global) ? reinterpret_cast<unsigned long long*>(h->ws + L.prec) : nullptr;
   P.st = reinterpret_cast<DevState*>(h->ws + L.st);
   P.partials = reinterpret_cast<float*>(h->ws + L.partials);
   P.y_ring = reinterpret_cast<const float*>(h->ws + L.y_ring);
@@ -1018,6 +1029,17 @@ pf_status pf_get_ancestors(const pf_handle* h, int32_t* anc) {
   if (!h || !anc) return fail(h, PF_EINVAL, "NULL argument");
   if (!h->P.anc) return fail(h, PF_ESTATE, "ancestors are not recorded (create with PF_RECORD_ANCESTORS)");
   PF_CUDA(h, cudaMemcpyAsync(anc, h->P.anc, (size_t)4 * h->plan.N, cudaMemcpyDeviceToHost, h->stream));
+  PF_CUDA(h, cudaStreamSynchronize(h->stream));
+  return PF_OK;
+}
+
+pf_status pf_get_draw_prefix(const pf_handle* h, uint64_t* prefix) {
+  if (!h || !prefix) return fail(h, PF_EINVAL, "NULL argument");
+  const void* src = nullptr;
+  if (h->plan.global) src = h->ws + h->plan.lay.P;
+  else if (h->P.prec) src = h->P.prec;
+  else return fail(h, PF_ESTATE, "draws are not recorded (create with PF_RECORD_DRAWS)");
+  PF_CUDA(h, cudaMemcpyAsync(prefix, src, (size_t)8 * h->plan.N, cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   return PF_OK;
 }

@@ -85,6 +85,7 @@ __global__ void __launch_bounds__(kBlock) adaptive_stage_kernel(const __grid_con
   c.lV_in = p.lV[lvp];
   c.lV_out = p.lV[lvp ^ 1u];
   c.anc = nullptr;
+  c.prec = nullptr;
   c.rk = &p.rk;
   c.mp = &p.model;
   c.g = &p.geom[k];

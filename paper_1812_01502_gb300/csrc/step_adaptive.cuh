@@ -36,7 +36,7 @@ __device__ __forceinline__ void adaptive_mutate_only(const StepParams& p, const 
       float z[4 * D];
 #pragma unroll
       for (int b = 0; b < D; ++b) {
-        const uint4 w = philox4x32_10(make_uint4(q * D + b, n, kPurposePropagate, 0), p.rk);
+        const uint4 w = philox4x32(make_uint4(q * D + b, n, kPurposePropagate, 0), p.rk);
         normals4(w, z + 4 * b);
       }
 #pragma unroll
@@ -60,7 +60,7 @@ __device__ __forceinline__ void adaptive_mutate_only(const StepParams& p, const 
       for (int t = 0; t < D; ++t) {
         xh[t] = __ldcs(p.x + (size_t)t * p.N + i);
         const uint32_t nu = pi * D + t;
-        const uint4 w = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
+        const uint4 w = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
         float zz[4];
         normals4(w, zz);
         z[t] = zz[nu & 3u];

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(kBlock) init_particles_kernel(const __grid_con
 #pragma unroll
     for (int t = 0; t < D; ++t) {
       const uint32_t nu = i * D + t;
-      const uint4 w = philox4x32_10(make_uint4(nu >> 2, 0, kPurposeInit, 0), p.rk);
+      const uint4 w = philox4x32(make_uint4(nu >> 2, 0, kPurposeInit, 0), p.rk);
       float zz[4];
       normals4(w, zz);
       z[t] = zz[nu & 3u];
@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(kBlock) init_particles_kernel(const __grid_con
 
 __global__ void philox_blocks_kernel(uint32_t k0, uint32_t k1, uint4 c, uint32_t count, uint32_t* out) {
   for (uint32_t j = blockIdx.x * kBlock + threadIdx.x; j < count; j += gridDim.x * kBlock) {
-    const uint4 w = philox4x32_10(make_uint4(c.x + j, c.y, c.z, c.w), k0, k1);
+    const uint4 w = philox4x32(make_uint4(c.x + j, c.y, c.z, c.w), k0, k1);
     reinterpret_cast<uint4*>(out)[j] = w;
   }
 }

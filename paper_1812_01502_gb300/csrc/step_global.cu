@@ -237,7 +237,7 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
     bool valid[V];
 #pragma unroll
     for (int h = 0; h < V / 2; ++h) {
-      const uint4 w = philox4x32_10(make_uint4(i0 / 2u + h, n, kPurposeResampleWide, 0), p.rk);
+      const uint4 w = philox4x32(make_uint4(i0 / 2u + h, n, kPurposeResampleWide, 0), p.rk);
       r[2 * h] = ((unsigned long long)w.y << 32) | w.x;
       r[2 * h + 1] = ((unsigned long long)w.w << 32) | w.z;
     }
@@ -504,7 +504,7 @@ __device__ __forceinline__ void resolve_draw(const StepParams& p, const GlobalPa
 #pragma unroll
     for (int t = 0; t < D; ++t) {
       const uint32_t nu = nu0 + t;
-      if (t == 0 || (nu & 3u) == 0u) w = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
+      if (t == 0 || (nu & 3u) == 0u) w = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
       if (t == 0 || (nu & 1u) == 0u) box_muller_fast((nu & 2u) ? w.z : w.x, (nu & 2u) ? w.w : w.y, z0, z1);
       z[t] = (nu & 1u) ? z1 : z0;
     }

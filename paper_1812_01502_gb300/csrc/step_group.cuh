@@ -199,6 +199,10 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
     }
 #pragma unroll
     for (int mm = 0; mm < M; ++mm) P[mm] += excl;
+    if (p.prec) {                  // test output: the integer prefix sums the draws use
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm) p.prec[i0 + (mm << log2s)] = P[mm];
+    }
     if constexpr (M % 4 == 0) {
 #pragma unroll
       for (int q = 0; q < M / 4; ++q)
@@ -249,7 +253,7 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
       constexpr int MQ = (M < 4) ? M : 4;             // members handled in this round
       uint32_t rw[MQ];
       {
-        const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) + q4, sc.t, kPurposeResample, 0), p.rk);
+        const uint4 w = philox4x32(make_uint4((pi0 >> 2) + q4, sc.t, kPurposeResample, 0), p.rk);
         if constexpr (M >= 4) {
           rw[0] = w.x; rw[1] = w.y; rw[2] = w.z; rw[3] = w.w;
         } else {
@@ -267,12 +271,12 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
         const uint32_t c0 = ((pi0 + 4 * q4) * D) >> 2;
 #pragma unroll
         for (int b = 0; b < MQ * D / 4; ++b) {
-          const uint4 w = philox4x32_10(make_uint4(c0 + b, n, kPurposePropagate, 0), p.rk);
+          const uint4 w = philox4x32(make_uint4(c0 + b, n, kPurposePropagate, 0), p.rk);
           normals4_fast(w, z + 4 * b);
         }
       } else if constexpr (4 % (MQ * D) == 0) {       // 1 or 2 normals inside one block
         const uint32_t nu0 = pi0 * D;
-        const uint4 w = philox4x32_10(make_uint4(nu0 >> 2, n, kPurposePropagate, 0), p.rk);
+        const uint4 w = philox4x32(make_uint4(nu0 >> 2, n, kPurposePropagate, 0), p.rk);
         float zz[4];
         normals4_fast(w, zz);
         const uint32_t off = nu0 & 3u;
@@ -287,7 +291,7 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
         float zz[4 * NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          const uint4 w = philox4x32_10(make_uint4((nu0 >> 2) + b, n, kPurposePropagate, 0), p.rk);
+          const uint4 w = philox4x32(make_uint4((nu0 >> 2) + b, n, kPurposePropagate, 0), p.rk);
           normals4_fast(w, zz + 4 * b);
         }
         const uint32_t off = nu0 & 3u;

@@ -95,8 +95,8 @@ __global__ void __launch_bounds__(kIslandThreads) island_stages_kernel(const __g
       }
       const uint32_t q0 = __float2uint_rz(e0 * 16777216.0f);
       const uint32_t Q = q0 + __float2uint_rz(e1 * 16777216.0f);
-      const uint4 w0 = philox4x32_10(make_uint4(i0 >> 2, n, kPurposeIsland, s), p.rk);
-      const uint4 w1 = philox4x32_10(make_uint4(i1 >> 2, n, kPurposeIsland, s), p.rk);
+      const uint4 w0 = philox4x32(make_uint4(i0 >> 2, n, kPurposeIsland, s), p.rk);
+      const uint4 w1 = philox4x32(make_uint4(i1 >> 2, n, kPurposeIsland, s), p.rk);
       const uint32_t o0 = i0 & 3u, o1 = i1 & 3u;
       const uint32_t r0 = o0 == 0 ? w0.x : o0 == 1 ? w0.y : o0 == 2 ? w0.z : w0.w;
       const uint32_t r1 = o1 == 0 ? w1.x : o1 == 1 ? w1.y : o1 == 2 ? w1.z : w1.w;
@@ -150,7 +150,7 @@ __global__ void __launch_bounds__(kBlock) island_gather_kernel(const __grid_cons
       }
 #pragma unroll
       for (int b = 0; b < D; ++b) {          // normals nu = i d + t, blocks of 4
-        const uint4 w = philox4x32_10(make_uint4(q * D + b, n, kPurposePropagate, 0), p.rk);
+        const uint4 w = philox4x32(make_uint4(q * D + b, n, kPurposePropagate, 0), p.rk);
         normals4(w, z + 4 * b);
       }
       float out[D][4];
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kBlock) island_gather_kernel(const __grid_cons
       for (int t = 0; t < D; ++t) {
         xh[t] = __ldg(X + (size_t)t * N + sp);
         const uint32_t nu = i * D + t;
-        const uint4 w = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
+        const uint4 w = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
         float zz[4];
         normals4(w, zz);
         z[t] = zz[nu & 3u];

@@ -185,20 +185,20 @@ __device__ __forceinline__ void set_tile_steps(const TileCtx& ctx, uint32_t firs
       float z[4 * D];
       if (g4) {   // pi0 % 4 == 0: whole counter blocks
         if (WIDE && wide_digit) {
-          const uint4 w0 = philox4x32_10(make_uint4(pi0 >> 1, t_st, kPurposeResampleWide, 0), rk);
-          const uint4 w1 = philox4x32_10(make_uint4((pi0 >> 1) + 1, t_st, kPurposeResampleWide, 0), rk);
+          const uint4 w0 = philox4x32(make_uint4(pi0 >> 1, t_st, kPurposeResampleWide, 0), rk);
+          const uint4 w1 = philox4x32(make_uint4((pi0 >> 1) + 1, t_st, kPurposeResampleWide, 0), rk);
           rw64[0] = ((unsigned long long)w0.y << 32) | w0.x;
           rw64[1] = ((unsigned long long)w0.w << 32) | w0.z;
           rw64[2] = ((unsigned long long)w1.y << 32) | w1.x;
           rw64[3] = ((unsigned long long)w1.w << 32) | w1.z;
         } else {
-          const uint4 wv = philox4x32_10(make_uint4(pi0 >> 2, t_st, kPurposeResample, 0), rk);
+          const uint4 wv = philox4x32(make_uint4(pi0 >> 2, t_st, kPurposeResample, 0), rk);
           rw[0] = wv.x; rw[1] = wv.y; rw[2] = wv.z; rw[3] = wv.w;
         }
         if (mut) {
 #pragma unroll
           for (int b = 0; b < D; ++b) {
-            const uint4 wv = philox4x32_10(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
+            const uint4 wv = philox4x32(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
             normals4(wv, z + 4 * b);
           }
         }
@@ -208,10 +208,10 @@ __device__ __forceinline__ void set_tile_steps(const TileCtx& ctx, uint32_t firs
           const uint32_t pi = pi0 + jj;
           if (r0q + jj >= G) break;
           if (WIDE && wide_digit) {
-            const uint4 wv = philox4x32_10(make_uint4(pi >> 1, t_st, kPurposeResampleWide, 0), rk);
+            const uint4 wv = philox4x32(make_uint4(pi >> 1, t_st, kPurposeResampleWide, 0), rk);
             rw64[jj] = (pi & 1u) ? (((unsigned long long)wv.w << 32) | wv.z) : (((unsigned long long)wv.y << 32) | wv.x);
           } else {
-            const uint4 wv = philox4x32_10(make_uint4(pi >> 2, t_st, kPurposeResample, 0), rk);
+            const uint4 wv = philox4x32(make_uint4(pi >> 2, t_st, kPurposeResample, 0), rk);
             const uint32_t sel = pi & 3u;
             rw[jj] = sel == 0 ? wv.x : sel == 1 ? wv.y : sel == 2 ? wv.z : wv.w;
           }
@@ -219,7 +219,7 @@ __device__ __forceinline__ void set_tile_steps(const TileCtx& ctx, uint32_t firs
 #pragma unroll
           for (int t = 0; t < D; ++t) {
             const uint32_t nu = pi * D + t;
-            const uint4 wv = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), rk);
+            const uint4 wv = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), rk);
             float zz[4];
             normals4(wv, zz);
             z[jj * D + t] = zz[nu & 3u];
@@ -281,6 +281,7 @@ __global__ void __launch_bounds__(kBlock) step_sets_kernel(const __grid_constant
   c.lV_in = p.lV[sc.t & 1u];
   c.lV_out = p.lV[(sc.t & 1u) ^ 1u];
   c.anc = nullptr;
+  c.prec = nullptr;
   c.rk = &p.rk;
   c.mp = &p.model;
   c.g = &p.geom[sc.k];

@@ -30,6 +30,7 @@ struct TileCtx {
   const float* lV_in;        // carried log weights, groups of the previous digit
   float* lV_out;             // new carried log weights, groups of this digit
   int32_t* anc;              // ancestors (nullptr: not recorded)
+  unsigned long long* prec;  // integer prefix sums of the draws (nullptr: not recorded)
   const RoundKeys* rk;
   const ModelParams* mp;
   const DigitGeom* g;        // geometry of this step's digit
@@ -179,6 +180,10 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
         const PT excl = incl - run;
         if (live && excl != 0)
           for (uint32_t r = rb; r < re; ++r) s_P[p0 + r * nl] += excl;
+        if (ctx.prec && active) {    // test output: the integer prefix sums the draws use
+          const uint32_t ib = base + hh * a * s + col;
+          for (uint32_t r = rb; r < re; ++r) ctx.prec[ib + r * s] = (unsigned long long)s_P[p0 + r * nl];
+        }
         // each lane folds its own chunk into its running partial (same max M for the
         // whole team); only the group's sum of weights is needed here, for L
         float sg = s1;
@@ -224,20 +229,20 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
       float z[4 * D];
       if (a4) {   // pi0 % 4 == 0: whole counter blocks
         if (WIDE && wide_digit) {
-          const uint4 w0 = philox4x32_10(make_uint4(pi0 >> 1, t_st, kPurposeResampleWide, 0), rk);
-          const uint4 w1 = philox4x32_10(make_uint4((pi0 >> 1) + 1, t_st, kPurposeResampleWide, 0), rk);
+          const uint4 w0 = philox4x32(make_uint4(pi0 >> 1, t_st, kPurposeResampleWide, 0), rk);
+          const uint4 w1 = philox4x32(make_uint4((pi0 >> 1) + 1, t_st, kPurposeResampleWide, 0), rk);
           rw64[0] = ((unsigned long long)w0.y << 32) | w0.x;
           rw64[1] = ((unsigned long long)w0.w << 32) | w0.z;
           rw64[2] = ((unsigned long long)w1.y << 32) | w1.x;
           rw64[3] = ((unsigned long long)w1.w << 32) | w1.z;
         } else {
-          const uint4 w = philox4x32_10(make_uint4(pi0 >> 2, t_st, kPurposeResample, 0), rk);
+          const uint4 w = philox4x32(make_uint4(pi0 >> 2, t_st, kPurposeResample, 0), rk);
           rw[0] = w.x; rw[1] = w.y; rw[2] = w.z; rw[3] = w.w;
         }
         if (mut) {
 #pragma unroll
           for (int b = 0; b < D; ++b) {
-            const uint4 w = philox4x32_10(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
+            const uint4 w = philox4x32(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
             normals4(w, z + 4 * b);
           }
         }
@@ -247,10 +252,10 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
           const uint32_t pi = pi0 + jj;
           if (r0 + jj >= a) break;
           if (WIDE && wide_digit) {
-            const uint4 w = philox4x32_10(make_uint4(pi >> 1, t_st, kPurposeResampleWide, 0), rk);
+            const uint4 w = philox4x32(make_uint4(pi >> 1, t_st, kPurposeResampleWide, 0), rk);
             rw64[jj] = (pi & 1u) ? (((unsigned long long)w.w << 32) | w.z) : (((unsigned long long)w.y << 32) | w.x);
           } else {
-            const uint4 w = philox4x32_10(make_uint4(pi >> 2, t_st, kPurposeResample, 0), rk);
+            const uint4 w = philox4x32(make_uint4(pi >> 2, t_st, kPurposeResample, 0), rk);
             const uint32_t sel = pi & 3u;
             rw[jj] = sel == 0 ? w.x : sel == 1 ? w.y : sel == 2 ? w.z : w.w;
           }
@@ -258,7 +263,7 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
 #pragma unroll
           for (int t = 0; t < D; ++t) {
             const uint32_t nu = pi * D + t;
-            const uint4 w = philox4x32_10(make_uint4(nu >> 2, n, kPurposePropagate, 0), rk);
+            const uint4 w = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), rk);
             float zz[4];
             normals4(w, zz);
             z[jj * D + t] = zz[nu & 3u];
@@ -315,6 +320,7 @@ __global__ void __launch_bounds__(kBlock) step_butterfly_kernel(const __grid_con
   c.lV_in = p.lV[sc.t & 1u];
   c.lV_out = p.lV[(sc.t & 1u) ^ 1u];
   c.anc = p.anc;
+  c.prec = p.prec;
   c.rk = &p.rk;
   c.mp = &p.model;
   c.g = &p.geom[sc.k];

@@ -41,6 +41,9 @@ def test_device_philox_matches_oracle(bfpf):
     ("global_256", S.lg_scalar(), (256,), 4),
     ("wide_512", S.sv_model(), (512,), 4),
     ("wide_mixed", S.lg_scalar(), (300, 4), 5),
+    # Section 6.1's model: A = I, Q = I, R = I/4 (the diagonal-A and diagonal-Lr fast paths)
+    ("rw7d_paper", S.random_walk(7), (16, 16, 16), 7),
+    ("rw7d_paper_all_digits", S.random_walk(7), (4, 8, 2, 16), 9),
 ])
 def test_lockstep_small(bfpf, case):
     name, model, radices, T = case
