@@ -20,8 +20,10 @@
 //
 // Integer resampling rule (shared with the oracle): delta = fp32(lw - max),
 // e = exp(delta), q = floor(e 2^24), P = inclusive prefix, Q = P_{A-1},
-// u = floor(r Q / 2^32), ancestor = #{j : P_j <= u}, found with two 16-byte
-// shared-memory loads (bucket pivots P_3, P_7, ..., then the bucket's 4 sums).
+// u = floor(r Q / 2^32), ancestor = #{j : P_j <= u}, found in two 4-ary
+// levels: the bucket from the pivots P_3, P_7, ... (registers when one lane
+// holds the whole group, else one 16-byte shared-memory load), then the
+// bucket's 4 sums from one 16-byte shared-memory load.
 #pragma once
 
 #include "bfpf_device.cuh"
@@ -211,7 +213,7 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
 #pragma unroll
       for (int mm = 0; mm < M; ++mm) row[j * M + mm] = P[mm];
     }
-    if constexpr (PIV > 0) {
+    if constexpr (PIV > 0 && G > 1) {   // one lane per group keeps its pivots in registers
 #pragma unroll
       for (int mm = 0; mm < M; ++mm)
         if (((j * M + mm) & 3u) == 3u) row[A + ((j * M + mm) >> 2)] = P[mm];
@@ -246,6 +248,12 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
 
     // ---- per 4 members: random words (group-major counters), draws, gather, mutate, store ----
     const uint32_t pi0 = g * A + j * M;
+    // Bucket pivots P_3, P_7, ... of a group held whole by one lane.
+    uint32_t piv[PIV > 1 ? PIV - 1 : 1];
+    if constexpr (G == 1 && PIV > 1) {
+#pragma unroll
+      for (int q = 0; q < PIV - 1; ++q) piv[q] = P[4 * q + 3];
+    }
     float xo[M][D];
     uint32_t coff[M];          // ancestor's digit k
 #pragma unroll
@@ -302,23 +310,30 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
       for (int mq = 0; mq < MQ; ++mq) {
         const int mm = 4 * q4 + mq;
         const uint32_t u = __umulhi(rw[mq], Q);       // floor(r Q / 2^32)
-        uint32_t c;                                    // #{j : P_j <= u}: 4-ary, two levels
+        // #{j : P_j <= u}: 4-ary, two levels.  Every P_j and u is below 2^29
+        // (at most 32 members of at most 2^24 each), so P_j + ~u = P_j - u - 1
+        // has its top bit set exactly when P_j <= u.
+        const uint32_t nu = ~u;
+        uint32_t c;
         if constexpr (A == 2) {
-          c = (u >= row[0]) ? 1u : 0u;
+          c = (row[0] + nu) >> 31;
         } else {
           uint32_t b = 0;                              // bucket: pivots P_{4b+3} <= u
-          if constexpr (PIV > 0) {
+          if constexpr (G == 1 && PIV > 1) {
+#pragma unroll
+            for (int q = 0; q < PIV - 1; ++q) b += (piv[q] + nu) >> 31;
+          } else if constexpr (PIV > 0) {
 #pragma unroll
             for (int q = 0; q < PIV / 4 + (PIV % 4 ? 1 : 0); ++q) {
               const uint4 pv = *reinterpret_cast<const uint4*>(row + A + 4 * q);
               const uint32_t pvs[4] = {pv.x, pv.y, pv.z, pv.w};
 #pragma unroll
               for (int e = 0; e < 4; ++e)
-                if (4 * q + e < PIV - 1) b += (u >= pvs[e]) ? 1u : 0u;
+                if (4 * q + e < PIV - 1) b += (pvs[e] + nu) >> 31;
             }
           }
           const uint4 v = *reinterpret_cast<const uint4*>(row + 4 * b);
-          c = 4 * b + ((u >= v.x) ? 1u : 0u) + ((u >= v.y) ? 1u : 0u) + ((u >= v.z) ? 1u : 0u);
+          c = 4 * b + ((v.x + nu) >> 31) + ((v.y + nu) >> 31) + ((v.z + nu) >> 31);
         }
         if (Q == 0) c = j * M + mm;                    // an all-zero group keeps its particles
         float xh[D];
