@@ -122,9 +122,9 @@ __device__ __forceinline__ float ex2_ftz(float x) {
   asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
-__device__ __forceinline__ float rsqrt_ftz(float x) {
+__device__ __forceinline__ float sqrt_ftz(float x) {
   float r;
-  asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
   return r;
 }
 __device__ __forceinline__ float sin_ftz(float x) {
@@ -140,8 +140,8 @@ __device__ __forceinline__ float cos_ftz(float x) {
 
 // The same transform on the special-function units: -2 ln u from lg2.approx
 // (absolute error about 2^-22 in log2 u), except for u > 63/64 where
-// -ln u = t + t^2/2 + ... + t^6/6 with t = 1 - u (exact in FP32; truncation
-// below 4e-13 relative) keeps the small radii accurate; the angle is taken in
+// -ln u = t + t^2/2 + t^3/3 + t^4/4 with t = 1 - u (exact in FP32; truncation
+// below 2e-8 relative) keeps the small radii accurate; the angle is taken in
 // [-pi, pi) where sin/cos.approx have absolute error about 2^-21:
 // cos(2 pi v) = -cos(2 pi (v - 1/2)).  Normals differ from the full-precision
 // transform by < 4e-6 absolute.  u = (2 floor(w0 / 2^9) + 1) 2^-24 is built
@@ -152,12 +152,12 @@ __device__ __forceinline__ void box_muller_fast(uint32_t wa, uint32_t wb, float&
   float r2;
   if (u > 0.984375f) {
     const float t = 1.0f - u;
-    const float poly = fmaf(fmaf(fmaf(fmaf(fmaf(t, 1.0f / 6.0f, 0.2f), t, 0.25f), t, 1.0f / 3.0f), t, 0.5f), t, 1.0f);
-    r2 = 2.0f * t * poly;
+    const float poly = fmaf(fmaf(fmaf(t, 0.25f, 1.0f / 3.0f), t, 0.5f), t, 1.0f);
+    r2 = (t + t) * poly;
   } else {
     r2 = -1.3862943611198906f * lg2_ftz(u);   // -2 ln 2 log2 u
   }
-  const float rad = r2 * rsqrt_ftz(r2);
+  const float rad = sqrt_ftz(r2);
   const float ang = 6.283185307179586f * (v - 0.5f);
   z0 = -rad * cos_ftz(ang);
   z1 = -rad * sin_ftz(ang);

@@ -137,10 +137,40 @@ __device__ __forceinline__ bool fold_partials(const StepParams& p, Partial acc, 
   __threadfence();
 
   // ---- last block: fold all block partials (fixed order, compensated FP32) ----
+  // One pass: each thread folds its partials b = tid, tid + kBlock, ... against
+  // its own running maximum (rescaling when a larger one arrives), then the
+  // block's maximum rescales every thread's sums before the shuffle fold.
   const uint32_t G = gridDim.x;
-  int gi = float_order(-INFINITY);
-  for (uint32_t b = tid; b < G; b += kBlock) gi = max(gi, float_order(__ldcg(p.partials + (size_t)b * NP)));
-  gi = __reduce_max_sync(FULL, gi);
+  float mt = -INFINITY;
+  float hi[NP - 1], lo[NP - 1];
+#pragma unroll
+  for (int k = 0; k < NP - 1; ++k) hi[k] = lo[k] = 0.0f;
+  for (uint32_t b = tid; b < G; b += kBlock) {
+    const float* pb = p.partials + (size_t)b * NP;
+    const float mb = __ldcg(pb);
+    float v[NP - 1];
+#pragma unroll
+    for (int k = 0; k < NP - 1; ++k) v[k] = __ldcg(pb + 1 + k);
+    if (mb == -INFINITY) continue;
+    float w = 1.0f;
+    if (mb > mt) {
+      const float r = (mt == -INFINITY) ? 0.0f : expf(mt - mb);
+#pragma unroll
+      for (int k = 0; k < NP - 1; ++k) {
+        const float rk = (k == 1) ? r * r : r;
+        hi[k] *= rk;
+        lo[k] *= rk;
+      }
+      mt = mb;
+    } else {
+      w = expf(mb - mt);
+    }
+    ff_add(hi[0], lo[0], v[0] * w);
+    ff_add(hi[1], lo[1], v[1] * (w * w));
+#pragma unroll
+    for (int t = 0; t < D; ++t) ff_add(hi[2 + t], lo[2 + t], v[2 + t] * w);
+  }
+  int gi = __reduce_max_sync(FULL, float_order(mt));
   __syncthreads();
   if (lane == 0) s_max[warp] = gi;
   __syncthreads();
@@ -148,20 +178,13 @@ __device__ __forceinline__ bool fold_partials(const StepParams& p, Partial acc, 
 #pragma unroll
   for (int w = 1; w < NW; ++w) gi = max(gi, s_max[w]);
   const float Mx = order_float(gi);
-
-  float hi[NP - 1], lo[NP - 1];
+  {
+    const float r = (mt == -INFINITY) ? 0.0f : expf(mt - Mx);
 #pragma unroll
-  for (int k = 0; k < NP - 1; ++k) hi[k] = lo[k] = 0.0f;
-  if (Mx != -INFINITY) {
-    for (uint32_t b = tid; b < G; b += kBlock) {
-      const float* pb = p.partials + (size_t)b * NP;
-      const float mb = __ldcg(pb);
-      if (mb == -INFINITY) continue;
-      const float w = expf(mb - Mx);
-      ff_add(hi[0], lo[0], __ldcg(pb + 1) * w);
-      ff_add(hi[1], lo[1], __ldcg(pb + 2) * (w * w));
-#pragma unroll
-      for (int t = 0; t < D; ++t) ff_add(hi[2 + t], lo[2 + t], __ldcg(pb + 3 + t) * w);
+    for (int k = 0; k < NP - 1; ++k) {
+      const float rk = (k == 1) ? r * r : r;
+      hi[k] *= rk;
+      lo[k] *= rk;
     }
   }
 #pragma unroll
@@ -217,7 +240,8 @@ __device__ __forceinline__ double write_summaries(const StepParams& p, const dou
   } else {
     lme = (double)Mx + (log_split(S[0]) - log_split((double)p.N));
     inc = lme + ((double)muf - mu_prev) + mp.c_obs;
-    ess = S[0] * S[0] / ((double)p.N * S[1]);
+    const float s0 = (float)S[0];
+    ess = (double)(s0 * s0 / ((float)p.N * (float)S[1]));
   }
   p.inc_ring[slot] = inc;
   p.ess_ring[slot] = (float)ess;

@@ -62,8 +62,9 @@ def test_lg8d_full_size_against_kalman(bfpf):
     """The 8-dimensional linear-Gaussian workload at full size (N = 2^20, T = 1000)
     against the exact Kalman filter.  The likelihood estimate is unbiased in p^,
     so over independent filter seeds the error of log p^ has mean about -Var/2
-    (measured: standard deviation about 1.5 for global resampling and 1.7 for all
-    stages per step, means -1.3 to -1.8); checked over six seeds, with the summed
+    (measured over 16 seeds: standard deviation 1.6 to 1.9 for global resampling,
+    means -1.9 to -2.2); checked over twelve seeds against the uncertainty of both
+    the mean and the half-variance (sd of s^2 / 2 = s^2 / sqrt(2 (n - 1))), with the summed
     squared error of the filtering means (about 4) bounded per run.  The
     one-digit schedule's error is reported, not bounded: it carries weights
     between steps, and sharp 8-dimensional likelihoods make them degenerate
@@ -73,8 +74,8 @@ def test_lg8d_full_size_against_kalman(bfpf):
     y = w.observations()
     kf = kalman.kalman_filter(w.model, y)
     res = {}
-    for name, rad, kw, seeds in (("one_digit", w.radices, {}, 1), ("all_stages", w.radices, {"all_stages": True}, 6),
-                                 ("global", (w.N,), {}, 6)):
+    for name, rad, kw, seeds in (("one_digit", w.radices, {}, 1), ("all_stages", w.radices, {"all_stages": True}, 12),
+                                 ("global", (w.N,), {}, 12)):
         errs, mse = [], []
         for r in range(seeds):
             f = bfpf.ButterflyFilter(w.model, w.N, rad, w.filter_seed + 101 * r, **kw)
@@ -86,7 +87,9 @@ def test_lg8d_full_size_against_kalman(bfpf):
     print("lg8d vs Kalman (loglik errors, summed squared mean errors)", res)
     for name in ("all_stages", "global"):
         err, mse = res[name]
-        se = err.std(ddof=1) / np.sqrt(len(err))
-        assert abs(err.mean() + 0.5 * err.var(ddof=1)) < 4 * se + 0.1, (name, err)
+        n = len(err)
+        var = err.var(ddof=1)
+        se = np.sqrt(var / n + (0.5 * var) ** 2 * 2.0 / (n - 1))
+        assert abs(err.mean() + 0.5 * var) < 4 * se + 0.1, (name, err)
         assert err.std(ddof=1) < 4.0, (name, err)
         assert np.all(mse < 8.0), (name, mse)
