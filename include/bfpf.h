@@ -161,8 +161,8 @@ typedef struct pf_handle pf_handle;
  * ancestors (4N), per-block partial sums and small rings for observations
  * and per-step outputs; global resampling (radices = {N}, N > 1024) adds a
  * second state buffer (4dN), log-weights (4N), prefix sums (8N), the draws
- * filed by bucket with their uniforms (about 16N) and an overflow list
- * (12N).  opts may be NULL.
+ * filed by bucket as 4-byte indices (about 4N, twice) and two overflow lists
+ * (4N each).  opts may be NULL.
  * Errors: PF_EINVAL (bad model / N / radices, see pf_create).
  */
 pf_status pf_workspace_size(const pf_model* model, int64_t N, const int32_t* radices,

@@ -21,13 +21,14 @@ struct GlobalParams {
   unsigned long long* agg;        // [nscan] scan tile aggregates
   unsigned long long* incl;       // [nscan] scan tile inclusive prefixes
   uint32_t* flag;                 // [nscan] 2n+1: aggregate ready, 2n+2: prefix ready (step n)
-  // A filed draw is one 16-byte entry {i, 0, low and high words of r_i}.
-  uint4* slot;                    // [buckets][cap] draws filed by bucket
+  // A filed draw is its particle index i: the uniform r_i is a function of the
+  // counter (i/2, n, 3, 0), recomputed wherever it is needed.
+  uint32_t* slot;                 // [buckets][cap] draws filed by bucket
   uint32_t* cnt;                  // [buckets + 1] fill counts (zero between steps); last: overflow count
-  uint4* cslot;                   // [2^cbits][ccap] draws filed by coarse bin (top cbits bits of r)
+  uint32_t* cslot;                // [2^cbits][ccap] draws filed by coarse bin (top cbits bits of r)
   uint32_t* ccnt;                 // [2^cbits + 1] coarse fill counts (zero between steps); last: overflow count
-  uint4* covf;                    // [N] draws whose coarse bin was full
-  uint4* ovf;                     // [N] draws whose bucket was full
+  uint32_t* covf;                 // [N] draws whose coarse bin was full
+  uint32_t* ovf;                  // [N] draws whose bucket was full
   uint32_t* jb;                   // [buckets + 1] jb[b] = #{j : P_j <= lowest u of bucket b}
   uint32_t nscan;                 // scan tiles of kScanTile particles
   uint32_t log2b, buckets;        // buckets = 2^log2b

@@ -322,8 +322,8 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     const uint32_t sdc = (uint32_t)std::ceil(std::sqrt((double)muc));
     pl.ccap = small_buckets ? 64u : std::min<uint32_t>(pl.N, muc + 8u * sdc + 64u);
     pl.nseg = (pl.ccap + kRefineSeg - 1) / kRefineSeg;
-    pl.smem_weight = (size_t)16 * kBlock * global_weight_vec(d) + (size_t)8 * (1u << pl.cbits);
-    pl.smem_refine = (size_t)16 * kRefineSeg + (size_t)8 * (1u << (pl.log2b - pl.cbits));
+    pl.smem_weight = (size_t)8 * kBlock * global_weight_vec(d) + (size_t)8 * (1u << pl.cbits);
+    pl.smem_refine = (size_t)8 * kRefineSeg + (size_t)8 * (1u << (pl.log2b - pl.cbits));
     pl.smem_resolve = (size_t)8 * global_stage_alloc(d) + (size_t)4 * d * (global_stage_alloc(d) + 1u);
     DigitGeom& g = pl.geom[0];
     g.a = pl.N;
@@ -575,12 +575,12 @@ pf_status finish_plan_global(Plan& pl, const pf_options* opts, int sms, std::str
   L.ess_ring = take((size_t)4 * kRing);
   L.lw = take((size_t)4 * pl.N);
   L.P = take((size_t)8 * pl.N);
-  L.slot = take((size_t)16 * pl.buckets * pl.bucket_cap);
+  L.slot = take((size_t)4 * pl.buckets * pl.bucket_cap);
   L.cnt = take((size_t)4 * (pl.buckets + 1u));
-  L.cslot = take((size_t)16 * (1u << pl.cbits) * pl.ccap);
+  L.cslot = take((size_t)4 * (1u << pl.cbits) * pl.ccap);
   L.ccnt = take((size_t)4 * ((1u << pl.cbits) + 1u));
-  L.covf = take((size_t)16 * pl.N);
-  L.ovf = take((size_t)16 * pl.N);
+  L.covf = take((size_t)4 * pl.N);
+  L.ovf = take((size_t)4 * pl.N);
   L.jb = take((size_t)4 * (pl.buckets + 1u));
   L.agg = take((size_t)8 * pl.nscan);
   L.incl = take((size_t)8 * pl.nscan);
@@ -826,12 +826,12 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
     G.agg = reinterpret_cast<unsigned long long*>(h->ws + L.agg);
     G.incl = reinterpret_cast<unsigned long long*>(h->ws + L.incl);
     G.flag = reinterpret_cast<uint32_t*>(h->ws + L.flag);
-    G.slot = reinterpret_cast<uint4*>(h->ws + L.slot);
+    G.slot = reinterpret_cast<uint32_t*>(h->ws + L.slot);
     G.cnt = reinterpret_cast<uint32_t*>(h->ws + L.cnt);
-    G.ovf = reinterpret_cast<uint4*>(h->ws + L.ovf);
-    G.cslot = reinterpret_cast<uint4*>(h->ws + L.cslot);
+    G.ovf = reinterpret_cast<uint32_t*>(h->ws + L.ovf);
+    G.cslot = reinterpret_cast<uint32_t*>(h->ws + L.cslot);
     G.ccnt = reinterpret_cast<uint32_t*>(h->ws + L.ccnt);
-    G.covf = reinterpret_cast<uint4*>(h->ws + L.covf);
+    G.covf = reinterpret_cast<uint32_t*>(h->ws + L.covf);
     G.jb = reinterpret_cast<uint32_t*>(h->ws + L.jb);
     G.cbits = pl.cbits;
     G.ccap = pl.ccap;

@@ -10,12 +10,13 @@
 // counter (i/2, n, 3, 0), ancestor = #{j : P_j <= u_i}.  Six kernels:
 //   1. weights: lw_i to memory, block partials -> last block: likelihood
 //      increment, mean, ESS, the global maximum and the one group's weight;
-//      every draw (i, r_i) is also filed under its coarse bin (the top cbits
-//      bits of r_i), counted per chunk of particles in shared memory so that
-//      one global atomic reserves a run of slots per bin and chunk;
+//      every draw (its index i) is also filed under its coarse bin (the top
+//      cbits bits of r_i), counted per chunk of particles in shared memory so
+//      that one global atomic reserves a run of slots per bin and chunk;
 //   2. refine: the same per coarse bin, filing every draw under its bucket
 //      b = top log2b bits of r_i (fixed capacity per bucket, an overflow list
-//      behind it);
+//      behind it); r_i is recomputed from its counter, so a filed draw is
+//      only its 4-byte index;
 //   3. scan: single-pass decoupled look-back prefix sum of q (tiles handed
 //      out by an atomic ticket so a tile only waits on tiles already running;
 //      waits are bounded and report kStatusTimeout), loads and stores staged
@@ -29,7 +30,7 @@
 //      kernels 1 and 2), gathers and mutates, and writes the particle's new
 //      state; a
 //      bucket whose index range is longer than the staging buffer, and the
-//      overflow list, search P in global memory;
+//      overflow list, search P in global memory (r_i again from its counter);
 //   6. advance: one thread clears the overflow counts and advances n.
 // Every particle's ancestor is #{j : P_j <= u_i} whatever the bucket layout:
 // bucketing only decides where the count is taken.
@@ -61,37 +62,34 @@ __device__ __forceinline__ uint32_t bucket_of(unsigned long long r, uint32_t log
   return log2b ? (uint32_t)(r >> (64u - log2b)) : 0u;
 }
 
-// A filed draw: one 16-byte entry {i, 0, low and high words of r_i}.
-__device__ __forceinline__ uint4 draw_entry(uint32_t i, unsigned long long r) {
-  return make_uint4(i, 0u, (uint32_t)r, (uint32_t)(r >> 32));
-}
-__device__ __forceinline__ unsigned long long entry_r(uint4 e) {
-  return ((unsigned long long)e.w << 32) | e.z;
+// The 64-bit uniform of particle i's draw at step n: words (2(i%2), 2(i%2)+1)
+// of the Philox block with counter (i/2, n, 3, 0).
+__device__ __forceinline__ unsigned long long draw_uniform(const StepParams& p, uint32_t i, uint32_t n) {
+  const uint4 w = philox4x32(make_uint4(i >> 1, n, kPurposeResampleWide, 0), p.rk);
+  return (i & 1u) ? (((unsigned long long)w.w << 32) | w.z) : (((unsigned long long)w.y << 32) | w.x);
 }
 
-// File draw (i, r) straight into its bucket (or the overflow list): the path
-// of the rare draws whose coarse bin was full.
-__device__ __forceinline__ void file_direct(const GlobalParams& gp, uint4 e) {
-  const uint32_t b = bucket_of(entry_r(e), gp.log2b);
+// File draw i straight into its bucket (or the overflow list): the path of the
+// rare draws whose coarse bin was full.
+__device__ __forceinline__ void file_direct(const StepParams& p, const GlobalParams& gp, uint32_t i, uint32_t n) {
+  const uint32_t b = bucket_of(draw_uniform(p, i, n), gp.log2b);
   const uint32_t pos = atomicAdd(gp.cnt + b, 1u);
-  if (pos < gp.cap) gp.slot[(size_t)b * gp.cap + pos] = e;
-  else gp.ovf[atomicAdd(gp.cnt + gp.buckets, 1u)] = e;
+  if (pos < gp.cap) gp.slot[(size_t)b * gp.cap + pos] = i;
+  else gp.ovf[atomicAdd(gp.cnt + gp.buckets, 1u)] = i;
 }
 
-// File one block's chunk of draws (thread t holds V of them: index i, uniform
-// r, bin = bin_of(r), valid) into nbins bins of capacity cap: dst[bin * cap +
-// pos], pos reserved from gcnt[bin]; a draw whose bin is full goes to
-// ovf[*ovf_cnt++].
+// File one block's chunk of draws (thread t holds V of them: index i, bin,
+// valid) into nbins bins of capacity cap: dst[bin * cap + pos] = i, pos
+// reserved from gcnt[bin]; a draw whose bin is full goes to ovf[*ovf_cnt++].
 // The chunk is counted per bin in shared memory, each non-empty bin reserves
 // its run with one global atomic, and the draws are ordered by bin in shared
 // memory first so that consecutive threads write consecutive slots.
-// Shared memory: s_cnt[nbins], s_off[nbins], s_buf[kBlock * V].
-template <int V, class BinOf>
-__device__ __forceinline__ void file_chunk(const uint32_t (&i)[V], const unsigned long long (&r)[V],
-                                           const uint32_t (&bin)[V], const bool (&valid)[V], BinOf bin_of,
-                                           uint32_t nbins, uint32_t* gcnt, uint4* dst, uint32_t cap,
-                                           uint32_t* ovf_cnt, uint4* ovf, uint32_t* s_cnt, uint32_t* s_off,
-                                           uint4* s_buf) {
+// Shared memory: s_cnt[nbins], s_off[nbins], s_buf[kBlock * V] of {i, bin}.
+template <int V>
+__device__ __forceinline__ void file_chunk(const uint32_t (&i)[V], const uint32_t (&bin)[V], const bool (&valid)[V],
+                                           uint32_t nbins, uint32_t* gcnt, uint32_t* dst, uint32_t cap,
+                                           uint32_t* ovf_cnt, uint32_t* ovf, uint32_t* s_cnt, uint32_t* s_off,
+                                           uint2* s_buf) {
   constexpr int NW = kBlock / 32;
   __shared__ uint32_t s_wsum[NW];
   __shared__ uint32_t s_total;
@@ -137,15 +135,15 @@ __device__ __forceinline__ void file_chunk(const uint32_t (&i)[V], const unsigne
   __syncthreads();
 #pragma unroll
   for (int j = 0; j < V; ++j)
-    if (valid[j]) s_buf[s_off[bin[j]] + rank[j]] = draw_entry(i[j], r[j]);
+    if (valid[j]) s_buf[s_off[bin[j]] + rank[j]] = make_uint2(i[j], bin[j]);
   __syncthreads();
   const uint32_t total = s_total;
   for (uint32_t k = tid; k < total; k += kBlock) {
-    const uint4 e = s_buf[k];
-    const uint32_t b = bin_of(entry_r(e));
+    const uint2 e = s_buf[k];
+    const uint32_t b = e.y;
     const uint32_t pos = s_cnt[b] + (k - s_off[b]);
-    if (pos < cap) dst[(size_t)b * cap + pos] = e;
-    else ovf[atomicAdd(ovf_cnt, 1u)] = e;
+    if (pos < cap) dst[(size_t)b * cap + pos] = e.x;
+    else ovf[atomicAdd(ovf_cnt, 1u)] = e.x;
   }
   __syncthreads();                                 // the caller reuses the shared buffers
 }
@@ -159,7 +157,7 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
   constexpr int V = global_weight_vec(D);
   constexpr uint32_t CH = kBlock * V;
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  uint4* const s_buf = reinterpret_cast<uint4*>(s_dyn);                 // [CH]
+  uint2* const s_buf = reinterpret_cast<uint2*>(s_dyn);                 // [CH]
   uint32_t* const s_cnt = reinterpret_cast<uint32_t*>(s_buf + CH);      // [2^cbits]
   const ModelParams& mp = p.model;
   DevState* st = p.st;
@@ -233,22 +231,19 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
     }
     // uniforms (pairs of particles share a Philox block) and their coarse bins
     uint32_t ii[V], cb[V];
-    unsigned long long r[V];
     bool valid[V];
 #pragma unroll
     for (int h = 0; h < V / 2; ++h) {
       const uint4 w = philox4x32(make_uint4(i0 / 2u + h, n, kPurposeResampleWide, 0), p.rk);
-      r[2 * h] = ((unsigned long long)w.y << 32) | w.x;
-      r[2 * h + 1] = ((unsigned long long)w.w << 32) | w.z;
+      cb[2 * h] = bucket_of(((unsigned long long)w.y << 32) | w.x, cbits);
+      cb[2 * h + 1] = bucket_of(((unsigned long long)w.w << 32) | w.z, cbits);
     }
 #pragma unroll
     for (int j = 0; j < V; ++j) {
       ii[j] = i0 + j;
-      cb[j] = bucket_of(r[j], cbits);
       valid[j] = i0 + j < N;
     }
-    file_chunk<V>(ii, r, cb, valid, [cbits](unsigned long long rr) { return bucket_of(rr, cbits); }, nbins,
-                  gp.ccnt, gp.cslot, gp.ccap, gp.ccnt + nbins, gp.covf, s_cnt, s_off, s_buf);
+    file_chunk<V>(ii, cb, valid, nbins, gp.ccnt, gp.cslot, gp.ccap, gp.ccnt + nbins, gp.covf, s_cnt, s_off, s_buf);
   }
   const Sched sc{n, n, 0u, true, true};   // one digit (m = 1): every step is one whole stage
   finish_step<D, false>(p, acc, accx, sc, status, muf, p.lV[(n & 1u) ^ 1u]);
@@ -260,9 +255,10 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
 __global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_constant__ StepParams p,
                                                               const __grid_constant__ GlobalParams gp) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
-  uint4* const s_buf = reinterpret_cast<uint4*>(s_dyn);                 // [kRefineSeg]
+  uint2* const s_buf = reinterpret_cast<uint2*>(s_dyn);                 // [kRefineSeg]
   uint32_t* const s_cnt = reinterpret_cast<uint32_t*>(s_buf + kRefineSeg);
   const uint32_t tid = threadIdx.x;
+  const uint32_t n = p.st->n;
   const uint32_t cbits = gp.cbits, fbits = gp.log2b - cbits, nfine = 1u << fbits;
   uint32_t* const s_off = s_cnt + nfine;
   const uint32_t cb = blockIdx.x / gp.nseg, sg = blockIdx.x % gp.nseg;
@@ -271,26 +267,23 @@ __global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_cons
   if (e0 < cfill) {                                // block-uniform
     const size_t cbase = (size_t)cb * gp.ccap;
     uint32_t ii[kRefineItems], fb[kRefineItems];
-    unsigned long long rr[kRefineItems];
     bool valid[kRefineItems];
 #pragma unroll
     for (int q = 0; q < kRefineItems; ++q) {
       const uint32_t e = e0 + q * kBlock + tid;
       valid[q] = e < cfill;
-      const uint4 en = valid[q] ? __ldcs(gp.cslot + cbase + e) : make_uint4(0, 0, 0, 0);
-      ii[q] = en.x;
-      rr[q] = entry_r(en);
-      fb[q] = bucket_of(rr[q], gp.log2b) & (nfine - 1u);
+      ii[q] = valid[q] ? __ldcs(gp.cslot + cbase + e) : 0u;
     }
+#pragma unroll
+    for (int q = 0; q < kRefineItems; ++q)
+      fb[q] = valid[q] ? (bucket_of(draw_uniform(p, ii[q], n), gp.log2b) & (nfine - 1u)) : 0u;
     const size_t b0 = (size_t)cb << fbits;         // this coarse bin's first bucket
-    const uint32_t log2b = gp.log2b, fmask = nfine - 1u;
-    file_chunk<kRefineItems>(ii, rr, fb, valid,
-                             [log2b, fmask](unsigned long long r) { return bucket_of(r, log2b) & fmask; }, nfine,
-                             gp.cnt + b0, gp.slot + b0 * gp.cap, gp.cap, gp.cnt + gp.buckets, gp.ovf, s_cnt, s_off,
-                             s_buf);
+    file_chunk<kRefineItems>(ii, fb, valid, nfine, gp.cnt + b0, gp.slot + b0 * gp.cap, gp.cap, gp.cnt + gp.buckets,
+                             gp.ovf, s_cnt, s_off, s_buf);
   }
   const uint32_t nco = __ldcg(gp.ccnt + (1u << cbits));
-  for (uint32_t e = blockIdx.x * kBlock + tid; e < nco; e += gridDim.x * kBlock) file_direct(gp, __ldcg(gp.covf + e));
+  for (uint32_t e = blockIdx.x * kBlock + tid; e < nco; e += gridDim.x * kBlock)
+    file_direct(p, gp, __ldcg(gp.covf + e), n);
 }
 
 __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_constant__ StepParams p,
@@ -466,14 +459,13 @@ __global__ void __launch_bounds__(kBlock) global_bounds_kernel(const __grid_cons
 // global memory.
 template <int D, int KIND>
 __device__ __forceinline__ void resolve_draw(const StepParams& p, const GlobalParams& gp, const float* __restrict__ Xin,
-                                             float* __restrict__ Xout, unsigned long long Q, uint32_t n, uint4 en,
+                                             float* __restrict__ Xout, unsigned long long Q, uint32_t n, uint32_t i,
                                              bool staged, uint32_t lo, uint32_t len,
                                              const unsigned long long* sP, const float* sX) {
   constexpr uint32_t SC = global_stage_alloc(D);
   static_assert((SC & (SC - 1)) == 0, "staging buffer must hold a power of two of indices");
   const uint32_t N = p.N;
-  const uint32_t i = en.x;
-  const unsigned long long r = entry_r(en);
+  const unsigned long long r = draw_uniform(p, i, n);
   uint32_t anc = i;                                // an all-zero population keeps its particles
   float xh[D];
   if (Q != 0) {
@@ -539,7 +531,7 @@ __global__ void __launch_bounds__(kBlock) global_resolve_kernel(const __grid_con
   // the first draw of every thread is loaded before the staging, so that the
   // two latencies overlap
   const bool first = tid < filled;
-  const uint4 e_first = first ? __ldcs(gp.slot + s0 + tid) : make_uint4(0, 0, 0, 0);
+  const uint32_t e_first = first ? __ldcs(gp.slot + s0 + tid) : 0u;
   if (staged) {
     const uint32_t p2 = 1u << (32 - __clz(len));   // power of two above len (<= SC)
     for (uint32_t j = tid; j < p2; j += kBlock) sP[j] = (j < len) ? __ldcg(gp.P + lo + j) : ~0ull;
@@ -554,13 +546,13 @@ __global__ void __launch_bounds__(kBlock) global_resolve_kernel(const __grid_con
   }
   if (first) resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, e_first, staged, lo, len, sP, sX);
   for (uint32_t e = tid + kBlock; e < filled; e += kBlock) {
-    const uint4 en = __ldcs(gp.slot + s0 + e);
-    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, en, staged, lo, len, sP, sX);
+    const uint32_t i = __ldcs(gp.slot + s0 + e);
+    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, staged, lo, len, sP, sX);
   }
   const uint32_t nov = __ldcg(gp.cnt + gp.buckets);
   for (uint32_t e = b * kBlock + tid; e < nov; e += gridDim.x * kBlock) {
-    const uint4 en = __ldcg(gp.ovf + e);
-    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, en, false, 0u, N, sP, sX);
+    const uint32_t i = __ldcg(gp.ovf + e);
+    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, false, 0u, N, sP, sX);
   }
 }
 
