@@ -372,86 +372,156 @@ def serving_leg(dev, n_requests=160, rate=40.0):
     return out
 
 
-def equal_error_leg(bf, w, dev, T=100, seed0=50_000):
-    """Filter-mean MSE (Section 6.1: sum over steps and components, mean over runs)
-    against the number of particles, for the butterfly (radix 16) and the global-
-    resampling filter on the same observations, and the time per step of each.
-    Reference mean: average of R = 4 independent global runs at N = 2^25; the
-    reference's own error (the runs' squared spread / (R - 1), divided by R for
-    their average) is subtracted.  Four runs per N for both methods."""
+def _kalman_reference(model, y):
+    """Kalman filtering means E[X_n | y_0..n] and the log-likelihood of a
+    linear-Gaussian model (measurement reference only)."""
+    import numpy as np
+    A, H = model.A, model.H
+    Q, R = model.Lq @ model.Lq.T, model.Lr @ model.Lr.T
+    m, P = model.m0.copy(), model.L0 @ model.L0.T
+    means = np.empty((len(y), model.d))
+    ll = 0.0
+    for n in range(len(y)):                       # prediction, then update
+        if n > 0:
+            m, P = A @ m, A @ P @ A.T + Q
+        Sv = H @ P @ H.T + R
+        r = y[n] - H @ m
+        ll += -0.5 * (r @ np.linalg.solve(Sv, r) + np.linalg.slogdet(2 * np.pi * Sv)[1])
+        K = P @ H.T @ np.linalg.inv(Sv)
+        m, P = m + K @ r, (np.eye(len(m)) - K @ H) @ P
+        means[n] = m
+    return means, ll
+
+
+def _sv_grid_reference(model, y, G=1024, width=8.0):
+    """Filtering means and log-likelihood of the stochastic-volatility model by a
+    point-mass grid filter on [-width s, width s], s the stationary standard
+    deviation (measurement reference only; G = 1024 agrees with G = 4096 to 1e-6)."""
+    import numpy as np
+    s = model.sigma / np.sqrt(1.0 - model.phi ** 2)
+    xg = np.linspace(-width * s, width * s, G)
+    dx = xg[1] - xg[0]
+    K = np.exp(-0.5 * ((xg[:, None] - model.phi * xg[None, :]) / model.sigma) ** 2) / (
+        np.sqrt(2 * np.pi) * model.sigma) * dx
+    p = np.exp(-0.5 * (xg / s) ** 2)
+    p /= p.sum()
+    means = np.empty((len(y), 1))
+    ll = 0.0
+    for n in range(len(y)):
+        if n > 0:
+            p = K @ p
+        var = model.beta ** 2 * np.exp(xg)
+        p = p * np.exp(-0.5 * y[n, 0] ** 2 / var) / np.sqrt(2 * np.pi * var)
+        c = p.sum()
+        ll += np.log(c)
+        p /= c
+        means[n, 0] = xg @ p
+    return means, ll
+
+
+def _radix_digits(N: int, a: int):
+    """Radix-a digits (plus one smaller digit) whose product is N (powers of two)."""
+    out, rem = [], N
+    while rem >= a:
+        out.append(a)
+        rem //= a
+    if rem > 1:
+        out.append(rem)
+    return tuple(out)
+
+
+def _equal_error_config(bf, dev, name, model, y, ref_mean, Ns, gNs, radix, island_M, R, seed0):
+    """MSE of the filtering means against the reference (Section 6.1: sum over steps
+    and components; mean over R seeds) and time per step, for every schedule and for
+    global resampling, then each schedule's speed-up at equal error."""
     import numpy as np
     import torch
+    T = len(y)
+    yd = torch.tensor(y.astype(np.float32), device=dev)
+    scheds = [
+        ("one_digit", lambda N: _radix_digits(N, radix), {}),
+        ("all_stages", lambda N: _radix_digits(N, radix), {"all_stages": True}),
+        ("adaptive_0.5", lambda N: _radix_digits(N, radix), {"adaptive": True, "ess_threshold": 0.5}),
+        ("airpf", lambda N: (island_M, N // island_M), {"islands": "modified"}),
+        ("global", lambda N: (N,), {}),
+    ]
+    res = {}
+    for sname, rad, kw in scheds:
+        rows = {"N": [], "mse": [], "mse_se": [], "ms_per_step": []}
+        for N in (gNs if sname == "global" else Ns):
+            errs, times = [], []
+            for j in range(R):
+                f = bf.ButterflyFilter(model, N, rad(N), seed0 + 1000 * j + N % 997, device=dev, **kw)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                torch.cuda.synchronize(dev)
+                e0.record(f.stream)
+                out = f.run(yd)
+                e1.record(f.stream)
+                torch.cuda.synchronize(dev)
+                times.append(e0.elapsed_time(e1) / T)
+                errs.append(float(np.sum((out["mean"].double().cpu().numpy() - ref_mean) ** 2)))
+                f.close()
+            rows["N"].append(N)
+            rows["mse"].append(float(np.mean(errs)))
+            rows["mse_se"].append(float(np.std(errs, ddof=1) / np.sqrt(R)))
+            rows["ms_per_step"].append(float(np.median(times)))
+        res[sname] = rows
+    # equal error: the global filter's N at a schedule's MSE, from a log-log fit of the
+    # global points, accepted only inside the measured global range (no extrapolation)
+    gN, gm, gt = (np.array(res["global"][k], dtype=float) for k in ("N", "mse", "ms_per_step"))
+    fit = np.polyfit(np.log(gN), np.log(gm), 1)
+    speedups = {}
+    for sname in ("one_digit", "all_stages", "adaptive_0.5", "airpf"):
+        rows = res[sname]
+        pts = []
+        for N, mse, t in zip(rows["N"], rows["mse"], rows["ms_per_step"]):
+            lN = (np.log(mse) - fit[1]) / fit[0]
+            if lN < np.log(gN[0]):
+                pts.append({"N": N, "global_N_at_equal_mse": None, "speedup": None,
+                            "note": f"the global filter is as accurate with fewer than {int(gN[0])} particles; "
+                                    f"speed-up below {float(gt[0] / t):.3g}"})
+            elif lN > np.log(gN[-1]):
+                pts.append({"N": N, "global_N_at_equal_mse": None, "speedup": None,
+                            "note": f"the global filter needs more than {int(gN[-1])} particles; "
+                                    f"speed-up above {float(gt[-1] / t):.3g}"})
+            else:
+                tg = float(np.exp(np.interp(lN, np.log(gN), np.log(gt))))
+                pts.append({"N": N, "global_N_at_equal_mse": float(np.exp(lN)), "speedup": tg / t})
+        best = [q for q in pts if q["speedup"] is not None]
+        speedups[sname] = {"points": pts, "at_largest_N": best[-1] if best else pts[-1]}
+    return {"T": T, "runs_per_N": R, "schedules": res, "global_mse_slope": float(fit[0]),
+            "equal_error": speedups}
+
+
+def equal_error_leg(bf, dev, R=8):
+    """Butterfly schedules against global resampling at equal filter-mean error on
+    the three workloads: 1-D and 8-D linear-Gaussian against their exact Kalman
+    filters, stochastic volatility against a converged grid filter (Figs 3-4's
+    error-versus-time comparison, MSE as in Section 6.1)."""
     import synthetic as S
-    y = S.simulate(w.model, T, w.data_seed)[1].astype(np.float32)
-
-    def run(N, radices, seed, **kw):
-        f = bf.ButterflyFilter(w.model, N, radices, seed, device=dev, **kw)
-        f.run(y[:4])                                  # graph capture / first touch
-        g = bf.ButterflyFilter(w.model, N, radices, seed, device=dev, **kw)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        yd = torch.tensor(y, device=dev)
-        torch.cuda.synchronize(dev)
-        e0.record(g.stream)
-        r = g.run(yd)
-        e1.record(g.stream)
-        torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / T
-        mean = r["mean"].double().cpu().numpy()
-        f.close()
-        g.close()
-        return mean, ms
-
-    R = 4
-    ref = [run(1 << 25, (1 << 25,), seed0 + 1 + j)[0] for j in range(R)]
-    ref_mean = sum(ref) / R
-    ref_mse = sum(float(np.sum((rk - ref_mean) ** 2)) for rk in ref) / (R - 1) / R   # error of the averaged reference
     out = {}
-    for name, Ns, rad, kw in (("butterfly", [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24], _radix16, {}),
-                              ("butterfly_all_stages", [1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24], _radix16,
-                               {"all_stages": True}),
-                              ("global", [1 << 12, 1 << 14, 1 << 16, 1 << 18, 1 << 20, 1 << 22, 1 << 24],
-                               lambda N: (N,), {})):
-        mses, times = [], []
-        for N in Ns:
-            J = 4
-            errs, ts = [], []
-            for j in range(J):
-                mean, ms = run(N, rad(N), seed0 + 100 * j + N % 97, **kw)
-                errs.append(float(np.sum((mean - ref_mean) ** 2)) - ref_mse)
-                ts.append(ms)
-            mses.append(max(float(np.mean(errs)), 1e-30))
-            times.append(float(np.median(ts)))
-        out[name] = {"N": Ns, "mse": mses, "ms_per_step": times}
-    # equal error: the global filter's N at the butterfly's MSE at the largest N (log-log fits)
-    bN, bm, bt = out["butterfly"]["N"], out["butterfly"]["mse"], out["butterfly"]["ms_per_step"]
-    gN, gm, gt = out["global"]["N"], out["global"]["mse"], out["global"]["ms_per_step"]
-    fit_g = np.polyfit(np.log(gN), np.log(gm), 1)
-    fit_b = np.polyfit(np.log(bN), np.log(bm), 1)
-    target = float(np.exp(np.polyval(fit_b, np.log(bN[-1]))))
-    logN_eq = (np.log(target) - fit_g[1]) / fit_g[0]
-    t_g = float(np.exp(np.interp(logN_eq, np.log(gN), np.log(gt),
-                                 left=None, right=None))) if logN_eq <= np.log(gN[-1]) else \
-        float(np.exp(np.polyval(np.polyfit(np.log(gN[-3:]), np.log(gt[-3:]), 1), logN_eq)))
-    t_b = bt[-1]
+    w = S.workload("lg1d_n1024")
+    y = w.observations()
+    ref, _ = _kalman_reference(w.model, y)
+    out["lg1d_n1024"] = _equal_error_config(bf, dev, "lg1d", w.model, y, ref, [1 << k for k in (6, 8, 10, 12, 14)],
+                                            [1 << k for k in (6, 8, 10, 12, 14, 16)], 2, 16, R, 61_000)
+    out["lg1d_n1024"]["reference"] = "Kalman filter (exact)"
+    w = S.workload("lg8d_n1m")
+    y = w.observations()
+    ref, _ = _kalman_reference(w.model, y)
+    out["lg8d_n1m"] = _equal_error_config(bf, dev, "lg8d", w.model, y, ref, [1 << k for k in (12, 14, 16, 18, 20)],
+                                          [1 << k for k in (8, 10, 12, 14, 16, 18, 20)], 32, 64, R, 62_000)
+    out["lg8d_n1m"]["reference"] = "Kalman filter (exact)"
+    w = S.workload("sv_n16m")
+    T = 500
+    y = S.simulate(w.model, T, w.data_seed)[1]
+    ref, _ = _sv_grid_reference(w.model, y)
+    out["sv_n16m"] = _equal_error_config(bf, dev, "sv", w.model, y, ref, [1 << k for k in (16, 18, 20, 22, 24)],
+                                         [1 << k for k in (12, 14, 16, 18, 20, 22, 24)], 16, 1024, R, 63_000)
+    out["sv_n16m"]["reference"] = "point-mass grid filter, 1024 nodes (converged)"
+    out["sv_n16m"]["note"] = "first 500 of the 2000 observations"
+    return out
 
-    def global_ms_at(mse):                     # the global filter's time per step at a given MSE
-        lN = (np.log(mse) - fit_g[1]) / fit_g[0]
-        if lN <= np.log(gN[-1]):
-            return float(np.exp(np.interp(lN, np.log(gN), np.log(gt))))
-        return float(np.exp(np.polyval(np.polyfit(np.log(gN[-3:]), np.log(gt[-3:]), 1), lN)))
-    aN, am, at = (out["butterfly_all_stages"][k] for k in ("N", "mse", "ms_per_step"))
-    fit_a = np.polyfit(np.log(aN), np.log(am), 1)
-    target_a = float(np.exp(np.polyval(fit_a, np.log(aN[-1]))))
-    all_stages = {"N": aN[-1], "mse": target_a, "ms_per_step": at[-1], "mse_slope": float(fit_a[0]),
-                  "global_ms_per_step_at_equal_mse": global_ms_at(target_a),
-                  "speedup_at_equal_error": global_ms_at(target_a) / at[-1]}
-    return {"T": T, "reference": "mean of 4 global runs at N=2^25, their spread subtracted", "runs_per_N": 4,
-            "butterfly": out["butterfly"], "global": out["global"],
-            "butterfly_all_stages": out["butterfly_all_stages"], "all_stages_at_equal_error": all_stages,
-            "mse_slope": {"butterfly": float(fit_b[0]), "global": float(fit_g[0])},
-            "butterfly_N": bN[-1], "butterfly_mse": target, "global_N_at_equal_mse": float(np.exp(logN_eq)),
-            "butterfly_ms_per_step": t_b, "global_ms_per_step_at_equal_mse": t_g,
-            "speedup_at_equal_error": t_g / t_b}
 
 def _random_walk_kalman_means(y, obs_var):
     """Kalman filtering means E[X_n | y_0..n] of the random walk X_n = X_{n-1} + N(0, I),
@@ -546,20 +616,7 @@ def lg8d_kalman_leg(bf, dev):
     import synthetic as S
     w = S.workload("lg8d_n1m")
     y = w.observations()
-    A, H = w.model.A, w.model.H
-    Q, R = w.model.Lq @ w.model.Lq.T, w.model.Lr @ w.model.Lr.T
-    m, P = w.model.m0.copy(), w.model.L0 @ w.model.L0.T
-    kmean = np.empty((len(y), w.model.d))
-    kll = 0.0
-    for n in range(len(y)):                       # Kalman filter (prediction, then update)
-        if n > 0:
-            m, P = A @ m, A @ P @ A.T + Q
-        Sv = H @ P @ H.T + R
-        r = y[n] - H @ m
-        kll += -0.5 * (r @ np.linalg.solve(Sv, r) + np.linalg.slogdet(2 * np.pi * Sv)[1])
-        K = P @ H.T @ np.linalg.inv(Sv)
-        m, P = m + K @ r, (np.eye(len(m)) - K @ H) @ P
-        kmean[n] = m
+    kmean, kll = _kalman_reference(w.model, y)
     yd = torch.tensor(y.astype(np.float32), device=dev)
     out = {"N": w.N, "T": len(y), "kalman_loglik": kll}
     for name, rad, kw in (("one_digit", w.radices, {}), ("all_stages", w.radices, {"all_stages": True}),
@@ -735,8 +792,8 @@ def ours_main(a):
                         "bucket arrays and the scattered writes of the new states are the global "
                         "method's overhead"}
     eq = None
-    if not a.no_global and not a.no_equal_error and rank == 0 and w.model.kind == "sv" and w.N == (1 << 24):
-        eq = equal_error_leg(bf, w, dev)
+    if not a.no_global and not a.no_equal_error and rank == 0:
+        eq = equal_error_leg(bf, dev)
     batched = None
     if not a.no_batched and rank == 0:
         batched = batched_leg(bf, dev, a.batched_filters, a.batched_steps)
