@@ -64,6 +64,7 @@ def _args():
     p.add_argument("--oracle-n", type=int, default=0, help=argparse.SUPPRESS)
     p.add_argument("--oracle-seconds", type=float, default=12.0, help=argparse.SUPPRESS)
     p.add_argument("--oracle-steps", type=int, default=0, help=argparse.SUPPRESS)
+    p.add_argument("--oracle-procs", type=int, default=1, help=argparse.SUPPRESS)
     return p.parse_args()
 
 
@@ -203,7 +204,10 @@ class ClockSampler:
 # CPU oracle timing (the reference of this build)
 # ---------------------------------------------------------------------------
 def oracle_rate_main(a):
-    """Run in a fresh single-threaded process: FP64 oracle particle-steps/s."""
+    """Run in a fresh process: FP64 oracle particle-steps/s, on one core, or with
+    the groups of every step split over a pool of worker processes."""
+    if a.oracle_procs > 1:
+        return oracle_pool_rate_main(a)
     try:   # one core: the timed baseline is the oracle as it stands, single-threaded
         os.sched_setaffinity(0, {sorted(os.sched_getaffinity(0))[0]})
     except (AttributeError, OSError):
@@ -213,11 +217,7 @@ def oracle_rate_main(a):
     from oracle import bpf
     w = S.workload(a.workload)
     N = a.oracle_n or w.N
-    radices = list(w.radices)
-    while int(np.prod(radices)) > N:        # shrink the top digits for a smaller sample
-        radices[-1] //= 2
-        if radices[-1] == 1:
-            radices.pop()
+    radices = _sample_radices(w.radices, N)
     N = int(np.prod(radices))
     y = w.observations(max(8, a.oracle_steps or 8))
     st = bpf.init_state(w.model, N, w.filter_seed)
@@ -231,10 +231,126 @@ def oracle_rate_main(a):
             break
         if not a.oracle_steps and (el >= a.oracle_seconds or steps >= len(y)):
             break
-    print(json.dumps({"value": N * steps / el, "N": N, "radices": radices, "steps": steps, "seconds": el}))
+    print(json.dumps({"value": N * steps / el, "N": N, "radices": radices, "steps": steps, "seconds": el,
+                      "procs": 1}))
 
 
-def _host_cpu() -> dict:
+def _sample_radices(radices, N):
+    """The workload's radices with the top digits shrunk until their product is <= N."""
+    import numpy as np
+    radices = list(radices)
+    while int(np.prod(radices)) > N:
+        radices[-1] //= 2
+        if radices[-1] == 1:
+            radices.pop()
+    return radices
+
+
+_POOL = {}
+
+
+def _pool_attach(names, N, d):
+    """Worker start-up: the shared state buffers (two ping-pong state arrays and
+    two per-particle carried-weight arrays)."""
+    import numpy as np
+    from multiprocessing import shared_memory
+    shms = [shared_memory.SharedMemory(name=nm) for nm in names]
+    _POOL["shm"] = shms
+    _POOL["x"] = [np.ndarray((N, d), dtype=np.float64, buffer=shms[k].buf) for k in (0, 1)]
+    _POOL["lv"] = [np.ndarray((N,), dtype=np.float64, buffer=shms[k].buf) for k in (2, 3)]
+
+
+def _pool_step(args):
+    """One slice of the groups of step n: the oracle's own per-group step (weights,
+    group log-sum-exp, integer draws, mutation), written into the other buffer;
+    returns the slice's partial sums for the step's summaries."""
+    import numpy as np
+    import synthetic as S
+    from oracle import bpf, butterfly
+    workload, radices, seed, n, mu_used, par, g0, g1 = args
+    w = S.workload(workload)
+    y = w.observations(n + 1)[n]
+    k = n % len(radices)
+    s_k = butterfly.strides(radices)[k]
+    gid = np.arange(g0, g1)
+    groups = np.stack([gid // s_k, gid % s_k], axis=1)
+    x, lv = _POOL["x"][par], _POOL["lv"][par]
+    o = bpf.step_on_groups(w.model, radices, seed, n, x, lv, mu_used, y, groups)
+    idx = o["idx"].reshape(-1)
+    _POOL["x"][par ^ 1][idx] = o["x_next"].reshape(-1, x.shape[1])
+    _POOL["lv"][par ^ 1][idx] = np.repeat(o["lV_new"], radices[k])
+    lw = o["lw"].reshape(-1)
+    m = float(np.max(lw))
+    e = np.exp(lw - m)
+    return m, float(e.sum()), float((e * e).sum()), (e[:, None] * x[idx]).sum(axis=0)
+
+
+def oracle_pool_run(workload: str, N: int, procs: int, steps: int = 0, seconds: float = 0.0):
+    """The oracle's step with its groups split over a pool of `procs` worker
+    processes (states in shared memory); the parent combines the slices' partial
+    sums into the normaliser exactly as the single-process step does.  Runs
+    `steps` steps (or until `seconds` have passed after the first) and returns
+    (states, per-particle carried weights, normaliser, steps timed, seconds)."""
+    import multiprocessing as mp
+    from multiprocessing import shared_memory
+    import numpy as np
+    import synthetic as S
+    from oracle import bpf
+    w = S.workload(workload)
+    radices = _sample_radices(w.radices, N)
+    N = int(np.prod(radices))
+    d = w.model.d
+    st = bpf.init_state(w.model, N, w.filter_seed)
+    shms = [shared_memory.SharedMemory(create=True, size=8 * N * sz) for sz in (d, d, 1, 1)]
+    try:
+        xs = [np.ndarray((N, d), dtype=np.float64, buffer=shms[k].buf) for k in (0, 1)]
+        lvs = [np.ndarray((N,), dtype=np.float64, buffer=shms[k].buf) for k in (2, 3)]
+        xs[0][:] = st.x
+        lvs[0][:] = 0.0
+        ctx = mp.get_context("spawn")
+        with ctx.Pool(procs, initializer=_pool_attach, initargs=([sh.name for sh in shms], N, d)) as pool:
+            mu = 0.0
+            n, t0, el = 0, None, 0.0
+            while True:
+                if n == 1:
+                    t0 = time.perf_counter()      # the first step also starts the workers
+                k = n % len(radices)
+                ng = N // radices[k]
+                cuts = np.linspace(0, ng, procs + 1).astype(np.int64)
+                tasks = [(workload, tuple(radices), w.filter_seed, n, mu, n & 1, int(cuts[j]), int(cuts[j + 1]))
+                         for j in range(procs) if cuts[j + 1] > cuts[j]]
+                parts = pool.map(_pool_step, tasks)
+                M = max(q[0] for q in parts)
+                s1 = sum(q[1] * np.exp(q[0] - M) for q in parts)
+                mu = float(M + np.log(s1 / N))       # next normaliser, as the single-process step
+                n += 1
+                if t0 is not None:
+                    el = time.perf_counter() - t0
+                if steps and n >= steps:
+                    break
+                if not steps and t0 is not None and (el >= seconds or n >= 64):
+                    break
+        return xs[n & 1].copy(), lvs[n & 1].copy(), mu, n - 1, el, radices
+    finally:
+        for sh in shms:
+            sh.close()
+            sh.unlink()
+
+
+def oracle_pool_rate_main(a):
+    import numpy as np
+    import synthetic as S
+    w = S.workload(a.workload)
+    N = a.oracle_n or w.N
+    _, _, _, timed, el, radices = oracle_pool_run(a.workload, N, a.oracle_procs,
+                                                  steps=(a.oracle_steps + 1) if a.oracle_steps else 0,
+                                                  seconds=a.oracle_seconds)
+    N = int(np.prod(radices))
+    print(json.dumps({"value": N * timed / el, "N": N, "radices": radices, "steps": timed, "seconds": el,
+                      "procs": a.oracle_procs}))
+
+
+def _host_cpu(threads: int = 1) -> dict:
     """The host the CPU baseline ran on: logical CPUs and the CPU model."""
     model = platform.processor() or platform.machine()
     try:
@@ -245,13 +361,14 @@ def _host_cpu() -> dict:
                     break
     except OSError:
         pass
-    return {"nproc": os.cpu_count(), "cpu": model, "threads_used": 1}
+    return {"nproc": os.cpu_count(), "cpu": model, "threads_used": threads}
 
 
-def oracle_rate(workload: str, n: int = 0, seconds: float = 12.0, steps: int = 0):
+def oracle_rate(workload: str, n: int = 0, seconds: float = 12.0, steps: int = 0, procs: int = 1):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1")
     cmd = [sys.executable, os.path.abspath(__file__), "--oracle-rate", "--workload", workload,
-           "--oracle-n", str(n), "--oracle-seconds", str(seconds), "--oracle-steps", str(steps)]
+           "--oracle-n", str(n), "--oracle-seconds", str(seconds), "--oracle-steps", str(steps),
+           "--oracle-procs", str(procs)]
     out = subprocess.run(cmd, capture_output=True, text=True, env=env, timeout=1200)
     if out.returncode != 0:
         raise RuntimeError(out.stderr[-2000:])
@@ -264,24 +381,26 @@ def reference_main(a):
         return
     import synthetic as S
     w = S.workload(a.workload)
-    # sample size chosen so that K steps of the oracle (about 1.5e6 particle-steps/s on
-    # one core) take about 100 s: the whole reference run stays within a few minutes
-    budget = 1.5e6 * 100.0 / max(1, a.steps)
+    # The oracle's step with its groups split over one worker process per host core.
+    # Sample size chosen so that K steps (about 1.5e6 particle-steps/s per core) take
+    # about 100 s: the whole reference run stays within a few minutes.
+    procs = max(1, os.cpu_count() or 1)
+    budget = 1.5e6 * procs * 100.0 / max(1, a.steps)
     n_sample = 1 << 10
-    while n_sample * 2 <= min(budget, 1 << 20):
+    while n_sample * 2 <= min(budget, w.N):
         n_sample *= 2
-    n_sample = min(n_sample, w.N)
-    # warm-up steps are included in the sample run's start-up; time K steps
-    r = oracle_rate(a.workload, n=n_sample, steps=max(1, a.steps))
-    sample = (f"first {r['steps']} time steps of {a.workload} with N={r['N']} particles "
-              f"(radices {r['radices']}) on the FP64 numpy oracle, 1 thread")
+    # one untimed step starts the workers; time K steps
+    r = oracle_rate(a.workload, n=n_sample, steps=max(1, a.steps), procs=procs)
+    sample = (f"{r['steps']} time steps of {a.workload} with N={r['N']} particles "
+              f"(radices {r['radices']}) on the FP64 numpy oracle, its groups split over {procs} processes")
     line = {"impl": "reference", "metric": METRIC, "value": r["value"], "unit": METRIC,
             "n_gpus": a.gpus, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": 1000.0 * r["seconds"] / r["steps"], "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": a.workload, "N": w.N, "radices": list(w.radices), "d": w.model.d,
                        "model": w.model.kind, "parallelism": "replicas1"},
-            "cpu_baseline": {"value": r["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "host": _host_cpu(),
+            "cpu_baseline": {"value": r["value"], "unit": METRIC, "cores": procs, "kind": "oracle",
+                             "host": _host_cpu(procs),
                              "sample": sample + f" (a bounded sample of the N = {w.N} workload; "
                                                 "the rate is particle-steps/s, as for the GPU arm)"},
             "e2e": {"value": r["value"], "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -839,13 +958,24 @@ def ours_main(a):
                                     "and the median SM clock sampled during the timed steps"}
     cpu = None
     if not a.no_cpu_baseline:
+        procs = max(1, os.cpu_count() or 1)
         try:
-            r = oracle_rate(a.workload, seconds=12.0)
-            cpu = {"value": r["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "host": _host_cpu(),
-                   "sample": f"first {r['steps']} time steps of {a.workload} at full size "
-                             f"(N={r['N']}) on the FP64 numpy oracle, 1 thread"}
+            r1 = oracle_rate(a.workload, seconds=12.0)
+            single = {"value": r1["value"], "cores": 1,
+                      "sample": f"first {r1['steps']} time steps of {a.workload} at full size "
+                                f"(N={r1['N']}) on the FP64 numpy oracle, 1 thread"}
         except Exception as ex:  # report, never hide
-            cpu = {"value": None, "unit": METRIC, "cores": 1, "kind": "oracle", "sample": f"failed: {ex}"}
+            single = {"value": None, "cores": 1, "sample": f"failed: {ex}"}
+        try:
+            rp = oracle_rate(a.workload, seconds=12.0, procs=procs)
+            cpu = {"value": rp["value"], "unit": METRIC, "cores": procs, "kind": "oracle", "host": _host_cpu(procs),
+                   "sample": f"{rp['steps']} time steps of {a.workload} at full size (N={rp['N']}) on the FP64 "
+                             f"numpy oracle, the groups of every step split over {procs} processes "
+                             "(after one untimed step)",
+                   "single_core": single}
+        except Exception as ex:  # report, never hide
+            cpu = {"value": single["value"], "unit": METRIC, "cores": 1, "kind": "oracle", "host": _host_cpu(),
+                   "sample": single["sample"] + f"; the all-core run failed: {ex}"}
     line = {
         "metric": METRIC, "value": value, "unit": METRIC, "n_gpus": world, "steps": K, "warmup": W,
         "ms_per_step": total_ms / K, "p50_ms": p50_ms, "p99_ms": p99_ms,
