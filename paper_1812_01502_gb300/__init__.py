@@ -380,12 +380,22 @@ class FilterBatch:
     """F independent filters (own model, N, radices, seed) advanced together, one
     kernel launch per time step for the whole batch (pf_batch_*)."""
 
-    def __init__(self, specs, *, chunk_len: int = 0, device=None, stream=None):
-        """specs: sequence of (model, N, radices, seed)."""
+    def __init__(self, specs, *, chunk_len: int = 0, device=None, stream=None, tile: int = 0, unit_work: int = 0,
+                 tune: bool = False):
+        """specs: sequence of (model, N, radices, seed).  tile: particles per tile of
+        the shared-memory tile code (0 = by state dimension); unit_work: work of one
+        thread block in particle-dimensions (a filter's step is split over
+        ceil(N (d + 1) / unit_work) blocks; 0 = the library's default); tune=True
+        takes both from the autotuner (cached per device and batch shape)."""
         torch = _torch()
         lib = load_library()
         if not torch.cuda.is_available():
             raise PFError(PF_ECUDA, "no CUDA device: the butterfly filter runs only on the GPU")
+        if tune:
+            from . import autotune
+            best = autotune.tune_batch(specs, device=device)
+            tile, unit_work = int(best["tile"]), int(best["unit_work"])
+        self.tile, self.unit_work = int(tile), int(unit_work)
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
         self.stream = stream if stream is not None else torch.cuda.current_stream(self.device)
         self.F = len(specs)
@@ -406,7 +416,7 @@ class FilterBatch:
         self._rad = (ctypes.c_int32 * len(flat))(*flat)
         self._m = (ctypes.c_int32 * self.F)(*[len(r) for r in self.radices])
         self._seeds = (ctypes.c_uint64 * self.F)(*[int(s[3]) for s in specs])
-        self._opts = PFOptions(tile=0, chunk_len=int(chunk_len), flags=0, grid=0,
+        self._opts = PFOptions(tile=int(tile), chunk_len=int(chunk_len), flags=0, grid=int(unit_work),
                                stream=ctypes.c_void_p(self.stream.cuda_stream))
         with torch.cuda.device(self.device):
             nbytes = ctypes.c_size_t(0)

@@ -1,4 +1,4 @@
-"""Autotuner for the launch configuration of a filter.
+"""Autotuner for the launch configuration of a filter or a batch of filters.
 
 For one problem (model kind, state dimension, N, radices) it times a few
 candidate configurations - the tile size of the shared-memory tile kernel
@@ -8,9 +8,14 @@ fastest.  Results are cached per device in a JSON file (``BFPF_TUNE_CACHE``,
 default ``~/.cache/bfpf/tune.json``), keyed by device name, SM count and the
 problem, so later filters of the same shape start with the tuned options.
 
-Tuning changes only how the work is split; the filter's results do not depend
-on the tile size, and on the grid only through the summation order of the
-likelihood partial sums.
+For a batch (``tune_batch``) it times the tile size and the work of one
+thread block (``unit_work``: how finely each filter's step is split over
+blocks), keyed by the batch's shape signature (the multiset of model kind,
+state dimension, N and radices).
+
+Tuning changes only how the work is split: states and ancestors do not depend
+on it, and the likelihood, mean and ESS only through the summation order of
+their FP32 partial sums.
 """
 from __future__ import annotations
 
@@ -106,6 +111,66 @@ def tune(model, N: int, radices: Sequence[int], *, cycles: int = 2, device=None,
             continue
     (tile, grid), ms = pick_best(timings)
     entry = {"tile": tile, "grid": grid, "ms_per_step": ms, "default_ms_per_step": timings.get((0, 0)),
+             "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
+    if use_cache:
+        store(key, entry)
+    return entry
+
+
+def batch_signature(specs) -> str:
+    """Shape signature of a batch: sorted (kind, d, N, radices) counts."""
+    import hashlib
+    shapes = {}
+    for model, N, radices, _seed in specs:
+        d = 1 if model.kind == "sv" else int(model.A.shape[0])
+        k = f"{model.kind}:{d}:{int(N)}:{'x'.join(str(int(a)) for a in radices)}"
+        shapes[k] = shapes.get(k, 0) + 1
+    text = ";".join(f"{k}*{v}" for k, v in sorted(shapes.items()))
+    return hashlib.sha1(text.encode()).hexdigest()[:16]
+
+
+def batch_candidates() -> Iterable[Tuple[int, int]]:
+    """(tile, unit_work) pairs: 0 means the library's own choice."""
+    for t in (0, 1024, 2048):
+        for u in (0, 8192, 16384, 65536, 131072):
+            yield t, u
+
+
+def tune_batch(specs, *, steps: int = 8, device=None, use_cache: bool = True,
+               timer: Optional[Callable] = None) -> dict:
+    """Tuned {tile, unit_work} for a batch of filters (cached per device and batch signature)."""
+    import torch
+    from . import FilterBatch
+    dev = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
+    props = torch.cuda.get_device_properties(dev)
+    key = f"{props.name}|{props.multi_processor_count}|batch|{batch_signature(specs)}"
+    if use_cache:
+        hit = load_cache().get(key)
+        if hit:
+            return hit
+    dy_max = max(1 if m.kind == "sv" else int(m.H.shape[0]) for m, _, _, _ in specs)
+    y = torch.zeros((len(specs), 2 * steps, dy_max), dtype=torch.float32, device=dev)
+
+    def default_timer(tile, unit_work):
+        b = FilterBatch(specs, tile=tile, unit_work=unit_work, chunk_len=steps, device=dev)
+        b.run(y[:, :steps], outputs=False)            # warm-up: graph capture
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(b.stream)
+        b.run(y[:, steps:], outputs=False)
+        e1.record(b.stream)
+        torch.cuda.synchronize(dev)
+        b.close()
+        return e0.elapsed_time(e1) / steps
+
+    run = timer or default_timer
+    timings = {}
+    for tile, uw in batch_candidates():
+        try:
+            timings[(tile, uw)] = run(tile, uw)
+        except Exception:          # a candidate that does not fit (shared memory) is skipped
+            continue
+    (tile, uw), ms = pick_best(timings)
+    entry = {"tile": tile, "unit_work": uw, "ms_per_step": ms, "default_ms_per_step": timings.get((0, 0)),
              "when": time.strftime("%Y-%m-%dT%H:%M:%S")}
     if use_cache:
         store(key, entry)

@@ -3,13 +3,16 @@
 //
 // Each filter is the filter of step_butterfly.cu (Algorithm 1 with one stage
 // of Algorithm 3 per step, Heine, Whiteley & Cemgil, arXiv 1812.01502).  One
-// launch covers a whole chunk of time steps of every filter of the batch:
-// block b runs filter order[b] (filters sorted by decreasing work, so the
-// largest start first) step after step with the shared tile code, finishing
-// each step's likelihood increment, filter mean and ESS inside the block - a
-// filter never needs another block, so nothing waits and blocks of small
-// filters flow through the chunk without per-step launches.  The last block
-// to finish advances the batch's step counter (last-block-done).
+// time step of every filter of the batch is one launch per class of filters
+// (model kind and state dimension) and a launch that advances the step.  A filter's step is
+// split into U work units (U from the filter's own size only, so a filter's
+// results do not depend on the rest of the batch): unit j runs the tiles j,
+// j + U, ... of the step's digit with the shared tile code.  A filter with one
+// unit finishes its step (likelihood increment, filter mean, ESS) inside its
+// block; with several, every unit writes its partial sums and the last unit to
+// arrive folds them in unit order (last-block-done per filter, deterministic).
+// Units are launched largest first, so that the big filters start at once and
+// small ones fill the machine behind them.
 #include <cfloat>
 #include <type_traits>
 
@@ -22,15 +25,13 @@ namespace bfpf {
 
 namespace {
 
-// Block-level end of one filter's step (the single-block form of finish_step).
+// Block reduction of the per-thread partials; the result is valid in thread 0.
 template <int D>
-__device__ __forceinline__ void block_finish(const BatchParams& bp, BatchFilter& f, uint32_t fid, uint32_t n,
-                                             Partial acc, float* accx, uint32_t status, float muf) {
+__device__ __forceinline__ void block_partial(Partial& acc, float* accx, Partial& b, float* bx) {
   constexpr int NP = 3 + D;
   constexpr int NW = kBlock / 32;
   __shared__ float s_red[NW][NP];
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  if (status) atomicOr(&f.st.status, status);
 #pragma unroll
   for (int off = 16; off; off >>= 1) shfl_merge<D>(acc, accx, off);
   if (lane == 0) {
@@ -41,36 +42,42 @@ __device__ __forceinline__ void block_finish(const BatchParams& bp, BatchFilter&
     for (int t = 0; t < D; ++t) s_red[warp][3 + t] = accx[t];
   }
   __syncthreads();
-  if (tid == 0) {
-    Partial b{-INFINITY, 0.0f, 0.0f};
-    float bx[D];
+  b = Partial{-INFINITY, 0.0f, 0.0f};
 #pragma unroll
-    for (int t = 0; t < D; ++t) bx[t] = 0.0f;
+  for (int t = 0; t < D; ++t) bx[t] = 0.0f;
+  if (tid == 0)
     for (int w = 0; w < NW; ++w) merge_partial<D>(b, bx, s_red[w][0], s_red[w][1], s_red[w][2], &s_red[w][3]);
-    const uint32_t slot = n % bp.ring;
-    double lme, inc, ess;
-    if (b.m == -INFINITY || !(b.s1 > 0.0f)) {
-      lme = -INFINITY;
-      inc = -INFINITY;
-      ess = 0.0;
-    } else {
-      lme = (double)b.m + log((double)b.s1 / (double)f.N);
-      inc = lme + ((double)muf - f.st.mu) + f.model.c_obs;
-      ess = (double)b.s1 * (double)b.s1 / ((double)f.N * (double)b.s2);
-    }
-    bp.inc_ring[(size_t)fid * bp.ring + slot] = inc;
-    bp.ess_ring[(size_t)fid * bp.ring + slot] = (float)ess;
-    for (int t = 0; t < D; ++t)
-      bp.mean_ring[((size_t)fid * bp.ring + slot) * bp.d_max + t] = (float)((double)bx[t] / (double)b.s1);
-    f.st.loglik += inc;
-    f.st.mu = lme;
-    f.st.mu_f = (float)lme;
-  }
 }
 
+// The step's summaries of filter fid from its folded sums (one thread).
+template <int D>
+__device__ __forceinline__ void filter_summaries(const BatchParams& bp, BatchFilter& f, uint32_t fid, uint32_t n,
+                                                 const Partial& b, const float* bx, float muf) {
+  const uint32_t slot = n % bp.ring;
+  double lme, inc, ess;
+  if (b.m == -INFINITY || !(b.s1 > 0.0f)) {
+    lme = -INFINITY;
+    inc = -INFINITY;
+    ess = 0.0;
+  } else {
+    lme = (double)b.m + log((double)b.s1 / (double)f.N);
+    inc = lme + ((double)muf - f.st.mu) + f.model.c_obs;
+    ess = (double)b.s1 * (double)b.s1 / ((double)f.N * (double)b.s2);
+  }
+  bp.inc_ring[(size_t)fid * bp.ring + slot] = inc;
+  bp.ess_ring[(size_t)fid * bp.ring + slot] = (float)ess;
+  for (int t = 0; t < D; ++t)
+    bp.mean_ring[((size_t)fid * bp.ring + slot) * bp.d_max + t] = (float)((double)bx[t] / (double)b.s1);
+  f.st.loglik += inc;
+  f.st.mu = lme;
+  f.st.mu_f = (float)lme;
+}
+
+// Unit j of U of filter fid at step n.
 template <int D, int KIND>
-__device__ __forceinline__ void batch_filter_step(const BatchParams& bp, BatchFilter& f, uint32_t fid, uint32_t n,
-                                                  unsigned char* smem) {
+__device__ __forceinline__ void batch_unit_step(const BatchParams& bp, BatchFilter& f, uint32_t fid, uint32_t n,
+                                                uint32_t j, uint32_t U, unsigned char* smem) {
+  __shared__ uint32_t s_last;
   TileCtx ctx;
   const uint32_t k = n % f.m;
   ctx.n = n;
@@ -90,64 +97,85 @@ __device__ __forceinline__ void batch_filter_step(const BatchParams& bp, BatchFi
   ctx.muf = f.st.mu_f;
   const float* yr = bp.y_ring + ((size_t)fid * bp.ring + n % bp.ring) * bp.dy_max;
 #pragma unroll
-  for (int j = 0; j < kMaxDim; ++j) ctx.y[j] = (j < (int)f.model.dy) ? yr[j] : 0.0f;
+  for (int q = 0; q < kMaxDim; ++q) ctx.y[q] = (q < (int)f.model.dy) ? yr[q] : 0.0f;
   uint32_t status = 0;
   Partial acc{-INFINITY, 0.0f, 0.0f};
   float accx[D];
 #pragma unroll
   for (int t = 0; t < D; ++t) accx[t] = 0.0f;
-  tile_steps<D, KIND, false>(ctx, 0, 1, smem, acc, accx, status);
-  block_finish<D>(bp, f, fid, n, acc, accx, status, ctx.muf);
-}
-
-// Steps n0 .. n0 + steps - 1 of one filter: a filter never depends on another,
-// so its block runs the whole chunk without any grid-wide synchronisation.
-template <int D, int KIND>
-__device__ __forceinline__ void batch_filter_steps(const BatchParams& bp, BatchFilter& f, uint32_t fid, uint32_t n0,
-                                                   uint32_t steps, unsigned char* smem) {
-  for (uint32_t j = 0; j < steps; ++j) {
-    batch_filter_step<D, KIND>(bp, f, fid, n0 + j, smem);
-    __syncthreads();   // this filter's normaliser and weights are in place for the next step
+  tile_steps<D, KIND, false>(ctx, j, U, smem, acc, accx, status);
+  if (status) atomicOr(&f.st.status, status);
+  Partial b;
+  float bx[D];
+  block_partial<D>(acc, accx, b, bx);
+  if (U == 1) {
+    if (threadIdx.x == 0) filter_summaries<D>(bp, f, fid, n, b, bx, ctx.muf);
+    return;
   }
+  if (threadIdx.x == 0) {
+    float* out = bp.partials + (size_t)(f.pbase + j) * kBatchNP;
+    out[0] = b.m;
+    out[1] = b.s1;
+    out[2] = b.s2;
+#pragma unroll
+    for (int t = 0; t < D; ++t) out[3 + t] = bx[t];
+    __threadfence();
+    const uint32_t prev = atomicAdd(&f.st.done, 1u);
+    s_last = (prev == U - 1) ? 1u : 0u;
+  }
+  __syncthreads();
+  if (!s_last || threadIdx.x != 0) return;
+  __threadfence();
+  // last unit of the filter: fold the U partials in unit order
+  Partial t{-INFINITY, 0.0f, 0.0f};
+  float tx[D];
+#pragma unroll
+  for (int q = 0; q < D; ++q) tx[q] = 0.0f;
+  for (uint32_t u = 0; u < U; ++u) {
+    const float* pu = bp.partials + (size_t)(f.pbase + u) * kBatchNP;
+    float ux[D];
+#pragma unroll
+    for (int q = 0; q < D; ++q) ux[q] = __ldcg(pu + 3 + q);
+    merge_partial<D>(t, tx, __ldcg(pu), __ldcg(pu + 1), __ldcg(pu + 2), ux);
+  }
+  filter_summaries<D>(bp, f, fid, n, t, tx, ctx.muf);
+  f.st.done = 0;
 }
 
 }  // namespace
 
-// One launch runs `steps` consecutive time steps of every filter (one block per filter).
-__global__ void __launch_bounds__(kBlock) batch_step_kernel(const __grid_constant__ BatchParams bp, uint32_t steps) {
+// One time step of the work units u0 .. u0 + gridDim.x - 1, all of one model
+// kind and state dimension (a kernel per class, so that each keeps the
+// registers its own dimension needs).
+template <int D, int KIND>
+__global__ void __launch_bounds__(kBlock) batch_class_kernel(const __grid_constant__ BatchParams bp, uint32_t u0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ uint32_t s_last;
   const uint32_t n = bp.state->n;
-  const uint32_t fid = bp.order[blockIdx.x];
-  BatchFilter& f = bp.filters[fid];
-  const int d = f.model.d;
-  if (f.model.kind == kStochVol) {
-    batch_filter_steps<1, kStochVol>(bp, f, fid, n, steps, smem_raw);
-  } else {
-    switch (d) {
-      case 1: batch_filter_steps<1, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
-      case 2: batch_filter_steps<2, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
-      case 3: batch_filter_steps<3, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
-      case 4: batch_filter_steps<4, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
-      case 5: batch_filter_steps<5, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
-      case 6: batch_filter_steps<6, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
-      case 7: batch_filter_steps<7, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
-      default: batch_filter_steps<8, kLinearGaussian>(bp, f, fid, n, steps, smem_raw); break;
-    }
-  }
-  // the last block to finish advances the batch's step counter
-  if (threadIdx.x == 0) {
-    __threadfence();
-    const uint32_t prev = atomicAdd(&bp.state->done, 1u);
-    s_last = (prev == gridDim.x - 1) ? 1u : 0u;
-  }
-  __syncthreads();
-  if (s_last && threadIdx.x == 0) {
-    bp.state->done = 0;
-    __threadfence();
-    bp.state->n = n + steps;
+  const uint2 un = bp.units[u0 + blockIdx.x];
+  const uint32_t fid = un.x, j = un.y & 0xffffu, U = un.y >> 16;
+  batch_unit_step<D, KIND>(bp, bp.filters[fid], fid, n, j, U, smem_raw);
+}
+
+// After every class of a step: advance the batch's step counter.
+__global__ void batch_advance_kernel(const __grid_constant__ BatchParams bp) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) bp.state->n = bp.state->n + 1;
+}
+
+const void* batch_class_kernel_ptr(int kind, int d) {
+  if (kind == kStochVol) return d == 1 ? reinterpret_cast<const void*>(&batch_class_kernel<1, kStochVol>) : nullptr;
+  switch (d) {
+    case 1: return reinterpret_cast<const void*>(&batch_class_kernel<1, kLinearGaussian>);
+    case 2: return reinterpret_cast<const void*>(&batch_class_kernel<2, kLinearGaussian>);
+    case 3: return reinterpret_cast<const void*>(&batch_class_kernel<3, kLinearGaussian>);
+    case 4: return reinterpret_cast<const void*>(&batch_class_kernel<4, kLinearGaussian>);
+    case 5: return reinterpret_cast<const void*>(&batch_class_kernel<5, kLinearGaussian>);
+    case 6: return reinterpret_cast<const void*>(&batch_class_kernel<6, kLinearGaussian>);
+    case 7: return reinterpret_cast<const void*>(&batch_class_kernel<7, kLinearGaussian>);
+    case 8: return reinterpret_cast<const void*>(&batch_class_kernel<8, kLinearGaussian>);
+    default: return nullptr;
   }
 }
+const void* batch_advance_kernel_ptr() { return reinterpret_cast<const void*>(&batch_advance_kernel); }
 
 // Initial particles of every filter (one block per filter).
 __global__ void __launch_bounds__(kBlock) batch_init_kernel(const __grid_constant__ BatchParams bp) {
@@ -176,7 +204,6 @@ __global__ void __launch_bounds__(kBlock) batch_init_kernel(const __grid_constan
   }
 }
 
-const void* batch_step_kernel_ptr() { return reinterpret_cast<const void*>(&batch_step_kernel); }
 const void* batch_init_kernel_ptr() { return reinterpret_cast<const void*>(&batch_init_kernel); }
 
 }  // namespace bfpf

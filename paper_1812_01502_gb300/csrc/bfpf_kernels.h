@@ -62,9 +62,11 @@ struct IslandKernels {
 };
 bool select_island_kernels(int d, int kind, IslandKernels& ik);
 
-// Batched filters (batch.cu): batch_step_kernel(BatchParams, uint32_t steps) runs a chunk of
-// steps of every filter; batch_init_kernel(BatchParams).
-const void* batch_step_kernel_ptr();
+// Batched filters (batch.cu): batch_class_kernel<D, KIND>(BatchParams, uint32_t u0) runs one
+// time step of the work units u0 .. u0 + grid - 1 (one class of model kind and
+// dimension); batch_advance_kernel(BatchParams) advances the step; batch_init_kernel(BatchParams).
+const void* batch_class_kernel_ptr(int kind, int d);
+const void* batch_advance_kernel_ptr();
 const void* batch_init_kernel_ptr();
 
 cudaError_t launch_philox_blocks(uint64_t seed, uint4 c, uint32_t count, uint32_t* out,

@@ -1381,7 +1381,9 @@ struct pf_batch {
   size_t smem = 0;
   BatchParams BP{};
   std::vector<BatchFilter> host_filters;    // host copy (pointers, sizes, geometry)
-  std::vector<uint32_t> order;
+  std::vector<uint2> units;                 // {filter, j | U << 16}, by class, largest work first
+  struct Class { const void* kernel; uint32_t u0, count; };
+  std::vector<Class> classes;               // one kernel launch per class and step
   uint64_t n_host = 0;
   cudaGraphExec_t graph = nullptr;
   std::string err;
@@ -1390,9 +1392,16 @@ struct pf_batch {
 namespace {
 
 struct BatchLayout {
-  size_t state, filters, order, y_ring, inc_ring, mean_ring, ess_ring, total;
+  size_t state, filters, units, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
   std::vector<size_t> x, lv0, lv1;
+  std::vector<uint32_t> U, pbase;   // work units of every filter, first partial slot
+  uint32_t nunits = 0, nslots = 0;
 };
+
+// Work of one filter's step in particle-dimensions, and the default work of one
+// thread block (a 2^14-particle filter of dimension 1, or 2^11 particles of dimension 8).
+inline double batch_work(const Plan& pl) { return (double)pl.N * (pl.d + 1); }
+constexpr double kBatchUnitWork = 32768.0;
 
 // Plan every filter and lay the batch out in one workspace.
 pf_status plan_batch(int32_t F, const pf_model* models, const int64_t* N, const int32_t* radices, const int32_t* m,
@@ -1420,11 +1429,29 @@ pf_status plan_batch(int32_t F, const pf_model* models, const int64_t* N, const 
     d_max = std::max(d_max, plans[f].d);
     smem = std::max(smem, plans[f].smem);
   }
+  // Work units: a filter's step is split into U = ceil(work / unit work) blocks
+  // (at most the fewest tiles of any of its digits), from the filter's own size
+  // only; opts->grid > 0 sets the unit work (particle-dimensions per block).
+  const double unit_work = (opts && opts->grid > 0) ? (double)opts->grid : kBatchUnitWork;
+  L.U.resize(F);
+  L.pbase.resize(F);
+  L.nunits = L.nslots = 0;
+  for (int32_t f = 0; f < F; ++f) {
+    uint32_t tiles = 0xffffffffu;
+    for (int k = 0; k < plans[f].m; ++k) tiles = std::min(tiles, plans[f].geom[k].ntiles);
+    const double want = std::ceil(batch_work(plans[f]) / unit_work);
+    const uint32_t U = (uint32_t)std::max(1.0, std::min({want, (double)tiles, 65535.0}));
+    L.U[f] = U;
+    L.pbase[f] = (U > 1) ? L.nslots : 0u;
+    if (U > 1) L.nslots += U;
+    L.nunits += U;
+  }
   size_t off = 0;
   auto take = [&](size_t bytes) { size_t o = off; off = align_up(off + bytes); return o; };
   L.state = take(sizeof(BatchState));
   L.filters = take(sizeof(BatchFilter) * (size_t)F);
-  L.order = take(4 * (size_t)F);
+  L.units = take(8 * (size_t)L.nunits);
+  L.partials = take((size_t)4 * kBatchNP * std::max(1u, L.nslots));
   L.y_ring = take((size_t)4 * F * ring * dy_max);
   L.inc_ring = take((size_t)8 * F * ring);
   L.mean_ring = take((size_t)4 * F * ring * d_max);
@@ -1488,8 +1515,6 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
     return bfail(nullptr, s, msg);
   }
   cudaError_t e = cudaGetDevice(&b->device);
-  if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(batch_step_kernel_ptr(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
   if (e != cudaSuccess) {
     delete b;
     return bfail(nullptr, PF_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));
@@ -1519,7 +1544,8 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
     return bfail(nullptr, PF_ECUDA, std::string("cudaStreamCreate: ") + cudaGetErrorString(e));
   }
   b->host_filters.resize(F);
-  std::vector<std::pair<double, uint32_t>> work(F);
+  std::vector<std::pair<double, uint2>> work;
+  work.reserve(L.nunits);
   for (int32_t f = 0; f < F; ++f) {
     BatchFilter& bf = b->host_filters[f];
     std::memset(&bf, 0, sizeof(bf));
@@ -1533,14 +1559,42 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
     bf.rk = make_round_keys(seeds[f]);
     bf.model = pl.mp;
     std::memcpy(bf.geom, pl.geom, sizeof(bf.geom));
-    work[f] = {-(double)pl.N * (pl.d + 1), (uint32_t)f};
+    bf.U = L.U[f];
+    bf.pbase = L.pbase[f];
+    const double uw = batch_work(pl) / L.U[f];
+    for (uint32_t j = 0; j < L.U[f]; ++j) work.push_back({-uw, make_uint2((uint32_t)f, j | (L.U[f] << 16))});
   }
-  std::sort(work.begin(), work.end());
-  b->order.resize(F);
-  for (int32_t f = 0; f < F; ++f) b->order[f] = work[f].second;
+  // classes of (model kind, dimension); inside a class, largest units first
+  auto cls = [&](const uint2& u) { return plans[u.x].kind * 16 + plans[u.x].d; };
+  std::stable_sort(work.begin(), work.end(), [&](const std::pair<double, uint2>& x, const std::pair<double, uint2>& y) {
+    const int cx = cls(x.second), cy = cls(y.second);
+    return cx != cy ? cx < cy : x.first < y.first;
+  });
+  b->units.resize(work.size());
+  for (size_t u = 0; u < work.size(); ++u) b->units[u] = work[u].second;
+  for (size_t u = 0; u < work.size(); ++u) {
+    if (u == 0 || cls(work[u].second) != cls(work[u - 1].second)) {
+      const Plan& pl = plans[work[u].second.x];
+      b->classes.push_back({batch_class_kernel_ptr(pl.kind, pl.d), (uint32_t)u, 0u});
+    }
+    b->classes.back().count += 1;
+  }
+  for (const auto& c : b->classes) {
+    if (!c.kernel) {
+      delete b;
+      return bfail(nullptr, PF_EINVAL, "unsupported (d, model) combination in the batch");
+    }
+    e = cudaFuncSetAttribute(c.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    if (e != cudaSuccess) {
+      delete b;
+      return bfail(nullptr, PF_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));
+    }
+  }
   BatchParams& P = b->BP;
   P.filters = reinterpret_cast<BatchFilter*>(b->ws + L.filters);
-  P.order = reinterpret_cast<const uint32_t*>(b->ws + L.order);
+  P.units = reinterpret_cast<const uint2*>(b->ws + L.units);
+  P.nunits = L.nunits;
+  P.partials = reinterpret_cast<float*>(b->ws + L.partials);
   P.state = reinterpret_cast<BatchState*>(b->ws + L.state);
   P.y_ring = reinterpret_cast<const float*>(b->ws + L.y_ring);
   P.inc_ring = reinterpret_cast<double*>(b->ws + L.inc_ring);
@@ -1561,7 +1615,7 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
   e = cudaMemcpyAsync(P.filters, b->host_filters.data(), sizeof(BatchFilter) * (size_t)F, cudaMemcpyHostToDevice,
                       b->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(const_cast<uint32_t*>(P.order), b->order.data(), 4 * (size_t)F, cudaMemcpyHostToDevice,
+    e = cudaMemcpyAsync(const_cast<uint2*>(P.units), b->units.data(), 8 * b->units.size(), cudaMemcpyHostToDevice,
                         b->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(P.state, 0, sizeof(BatchState), b->stream);
   for (int32_t f = 0; f < F && e == cudaSuccess; ++f)
@@ -1580,8 +1634,17 @@ pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_in
   if (!b) return bfail(nullptr, PF_EINVAL, "batch is NULL");
   if (T < 0 || (T > 0 && !y)) return bfail(b, PF_EINVAL, "need T >= 0 and y != NULL");
   const int R = b->ring, F = b->F;
-  uint32_t chunk_steps = 0;
-  void* args[] = {&b->BP, &chunk_steps};
+  // one time step: a launch per class of filters, then the step counter
+  auto launch_step = [&](cudaStream_t s) -> cudaError_t {
+    for (auto& c : b->classes) {
+      uint32_t u0 = c.u0;
+      void* cargs[] = {&b->BP, &u0};
+      cudaError_t le = cudaLaunchKernel(c.kernel, dim3(c.count), dim3(kBlock), cargs, b->smem, s);
+      if (le != cudaSuccess) return le;
+    }
+    void* aargs[] = {&b->BP};
+    return cudaLaunchKernel(batch_advance_kernel_ptr(), dim3(1), dim3(32), aargs, 0, s);
+  };
   int32_t done = 0;
   while (done < T) {
     const uint32_t slot0 = (uint32_t)(b->n_host % (uint64_t)R);
@@ -1593,9 +1656,8 @@ pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_in
       if (!b->graph) {
         cudaGraph_t graph = nullptr;
         PF_BCUDA(b, cudaStreamBeginCapture(b->cap_stream, cudaStreamCaptureModeThreadLocal));
-        chunk_steps = (uint32_t)L;           // one launch runs the whole chunk
-        cudaError_t le = cudaLaunchKernel(batch_step_kernel_ptr(), dim3(F), dim3(kBlock), args, b->smem,
-                                          b->cap_stream);
+        cudaError_t le = cudaSuccess;        // the launches of every time step of the chunk
+        for (int32_t j = 0; j < L && le == cudaSuccess; ++j) le = launch_step(b->cap_stream);
         cudaError_t ce = cudaStreamEndCapture(b->cap_stream, &graph);
         if (le != cudaSuccess) return bfail(b, PF_ECUDA, std::string("capture launch: ") + cudaGetErrorString(le));
         if (ce != cudaSuccess) return bfail(b, PF_ECUDA, std::string("cudaStreamEndCapture: ") + cudaGetErrorString(ce));
@@ -1608,8 +1670,7 @@ pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_in
       }
       PF_BCUDA(b, cudaGraphLaunch(b->graph, b->stream));
     } else {
-      chunk_steps = (uint32_t)L;
-      PF_BCUDA(b, cudaLaunchKernel(batch_step_kernel_ptr(), dim3(F), dim3(kBlock), args, b->smem, b->stream));
+      for (int32_t j = 0; j < L; ++j) PF_BCUDA(b, launch_step(b->stream));
     }
     if (loglik_incs)
       PF_BCUDA(b, cudaMemcpy2DAsync(loglik_incs + done, (size_t)8 * T, b->BP.inc_ring + slot0, (size_t)8 * R,
