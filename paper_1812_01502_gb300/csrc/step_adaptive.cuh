@@ -37,7 +37,7 @@ __device__ __forceinline__ void adaptive_mutate_only(const StepParams& p, const 
 #pragma unroll
       for (int b = 0; b < D; ++b) {
         const uint4 w = philox4x32(make_uint4(q * D + b, n, kPurposePropagate, 0), p.rk);
-        normals4(w, z + 4 * b);
+        normals4_fast(w, z + 4 * b);
       }
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
@@ -62,7 +62,7 @@ __device__ __forceinline__ void adaptive_mutate_only(const StepParams& p, const 
         const uint32_t nu = pi * D + t;
         const uint4 w = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
         float zz[4];
-        normals4(w, zz);
+        normals4_fast(w, zz);
         z[t] = zz[nu & 3u];
       }
       mutate<D, KIND>(mp, xh, z, xo);

@@ -151,7 +151,7 @@ __global__ void __launch_bounds__(kBlock) island_gather_kernel(const __grid_cons
 #pragma unroll
       for (int b = 0; b < D; ++b) {          // normals nu = i d + t, blocks of 4
         const uint4 w = philox4x32(make_uint4(q * D + b, n, kPurposePropagate, 0), p.rk);
-        normals4(w, z + 4 * b);
+        normals4_fast(w, z + 4 * b);
       }
       float out[D][4];
 #pragma unroll
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(kBlock) island_gather_kernel(const __grid_cons
         const uint32_t nu = i * D + t;
         const uint4 w = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), p.rk);
         float zz[4];
-        normals4(w, zz);
+        normals4_fast(w, zz);
         z[t] = zz[nu & 3u];
       }
       mutate<D, KIND>(mp, xh, z, xo);

@@ -199,7 +199,7 @@ __device__ __forceinline__ void set_tile_steps(const TileCtx& ctx, uint32_t firs
 #pragma unroll
           for (int b = 0; b < D; ++b) {
             const uint4 wv = philox4x32(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
-            normals4(wv, z + 4 * b);
+            normals4_fast(wv, z + 4 * b);
           }
         }
       } else {    // members straddle counter blocks: one block per draw / normal
@@ -221,7 +221,7 @@ __device__ __forceinline__ void set_tile_steps(const TileCtx& ctx, uint32_t firs
             const uint32_t nu = pi * D + t;
             const uint4 wv = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), rk);
             float zz[4];
-            normals4(wv, zz);
+            normals4_fast(wv, zz);
             z[jj * D + t] = zz[nu & 3u];
           }
         }

@@ -243,7 +243,7 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
 #pragma unroll
           for (int b = 0; b < D; ++b) {
             const uint4 w = philox4x32(make_uint4((pi0 >> 2) * D + b, n, kPurposePropagate, 0), rk);
-            normals4(w, z + 4 * b);
+            normals4_fast(w, z + 4 * b);
           }
         }
       } else {    // members straddle counter blocks: one block per draw / normal
@@ -265,7 +265,7 @@ __device__ __forceinline__ void tile_steps(const TileCtx& ctx, uint32_t first, u
             const uint32_t nu = pi * D + t;
             const uint4 w = philox4x32(make_uint4(nu >> 2, n, kPurposePropagate, 0), rk);
             float zz[4];
-            normals4(w, zz);
+            normals4_fast(w, zz);
             z[jj * D + t] = zz[nu & 3u];
           }
         }
