@@ -56,8 +56,7 @@ def _args():
     p.add_argument("--batched-filters", type=int, default=4096)
     p.add_argument("--batched-steps", type=int, default=500)
     p.add_argument("--no-serving", action="store_true", help="skip the serving leg")
-    p.add_argument("--serving-requests", type=int, default=160)
-    p.add_argument("--serving-rate", type=float, default=40.0, help="Poisson arrival rate, requests/s")
+    p.add_argument("--serving-requests", type=int, default=96, help="requests per arrival rate of the sweep")
     p.add_argument("--no-paper", action="store_true", help="skip the Section 6.1 random-walk leg")
     p.add_argument("--no-schedules", action="store_true", help="skip the all-stages / adaptive leg")
     p.add_argument("--oracle-rate", action="store_true", help=argparse.SUPPRESS)
@@ -476,19 +475,35 @@ def batched_leg(bf, dev, F=4096, T=500):
             "launches_per_step": 1}
 
 
-def serving_leg(dev, n_requests=160, rate=40.0):
+def serving_leg(dev, n_requests=96, chunk_interval=0.01, fractions=(0.25, 0.5, 0.75, 0.9)):
     """Poisson arrivals of filtering requests (LG d in {1,4,8} or SV; N = 2^U{10..20};
-    T = U(100, 2000); observations in chunks of 50) served with memory admission and
-    continuous batching; p50/p99 request latency beside throughput."""
+    T = U(100, 2000); observations in chunks of 50, one chunk every chunk_interval
+    seconds after the request's arrival) served with admission by the device's
+    free memory and continuous batching.  The capacity (requests/s) is measured
+    with every request present at time 0 and its observations all arrived; the
+    arrival rate is then swept to 90 % of it, with p50 / p99 request and chunk
+    latency and throughput at each rate."""
     import synthetic as S
     from paper_1812_01502_gb300 import serve
-    reqs = serve.requests_from_stream(S.serving_stream(n_requests, rate_hz=rate), chunk=50)
-    srv = serve.Server(memory_budget=24 << 30, slots=32, device=dev)
+    slots = 32
+    reqs = serve.requests_from_stream(S.serving_stream(n_requests, rate_hz=1e9), chunk=50)
+    srv = serve.Server(slots=slots, device=dev)
     done = srv.run(reqs)
-    out = serve.summarize(done, srv.wall)
-    out.update({"arrival_rate_hz": rate, "slots": 32, "memory_budget_gb": 24, "chunk": 50,
-                "max_concurrent": srv.max_active})
-    return out
+    cap = serve.summarize(done, srv.wall)
+    capacity = len(done) / srv.wall
+    sweep = []
+    for frac in fractions:
+        rate = frac * capacity
+        reqs = serve.requests_from_stream(S.serving_stream(n_requests, rate_hz=rate), chunk=50,
+                                          chunk_interval=chunk_interval)
+        srv = serve.Server(slots=slots, device=dev)
+        done = srv.run(reqs)
+        row = serve.summarize(done, srv.wall)
+        row.update({"load": frac, "arrival_rate_hz": rate, "max_concurrent": srv.max_active})
+        sweep.append(row)
+    return {"capacity_requests_per_s": capacity, "capacity_run": cap, "sweep": sweep, "slots": slots,
+            "admission": "device free memory less a 2 GB reserve", "chunk": 50,
+            "chunk_interval_s": chunk_interval, "requests_per_rate": n_requests}
 
 
 def _kalman_reference(model, y):
@@ -918,7 +933,7 @@ def ours_main(a):
         batched = batched_leg(bf, dev, a.batched_filters, a.batched_steps)
     serving = None
     if not a.no_serving and rank == 0:
-        serving = serving_leg(dev, a.serving_requests, a.serving_rate)
+        serving = serving_leg(dev, a.serving_requests)
     paper = None
     if not a.no_paper and rank == 0:
         paper = paper_workload_leg(bf, dev)

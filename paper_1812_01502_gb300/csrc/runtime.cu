@@ -9,6 +9,7 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
@@ -544,14 +545,31 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
   return PF_OK;
 }
 
+// The dynamic shared-memory limit is an attribute of the kernel, shared by every
+// handle in the process: raise it when a handle needs more, never lower it
+// (another handle may be running the same kernel with a larger tile).
+cudaError_t raise_smem_limit(const void* kernel, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{dev, kernel}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
+}
+
 // Needs a CUDA device: occupancy decides the persistent grid size.
 pf_status finish_plan_global(Plan& pl, const pf_options* opts, int sms, std::string& msg) {
   int nw = 0;
-  cudaError_t e = cudaFuncSetAttribute(pl.gk.resolve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_resolve);
+  cudaError_t e = raise_smem_limit(pl.gk.resolve, pl.smem_resolve);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pl.gk.weight, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_weight);
+    e = raise_smem_limit(pl.gk.weight, pl.smem_weight);
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(pl.gk.refine, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem_refine);
+    e = raise_smem_limit(pl.gk.refine, pl.smem_refine);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nw, pl.gk.weight, kBlock, pl.smem_weight);
   if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
   const int units = (int)((pl.N + kBlock - 1) / kBlock);
@@ -599,7 +617,7 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
                             : pl.sps > 1 ? pl.ks.step_staged : pl.ks.step;
   if (!tile_kernel) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
   if (e == cudaSuccess)   // opt in beyond the 48 KB default whatever the size
-    e = cudaFuncSetAttribute(tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    e = raise_smem_limit(tile_kernel, pl.smem);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, tile_kernel, kBlock, pl.smem);
   if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
   if (nb < 1) { msg = "tile does not fit in shared memory; choose a smaller tile"; return PF_EINVAL; }
@@ -642,7 +660,7 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
     L.x2 = take((size_t)4 * pl.d * pl.N);
     L.src = take((size_t)4 * pl.geom[1].a);
     const int smem_isl = (int)(8 * pl.geom[1].a);
-    e = cudaFuncSetAttribute(pl.ik.stages, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_isl);
+    e = raise_smem_limit(pl.ik.stages, (size_t)smem_isl);
     if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
   }
   L.total = off;
@@ -1584,7 +1602,7 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
       delete b;
       return bfail(nullptr, PF_EINVAL, "unsupported (d, model) combination in the batch");
     }
-    e = cudaFuncSetAttribute(c.kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)b->smem);
+    e = raise_smem_limit(c.kernel, b->smem);
     if (e != cudaSuccess) {
       delete b;
       return bfail(nullptr, PF_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));

@@ -1,16 +1,20 @@
 """Serving loop: filtering requests admitted by device memory, continuously batched.
 
 A request is one filtering job - a model, N, radices, seed and an observation
-series that arrives in chunks (50 observations by default).  The server keeps
-at most ``slots`` requests on the GPU, each with its own filter handle,
-workspace and CUDA stream; particle state stays resident on the device
-between chunks.  Requests that arrive while others run are admitted as soon
-as a slot and enough device memory (the handle's workspace size, checked
-against ``memory_budget``) are free.  Every scheduling pass enqueues the next
-chunk of every active request that has one ready, so the chunks of different
-requests overlap on the device; completions are detected with CUDA events.
+series that arrives in chunks (50 observations by default), chunk c at
+arrival + (c + 1) * chunk_interval (all at once when the interval is 0).  The
+server keeps at most ``slots`` requests on the GPU, each with its own filter
+handle, workspace and CUDA stream; particle state stays resident on the device
+between chunks.  Requests that arrive while others run are admitted as soon as
+a slot and enough device memory are free: the handle's workspace size checked
+against ``memory_budget`` when one is given, else against the device's free
+memory (cudaMemGetInfo, plus what the PyTorch allocator holds unused) less
+``reserve``.  Every scheduling pass copies each arrived chunk from pinned host
+memory and enqueues its steps, so the chunks of different requests overlap on
+the device; completions are detected with CUDA events.
 
-Latency of a request = completion of its last chunk - its arrival.  A request
+Latency of a request = completion of its last chunk - its arrival; latency
+of a chunk = its completion - the later of its arrival and its admission.  A request
 whose filter reports non-finite weights (a NaN observation, say) is finished
 with ``error`` set; the other requests are not affected.  The
 server reports p50 / p99 request latency, chunk latency and throughput in
@@ -40,6 +44,7 @@ class Request:
     seed: int
     y: np.ndarray                  # (T, dy) observations
     chunk: int = 50
+    chunk_interval: float = 0.0    # seconds between the arrivals of consecutive chunks
     # filled in by the server
     admitted: Optional[float] = None
     finished: Optional[float] = None
@@ -72,7 +77,8 @@ class _Active:
         self.nbytes = nbytes
         T = len(req.y)
         self.T = T
-        self.y_dev = torch.tensor(np.asarray(req.y, dtype=np.float32).reshape(T, -1), device=device)
+        # observations wait in pinned host memory; each chunk is copied when it arrives
+        self.y_host = torch.tensor(np.asarray(req.y, dtype=np.float32).reshape(T, -1)).pin_memory()
         self.means = torch.empty((T, filt.d), dtype=torch.float32, device=device)
         self.incs = torch.empty(T, dtype=torch.float64, device=device)
         self.next = 0                      # first observation not yet enqueued
@@ -82,11 +88,13 @@ class _Active:
 class Server:
     """Continuous-batching server on one GPU."""
 
-    def __init__(self, memory_budget: int, slots: int = 16, device=None, chunk_len: int = 50):
+    def __init__(self, memory_budget: Optional[int] = None, slots: int = 16, device=None, chunk_len: int = 50,
+                 reserve: int = 2 << 30):
         import torch
         self.torch = torch
         self.device = torch.device(device) if device is not None else torch.device("cuda", torch.cuda.current_device())
-        self.memory_budget = int(memory_budget)
+        self.memory_budget = None if memory_budget is None else int(memory_budget)
+        self.reserve = int(reserve)
         self.slots = int(slots)
         self.chunk_len = int(chunk_len)
         self.streams = [torch.cuda.Stream(self.device) for _ in range(self.slots)]
@@ -95,9 +103,18 @@ class Server:
         self.active: Dict[int, _Active] = {}
         self.done: List[Request] = []
 
+    def available(self) -> int:
+        """Device bytes a new request may take now."""
+        if self.memory_budget is not None:
+            return self.memory_budget - self.in_use
+        torch = self.torch
+        free, _total = torch.cuda.mem_get_info(self.device)
+        cached = torch.cuda.memory_reserved(self.device) - torch.cuda.memory_allocated(self.device)
+        return free + cached - self.reserve
+
     def _admit(self, req: Request, now: float) -> bool:
         need = workspace_bytes(req.model, req.N, req.radices)
-        if not self.free_streams or self.in_use + need > self.memory_budget:
+        if not self.free_streams or need > self.available():
             return False
         si = self.free_streams.pop()
         stream = self.streams[si]
@@ -117,16 +134,19 @@ class Server:
             return
         s = act.next
         e = min(act.T, s + act.req.chunk)
+        ready = act.req.arrival + (s // act.req.chunk + 1) * act.req.chunk_interval
+        if now < ready:                     # this chunk's observations have not arrived yet
+            return
         lib = load_library()
         h = act.filt._h
         with torch.cuda.stream(act.stream):
-            _check(lib.pf_push_observations(h, ctypes.c_void_p(act.y_dev[s:e].data_ptr()), e - s), h)
+            _check(lib.pf_push_observations(h, ctypes.c_void_p(act.y_host[s:e].data_ptr()), e - s), h)
             _check(lib.pf_advance(h, e - s, ctypes.c_void_p(act.means[s:e].data_ptr()),
                                   ctypes.c_void_p(act.incs[s:e].data_ptr()), None), h)
             ev = torch.cuda.Event()
             ev.record(act.stream)
         act.filt.steps += e - s
-        act.inflight.append((ev, now, e))
+        act.inflight.append((ev, max(ready, act.req.admitted), e))
         act.next = e
 
     def _retire(self, act: _Active, now: float) -> bool:
@@ -169,7 +189,7 @@ class Server:
                 waiting.popleft()
             if waiting and not self.active:
                 req = waiting[0]
-                if workspace_bytes(req.model, req.N, req.radices) > self.memory_budget:
+                if workspace_bytes(req.model, req.N, req.radices) > self.available():
                     raise MemoryError(f"request {req.rid} needs more than the whole memory budget")
             self.max_active = max(getattr(self, "max_active", 0), len(self.active))
             self.max_in_use = max(getattr(self, "max_in_use", 0), self.in_use)
@@ -188,17 +208,21 @@ def summarize(done: Sequence[Request], wall: float) -> dict:
     failed = sum(1 for r in done if r.error)
     lat = np.array([r.finished - r.arrival for r in done])
     clat = np.array([c for r in done for c in r.chunk_latencies])
+    # the server's own delay: completion after the last chunk's arrival
+    extra = np.array([r.finished - (r.arrival + -(-len(r.y) // r.chunk) * r.chunk_interval) for r in done])
     ps = sum(r.N * len(r.y) for r in done)
     return {"requests": len(done), "p50_latency_s": float(np.percentile(lat, 50)),
             "p99_latency_s": float(np.percentile(lat, 99)), "p50_chunk_latency_s": float(np.percentile(clat, 50)),
-            "p99_chunk_latency_s": float(np.percentile(clat, 99)), "wall_s": wall,
+            "p99_chunk_latency_s": float(np.percentile(clat, 99)),
+            "p50_after_last_chunk_s": float(np.percentile(extra, 50)),
+            "p99_after_last_chunk_s": float(np.percentile(extra, 99)), "wall_s": wall,
             "particle_steps_per_s": ps / wall, "failed_requests": failed}
 
 
-def requests_from_stream(stream, chunk: int = 50) -> List[Request]:
+def requests_from_stream(stream, chunk: int = 50, chunk_interval: float = 0.0) -> List[Request]:
     """Requests from (arrival, workload) pairs (synthetic.serving_stream)."""
     out = []
     for rid, (t, w) in enumerate(stream):
         out.append(Request(rid=rid, arrival=float(t), model=w.model, N=w.N, radices=w.radices, seed=w.filter_seed,
-                           y=w.observations(), chunk=chunk))
+                           y=w.observations(), chunk=chunk, chunk_interval=chunk_interval))
     return out

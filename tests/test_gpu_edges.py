@@ -41,3 +41,18 @@ def test_arguments_outside_the_limits(bfpf):
         bfpf.ButterflyFilter(S.lg_scalar(), 2 ** 33, (2,) * 33, 1)                           # more than 32 digits
     with pytest.raises(bfpf.PFError):
         bfpf.ButterflyFilter(S.lg_scalar(), 1, (1,), 1)                                       # N < 2
+
+
+def test_filter_keeps_running_after_a_smaller_tile_is_created(bfpf):
+    """The shared-memory limit of a kernel is shared by every handle: creating a
+    filter with a smaller tile must not break a running filter with a larger one."""
+    model = S.lg_scalar()
+    big = bfpf.ButterflyFilter(model, 4096, (64, 64), 1, tile=4096)
+    small = bfpf.ButterflyFilter(model, 4096, (64, 64), 2, tile=256)
+    y = S.simulate(model, 3, seed=3)[1]
+    for n in range(3):
+        big.step(y[n])
+        small.step(y[n])
+    assert np.isfinite(big.loglik()) and np.isfinite(small.loglik())
+    big.close()
+    small.close()

@@ -80,3 +80,37 @@ def test_failed_request_is_isolated(bfpf):
         assert np.array_equal(one.incs, done[rid].incs)
     assert serve.summarize(list(done.values()), 1.0)["failed_requests"] == 1
 
+
+
+def test_admission_by_device_free_memory(bfpf):
+    """Without a fixed budget the server admits against the device's free memory
+    (less a reserve); results are those of each request alone."""
+    from paper_1812_01502_gb300 import serve
+    mix = _requests(serve, n=8, seed=13)
+    srv = serve.Server(slots=4)
+    assert srv.available() > 0
+    done = {r.rid: r for r in srv.run(mix)}
+    assert len(done) == len(mix) and srv.max_active > 1
+    alone = _requests(serve, n=8, seed=13)[6]
+    alone.arrival = 0.0
+    one = serve.Server(slots=1).run([alone])[0]
+    assert np.array_equal(one.means, done[6].means)
+
+
+def test_chunks_arrive_after_admission(bfpf):
+    """Observation chunks that arrive every 20 ms are enqueued only once they have
+    arrived: a request of k chunks finishes no earlier than arrival + k * 20 ms,
+    and its result is the same as with every observation available at once."""
+    from paper_1812_01502_gb300 import serve
+    reqs = _requests(serve, n=3, seed=17)
+    for r in reqs:
+        r.chunk_interval = 0.02
+    done = {r.rid: r for r in serve.Server(memory_budget=8 << 30, slots=3).run(reqs)}
+    for r in reqs:
+        k = -(-len(r.y) // r.chunk)
+        assert done[r.rid].finished >= r.arrival + k * 0.02 - 1e-9
+        assert len(done[r.rid].chunk_latencies) == k
+    instant = _requests(serve, n=3, seed=17)[1]
+    instant.arrival = 0.0
+    one = serve.Server(memory_budget=8 << 30, slots=1).run([instant])[0]
+    assert np.array_equal(one.incs, done[1].incs)
