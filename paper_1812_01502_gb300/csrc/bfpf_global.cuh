@@ -44,6 +44,9 @@ __host__ __device__ constexpr int global_weight_vec(int d) { return d <= 2 ? 8 :
 // Indices of P (and states) the resolve kernel's shared-memory buffer holds.
 __host__ __device__ constexpr uint32_t global_stage_alloc(int d) { return d <= 2 ? 2048u : 1024u; }
 
+// Bins of the resolve kernel's guide table over a bucket's u interval.
+constexpr uint32_t kGuideBins = 1024;
+
 constexpr int kScanItems = 16;
 constexpr uint32_t kMaxCoarse = 4096;                          // coarse bins and buckets per coarse bin
 constexpr int kRefineItems = 8;                                // draws per thread of a refine block

@@ -325,7 +325,8 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     pl.nseg = (pl.ccap + kRefineSeg - 1) / kRefineSeg;
     pl.smem_weight = (size_t)8 * kBlock * global_weight_vec(d) + (size_t)8 * (1u << pl.cbits);
     pl.smem_refine = (size_t)8 * kRefineSeg + (size_t)8 * (1u << (pl.log2b - pl.cbits));
-    pl.smem_resolve = (size_t)8 * global_stage_alloc(d) + (size_t)4 * d * (global_stage_alloc(d) + 1u);
+    pl.smem_resolve = (size_t)8 * global_stage_alloc(d) + (size_t)4 * d * (global_stage_alloc(d) + 1u) +
+                      (size_t)4 * kGuideBins;
     DigitGeom& g = pl.geom[0];
     g.a = pl.N;
     g.s = 1;

@@ -25,10 +25,11 @@
 //      floor(b 2^(64-log2b) Q / 2^64) to the next bucket's start; one warp per
 //      bucket edge finds jb[b] = #{j : P_j <= that u} by a 32-ary search;
 //   5. resolve: one block per bucket stages P[jb[b] .. jb[b+1]) and the
-//      states x[jb[b] .. jb[b+1]] in shared memory, counts P_j <= u_i there for
-//      every particle of the bucket (its index and uniform were filed by
-//      kernels 1 and 2), gathers and mutates, and writes the particle's new
-//      state; a
+//      states x[jb[b] .. jb[b+1]] in shared memory, files the staged P_j into
+//      equal bins of the bucket's u interval (a shared-memory histogram and
+//      its scan: a guide table), counts P_j <= u_i there for every particle of
+//      the bucket from its bin's first index (its index was filed by kernels
+//      1 and 2), gathers and mutates, and writes the particle's new state; a
 //      bucket whose index range is longer than the staging buffer, and the
 //      overflow list, search P in global memory (r_i again from its counter);
 //   6. advance: one thread clears the overflow counts and advances n.
@@ -453,17 +454,29 @@ __global__ void __launch_bounds__(kBlock) global_bounds_kernel(const __grid_cons
   if (lane == 0) gp.jb[b] = lo;
 }
 
+static_assert(kGuideBins % kBlock == 0, "guide bins are scanned kGuideBins / kBlock per thread");
+
+// Bin of a value v of the bucket's u interval [ulo, ulo + W) among the
+// kGuideBins bins of the guide table: a monotone function of v (every step
+// rounds monotonically), which is all the exact count below relies on.
+__device__ __forceinline__ uint32_t guide_bin(unsigned long long v, unsigned long long ulo, float scale) {
+  const float f = __ull2float_rz(v - ulo) * scale;
+  return min((uint32_t)f, kGuideBins - 1u);
+}
+
 // Ancestor, gather and mutation of particle i with uniform r.  Its ancestor
 // lies in [lo, lo + len]: ancestor = lo + #{j in [lo, lo + len) : P_j <= u},
-// counted in the staged copy (sP; states sX with row stride SC + 1) or in
-// global memory.
+// counted in the staged copy (sP, with the guide table sG[t] = #{staged P_j
+// of a bin before t}; states sX with row stride SC + 1) or in global memory.
+// In the staged copy every P_j of a bin before u's is <= u and every P_j of a
+// later bin is > u, so the count starts at sG[bin(u)] and scans u's own bin.
 template <int D, int KIND>
 __device__ __forceinline__ void resolve_draw(const StepParams& p, const GlobalParams& gp, const float* __restrict__ Xin,
                                              float* __restrict__ Xout, unsigned long long Q, uint32_t n, uint32_t i,
                                              bool staged, uint32_t lo, uint32_t len,
-                                             const unsigned long long* sP, const float* sX) {
+                                             const unsigned long long* sP, const float* sX, const uint32_t* sG,
+                                             unsigned long long ulo, float scale) {
   constexpr uint32_t SC = global_stage_alloc(D);
-  static_assert((SC & (SC - 1)) == 0, "staging buffer must hold a power of two of indices");
   const uint32_t N = p.N;
   const unsigned long long r = draw_uniform(p, i, n);
   uint32_t anc = i;                                // an all-zero population keeps its particles
@@ -471,8 +484,9 @@ __device__ __forceinline__ void resolve_draw(const StepParams& p, const GlobalPa
   if (Q != 0) {
     const unsigned long long u = __umul64hi(r, Q);
     uint32_t c = 0;
-    if (staged) {                                  // sP padded with 2^64 - 1 up to the power of two above len
-      for (uint32_t stp = (1u << (32 - __clz(len))) >> 1; stp; stp >>= 1) c += (sP[c + stp - 1u] <= u) ? stp : 0u;
+    if (staged) {
+      c = sG[guide_bin(u, ulo, scale)];
+      while (c < len && sP[c] <= u) ++c;
 #pragma unroll
       for (int t = 0; t < D; ++t) xh[t] = sX[t * (SC + 1u) + c];
     } else {
@@ -516,6 +530,8 @@ __global__ void __launch_bounds__(kBlock) global_resolve_kernel(const __grid_con
   extern __shared__ __align__(16) unsigned char s_dyn[];
   unsigned long long* const sP = reinterpret_cast<unsigned long long*>(s_dyn);   // [SC]
   float* const sX = reinterpret_cast<float*>(sP + SC);                            // [D][SC + 1]
+  uint32_t* const sG = reinterpret_cast<uint32_t*>(sX + D * (SC + 1u));           // [kGuideBins]
+  __shared__ uint32_t s_wsum[kBlock / 32];
   DevState* st = p.st;
   const uint32_t n = st->n;
   const uint32_t N = p.N;
@@ -532,27 +548,59 @@ __global__ void __launch_bounds__(kBlock) global_resolve_kernel(const __grid_con
   // two latencies overlap
   const bool first = tid < filled;
   const uint32_t e_first = first ? __ldcs(gp.slot + s0 + tid) : 0u;
+  // the bucket's u interval [ulo, ulo + W) and the scale of its guide bins
+  const unsigned long long ulo = (gp.log2b && b) ? __umul64hi((unsigned long long)b << (64u - gp.log2b), Q) : 0ull;
+  const unsigned long long uhi = (b + 1u < gp.buckets) ? __umul64hi((unsigned long long)(b + 1u) << (64u - gp.log2b), Q) : Q;
+  const float scale = (float)kGuideBins / fmaxf(__ull2float_ru(uhi - ulo), 1.0f);
   if (staged) {
-    const uint32_t p2 = 1u << (32 - __clz(len));   // power of two above len (<= SC)
-    for (uint32_t j = tid; j < p2; j += kBlock) sP[j] = (j < len) ? __ldcg(gp.P + lo + j) : ~0ull;
+    for (uint32_t j = tid; j < len; j += kBlock) sP[j] = __ldcg(gp.P + lo + j);
 #pragma unroll
     for (int t = 0; t < D; ++t)
       for (uint32_t j = tid; j <= len; j += kBlock) sX[t * (SC + 1u) + j] = __ldg(Xin + (size_t)t * N + lo + j);
+    for (uint32_t k = tid; k < kGuideBins; k += kBlock) sG[k] = 0u;
+  }
+  __syncthreads();
+  if (staged) {                                    // guide table: histogram of the bins, then its scan
+    for (uint32_t j = tid; j < len; j += kBlock) atomicAdd(sG + guide_bin(sP[j], ulo, scale), 1u);
+    __syncthreads();
+    constexpr uint32_t E = kGuideBins / kBlock;    // consecutive bins per thread
+    uint32_t cnt[E], sum = 0;
+#pragma unroll
+    for (uint32_t e = 0; e < E; ++e) {
+      cnt[e] = sG[tid * E + e];
+      sum += cnt[e];
+    }
+    const uint32_t lane = tid & 31u, warp = tid >> 5;
+    uint32_t incl = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const uint32_t v = __shfl_up_sync(0xffffffffu, incl, off);
+      if ((int)lane >= off) incl += v;
+    }
+    if (lane == 31) s_wsum[warp] = incl;
+    __syncthreads();
+    uint32_t base = incl - sum;
+    for (uint32_t w = 0; w < warp; ++w) base += s_wsum[w];
+#pragma unroll
+    for (uint32_t e = 0; e < E; ++e) {
+      sG[tid * E + e] = base;
+      base += cnt[e];
+    }
   }
   __syncthreads();
   if (tid == 0) {                                  // zero the counters for the next step
     gp.cnt[b] = 0;                                 // (read above by every thread)
     if (b < (1u << gp.cbits)) gp.ccnt[b] = 0;
   }
-  if (first) resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, e_first, staged, lo, len, sP, sX);
+  if (first) resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, e_first, staged, lo, len, sP, sX, sG, ulo, scale);
   for (uint32_t e = tid + kBlock; e < filled; e += kBlock) {
     const uint32_t i = __ldcs(gp.slot + s0 + e);
-    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, staged, lo, len, sP, sX);
+    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, staged, lo, len, sP, sX, sG, ulo, scale);
   }
   const uint32_t nov = __ldcg(gp.cnt + gp.buckets);
   for (uint32_t e = b * kBlock + tid; e < nov; e += gridDim.x * kBlock) {
     const uint32_t i = __ldcg(gp.ovf + e);
-    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, false, 0u, N, sP, sX);
+    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, false, 0u, N, sP, sX, sG, 0ull, 0.0f);
   }
 }
 
