@@ -41,7 +41,7 @@ typedef enum {
     PF_EINVAL = 1,    /* invalid argument: sizes, radices, model, null pointers   */
     PF_ENOMEM = 2,    /* workspace too small or device allocation failed          */
     PF_ECUDA = 3,     /* a CUDA runtime call failed (message has the CUDA error)   */
-    PF_ETIMEOUT = 4,  /* a bounded device-side wait gave up                        */
+    PF_ETIMEOUT = 4,  /* reserved (no kernel of the library waits on another)       */
     PF_ESTATE = 5     /* call not valid in the handle's current state              */
 } pf_status;
 
@@ -131,11 +131,6 @@ typedef struct {
  * uniform with; read by pf_get_draw_prefix).  Implies PF_RECORD_ANCESTORS and
  * its limits.  Adds 8N bytes of workspace. */
 #define PF_RECORD_DRAWS 128u
-/* Test hook for failure reporting (global resampling with N > 4096 only):
- * the second scan tile waits on a flag that nothing sets, so its bounded wait
- * runs out (well under a second) every step, status bit 2 is set and
- * pf_loglik returns PF_ETIMEOUT.  The results of such a filter are invalid. */
-#define PF_TEST_SCAN_TIMEOUT 0x80000000u
 /* Test hook for the global-resampling draws (radices = {N}, N > 1024): every
  * bucket of draws holds 16 particles and stages at most 64 indices, so most
  * draws go through the overflow list and most buckets search P in global
@@ -222,8 +217,7 @@ pf_status pf_push_observations(pf_handle* h, const float* y, int32_t T);
 pf_status pf_advance(pf_handle* h, int32_t T, float* means, double* loglik_incs, float* ess);
 
 /* Cumulative log-likelihood estimate log p^(y_0..y_{n-1}) accumulated in
- * FP64 across time.  Synchronises the stream.  Returns PF_ETIMEOUT (value
- * still written) if a bounded device-side wait gave up (status bit 2). */
+ * FP64 across time.  Synchronises the stream. */
 pf_status pf_loglik(const pf_handle* h, double* out);
 
 /*
@@ -266,8 +260,7 @@ pf_status pf_get_draw_prefix(const pf_handle* h, uint64_t* prefix);
 
 /* Sticky device-side status bits of the handle (0 = none): bit 0 = a
  * non-finite log-weight was seen and treated as weight zero; bit 1 = a group
- * had zero total weight and kept its particles; bit 2 = a bounded wait of the
- * global-resampling scan gave up (results invalid).  Synchronises. */
+ * had zero total weight and kept its particles.  Synchronises. */
 pf_status pf_get_status(const pf_handle* h, uint32_t* bits);
 
 /*

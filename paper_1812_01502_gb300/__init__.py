@@ -34,7 +34,6 @@ PF_ADAPTIVE = 4
 PF_ROTATE = 8
 PF_ISLANDS = 16
 PF_ISLANDS_PLAIN = 32
-PF_TEST_SCAN_TIMEOUT = 0x80000000
 PF_TEST_SMALL_BUCKETS = 0x40000000
 PF_DIGIT_SETS = 64
 PF_RECORD_DRAWS = 128

@@ -39,7 +39,6 @@ constexpr uint32_t kPurposeIsland = 4;       // island-level draws of augmented 
 
 constexpr uint32_t kStatusNonFinite = 1u;
 constexpr uint32_t kStatusZeroGroup = 2u;
-constexpr uint32_t kStatusTimeout = 4u;    // a bounded wait gave up (global scan)
 
 enum ModelKind : int { kLinearGaussian = 1, kStochVol = 2 };
 
@@ -273,7 +272,6 @@ struct DevState {
   double loglik;       // cumulative log-likelihood (FP64)
   float gmax;          // global resampling: maximum log-weight of the step
   uint32_t done2;      // reserved (zero)
-  unsigned long long ticket;   // global resampling: scan tiles handed out so far
   uint32_t stage;      // next stage of time step n (0 unless every stage runs in each step)
   // fully adapted schedule (per-particle carried weights)
   uint32_t lvp;        // which lV buffer holds the current weights

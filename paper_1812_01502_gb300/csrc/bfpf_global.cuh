@@ -18,9 +18,9 @@ struct GlobalParams {
   float* xbuf[2];                 // states, ping-pong by time-step parity (gather is random)
   float* lw;                      // [N] log-weights of the step
   unsigned long long* P;          // [N] inclusive prefix sums of the integer weights
-  unsigned long long* agg;        // [nscan] scan tile aggregates
-  unsigned long long* incl;       // [nscan] scan tile inclusive prefixes
-  uint32_t* flag;                 // [nscan] 2n+1: aggregate ready, 2n+2: prefix ready (step n)
+  unsigned long long* tsum;       // [nscan] integer-weight sum of every scan tile
+  unsigned long long* toff;       // [nscan + 1] tile offsets (exclusive prefix of tsum); toff[nscan] = Q
+  uint32_t* done;                 // blocks of the reduce pass finished (zero between steps)
   // A filed draw is its particle index i: the uniform r_i is a function of the
   // counter (i/2, n, 3, 0), recomputed wherever it is needed.
   uint32_t* slot;                 // [buckets][cap] draws filed by bucket
@@ -36,7 +36,6 @@ struct GlobalParams {
                                   // capacity, refine blocks per coarse bin
   uint32_t cap;                   // slots per bucket
   uint32_t stage_cap;             // longest index range staged in shared memory (<= global_stage_alloc(d))
-  uint32_t stall_tile;            // test hook (0 = off): this scan tile waits on a flag nothing sets
 };
 
 // Consecutive particles per thread of the global weight kernel.

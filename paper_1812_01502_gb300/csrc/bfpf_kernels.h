@@ -37,9 +37,9 @@ const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt, bo
 // taking (StepParams, GlobalParams).
 struct GlobalKernels {
   const void* weight;
-  const void* scan;
   const void* refine;
-  const void* bounds;
+  const void* reduce;
+  const void* scan;
   const void* resolve;
   const void* advance;
 };

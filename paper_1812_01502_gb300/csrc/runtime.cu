@@ -43,7 +43,7 @@ size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
   size_t st, x, lv0, lv1, anc, prec, partials, y_ring, inc_ring, mean_ring, ess_ring, total;
-  size_t x2, lw, P, agg, incl, flag;        // global resampling only (x2: also AIRPF)
+  size_t x2, lw, P, tsum, toff, done;       // global resampling only (x2: also AIRPF)
   size_t slot, cnt, ovf, jb, cslot, ccnt, covf;   // global resampling: draws filed by coarse bin, then bucket
   size_t src;                               // AIRPF: island sources
 };
@@ -301,15 +301,17 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     if (!select_global_kernels(d, pl.kind, pl.gk)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
     if (!select_kernels(d, pl.kind, true, pl.ks)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
     pl.nscan = (pl.N + kScanTile - 1) / kScanTile;
-    // Draws are resolved per bucket of their uniform: about stage_cap / 4 to
-    // stage_cap / 2 draws per bucket, so that a bucket's index range normally
-    // fits the shared-memory staging buffer (8 + 4 d bytes per index).
+    // Draws are resolved per bucket of their uniform: about stage_cap / 2 to
+    // stage_cap draws per bucket (a population in random index order puts
+    // about as many prefix sums as draws in a bucket's u interval), so that a
+    // bucket's index range normally fits the shared-memory staging buffer
+    // (8 + 4 d bytes per index).
     const bool small_buckets = opts && (opts->flags & PF_TEST_SMALL_BUCKETS);
     pl.stage_cap = global_stage_alloc(d);
     uint32_t lgN = 0, lgc = 0;
     while ((2ull << lgN) <= pl.N) ++lgN;            // floor(log2 N)
     while ((2u << lgc) <= pl.stage_cap) ++lgc;      // log2 stage_cap
-    pl.log2b = lgN > lgc - 2 ? std::min<uint32_t>(lgN - (lgc - 2), 24u) : 0u;
+    pl.log2b = lgN > lgc - 1 ? std::min<uint32_t>(lgN - (lgc - 1), 24u) : 0u;
     pl.buckets = 1u << pl.log2b;
     const uint32_t mu = (uint32_t)((pl.N + pl.buckets - 1) / pl.buckets);
     const uint32_t sd = (uint32_t)std::ceil(std::sqrt((double)mu));
@@ -601,9 +603,9 @@ pf_status finish_plan_global(Plan& pl, const pf_options* opts, int sms, std::str
   L.covf = take((size_t)4 * pl.N);
   L.ovf = take((size_t)4 * pl.N);
   L.jb = take((size_t)4 * (pl.buckets + 1u));
-  L.agg = take((size_t)8 * pl.nscan);
-  L.incl = take((size_t)8 * pl.nscan);
-  L.flag = take((size_t)4 * pl.nscan);
+  L.tsum = take((size_t)8 * pl.nscan);
+  L.toff = take((size_t)8 * (pl.nscan + 1u));
+  L.done = take(4);
   L.total = off;
   return PF_OK;
 }
@@ -677,9 +679,8 @@ cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
     if (e == cudaSuccess)
       e = cudaLaunchKernel(h->plan.gk.refine, dim3((1u << h->plan.cbits) * h->plan.nseg), dim3(kBlock), args,
                            h->plan.smem_refine, stream);
+    if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.reduce, dim3(h->plan.nscan), dim3(kBlock), args, 0, stream);
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.scan, dim3(h->plan.nscan), dim3(kBlock), args, 0, stream);
-    const uint32_t nbw = (uint32_t)(((uint64_t)(h->plan.buckets + 1u) * 32u + kBlock - 1) / kBlock);
-    if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.bounds, dim3(nbw), dim3(kBlock), args, 0, stream);
     if (e == cudaSuccess)
       e = cudaLaunchKernel(h->plan.gk.resolve, dim3(h->plan.buckets), dim3(kBlock), args, h->plan.smem_resolve, stream);
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.advance, dim3(1), dim3(32), args, 0, stream);
@@ -842,9 +843,9 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
     G.xbuf[1] = reinterpret_cast<float*>(h->ws + L.x2);
     G.lw = reinterpret_cast<float*>(h->ws + L.lw);
     G.P = reinterpret_cast<unsigned long long*>(h->ws + L.P);
-    G.agg = reinterpret_cast<unsigned long long*>(h->ws + L.agg);
-    G.incl = reinterpret_cast<unsigned long long*>(h->ws + L.incl);
-    G.flag = reinterpret_cast<uint32_t*>(h->ws + L.flag);
+    G.tsum = reinterpret_cast<unsigned long long*>(h->ws + L.tsum);
+    G.toff = reinterpret_cast<unsigned long long*>(h->ws + L.toff);
+    G.done = reinterpret_cast<uint32_t*>(h->ws + L.done);
     G.slot = reinterpret_cast<uint32_t*>(h->ws + L.slot);
     G.cnt = reinterpret_cast<uint32_t*>(h->ws + L.cnt);
     G.ovf = reinterpret_cast<uint32_t*>(h->ws + L.ovf);
@@ -860,7 +861,6 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
     G.buckets = pl.buckets;
     G.cap = pl.bucket_cap;
     G.stage_cap = pl.stage_cap;
-    G.stall_tile = (opts && (opts->flags & PF_TEST_SCAN_TIMEOUT) && pl.nscan > 1) ? 1u : 0u;
   }
 
   // Algorithm 1, first loop: zeta_0 ~ pi_0; carried weights start at zero.
@@ -877,7 +877,7 @@ pf_status pf_create(const pf_model* model, int64_t N, const int32_t* radices, in
                       h->stream);
   if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
   if (pl.global) {
-    e = cudaMemsetAsync(h->ws + L.flag, 0, (size_t)4 * pl.nscan, h->stream);
+    e = cudaMemsetAsync(h->ws + L.done, 0, 4, h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.cnt, 0, (size_t)4 * (pl.buckets + 1u), h->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(h->ws + L.ccnt, 0, (size_t)4 * ((1u << pl.cbits) + 1u), h->stream);
     if (e != cudaSuccess) return bail(e, "cudaMemsetAsync");
@@ -1010,8 +1010,6 @@ pf_status pf_loglik(const pf_handle* h, double* out) {
   PF_CUDA(h, cudaMemcpyAsync(&st, h->P.st, sizeof(st), cudaMemcpyDeviceToHost, h->stream));
   PF_CUDA(h, cudaStreamSynchronize(h->stream));
   *out = st.loglik;
-  if (st.status & kStatusTimeout)
-    return fail(h, PF_ETIMEOUT, "a bounded device-side wait gave up; this filter's results are not valid");
   return PF_OK;
 }
 

@@ -17,13 +17,15 @@
 //      b = top log2b bits of r_i (fixed capacity per bucket, an overflow list
 //      behind it); r_i is recomputed from its counter, so a filed draw is
 //      only its 4-byte index;
-//   3. scan: single-pass decoupled look-back prefix sum of q (tiles handed
-//      out by an atomic ticket so a tile only waits on tiles already running;
-//      waits are bounded and report kStatusTimeout), loads and stores staged
-//      through shared memory so that both are coalesced;
-//   4. bounds: u is monotone in r, so bucket b covers the u interval from
-//      floor(b 2^(64-log2b) Q / 2^64) to the next bucket's start; one warp per
-//      bucket edge finds jb[b] = #{j : P_j <= that u} by a 32-ary search;
+//   3. reduce: the integer weights q_i = floor(exp(lw_i - max lw) 2^32) summed
+//      per tile of 4096 particles; the last block turns the tile sums into
+//      tile offsets and the total Q;
+//   4. scan: every tile's prefix sums P from its offset (loads and stores
+//      staged through shared memory so that both are coalesced), and the
+//      bucket edges: u is monotone in r, so bucket b covers the u interval
+//      from u_b = floor(b 2^(64-log2b) Q / 2^64) to the next bucket's start,
+//      and jb[b] = #{j : P_j <= u_b} is the particle j with
+//      P_{j-1} <= u_b < P_j, found by the thread that holds it;
 //   5. resolve: one block per bucket stages P[jb[b] .. jb[b+1]) and the
 //      states x[jb[b] .. jb[b+1]] in shared memory, files the staged P_j into
 //      equal bins of the bucket's u interval (a shared-memory histogram and
@@ -33,6 +35,7 @@
 //      bucket whose index range is longer than the staging buffer, and the
 //      overflow list, search P in global memory (r_i again from its counter);
 //   6. advance: one thread clears the overflow counts and advances n.
+// No kernel waits on another block.
 // Every particle's ancestor is #{j : P_j <= u_i} whatever the bucket layout:
 // bucketing only decides where the count is taken.
 #include <cfloat>
@@ -46,15 +49,6 @@
 namespace bfpf {
 
 namespace {
-
-constexpr uint32_t kSpinLimit = 1u << 20;   // bounded wait on a predecessor tile (well under a second)
-
-__device__ __forceinline__ unsigned long long ld_volatile_u64(const unsigned long long* p) {
-  return *reinterpret_cast<const volatile unsigned long long*>(p);
-}
-__device__ __forceinline__ uint32_t ld_volatile_u32(const uint32_t* p) {
-  return *reinterpret_cast<const volatile uint32_t*>(p);
-}
 
 }  // namespace
 
@@ -287,22 +281,111 @@ __global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_cons
     file_direct(p, gp, __ldcg(gp.covf + e), n);
 }
 
+// Integer weight of log-weight lw, with the population's maximum log-weight
+// gmax weighing exactly 2^32 (the same on both scan passes).
+__device__ __forceinline__ unsigned long long global_qweight(float lw, float gmax) {
+  return __float2ull_rz(exp_weight(lw - gmax) * 4294967296.0f);
+}
+
+// 3a. reduce: the sum of the integer weights of every scan tile; the last
+// block to finish turns the tile sums into tile offsets (their exclusive
+// prefix sums) and the total Q, toff[nscan].
+__global__ void __launch_bounds__(kBlock) global_reduce_kernel(const __grid_constant__ StepParams p,
+                                                              const __grid_constant__ GlobalParams gp) {
+  __shared__ unsigned long long s_warp[kBlock / 32];
+  __shared__ bool s_last;
+  const uint32_t N = p.N;
+  const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
+  const float gmax = p.st->gmax;
+  const uint32_t tbase = blockIdx.x * kScanTile;
+  unsigned long long sum = 0;
+  if (gmax != -INFINITY) {
+#pragma unroll
+    for (int k = 0; k < kScanItems; ++k) {         // the scan pass reads the tile again, from L2
+      const uint32_t idx = tbase + k * kBlock + tid;
+      if (idx < N) sum += global_qweight(__ldcg(gp.lw + idx), gmax);
+    }
+  }
+#pragma unroll
+  for (int off = 16; off; off >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, off);
+  if (lane == 0) s_warp[warp] = sum;
+  __syncthreads();
+  if (tid == 0) {
+    unsigned long long tsum = 0;
+#pragma unroll
+    for (int w = 0; w < kBlock / 32; ++w) tsum += s_warp[w];
+    gp.tsum[blockIdx.x] = tsum;
+    __threadfence();
+    s_last = atomicAdd(gp.done, 1u) == gp.nscan - 1u;
+  }
+  __syncthreads();
+  if (!s_last) return;
+  // last block: exclusive prefix of the tile sums, E consecutive tiles per thread
+  __threadfence();
+  const uint32_t nt = gp.nscan;
+  const uint32_t E = (nt + kBlock - 1u) / kBlock;
+  const uint32_t k0 = min(tid * E, nt), k1 = min(k0 + E, nt);
+  unsigned long long tot = 0;
+  for (uint32_t k = k0; k < k1; ++k) tot += __ldcg(gp.tsum + k);
+  unsigned long long incl = tot;
+#pragma unroll
+  for (int off = 1; off < 32; off <<= 1) {
+    const unsigned long long v = __shfl_up_sync(0xffffffffu, incl, off);
+    if ((int)lane >= off) incl += v;
+  }
+  __syncthreads();                                 // s_warp is reused
+  if (lane == 31) s_warp[warp] = incl;
+  __syncthreads();
+  unsigned long long run = incl - tot;
+  for (int w = 0; w < (int)warp; ++w) run += s_warp[w];
+  for (uint32_t k = k0; k < k1; ++k) {
+    gp.toff[k] = run;
+    run += __ldcg(gp.tsum + k);
+  }
+  if (tid == kBlock - 1) {
+    gp.toff[nt] = run;                             // Q: the last thread's running sum ends at the total
+    *gp.done = 0;                                  // ready for the next step
+  }
+}
+
+// Bucket edge b: the smallest u of bucket b, floor(b 2^(64-log2b) Q / 2^64);
+// Q itself for b = buckets (a bound above every u).
+__device__ __forceinline__ unsigned long long edge_u(uint32_t b, unsigned long long Q, uint32_t log2b,
+                                                     uint32_t buckets) {
+  if (b >= buckets) return Q;
+  return log2b ? __umul64hi((unsigned long long)b << (64u - log2b), Q) : 0ull;
+}
+
+// #{b in [0, buckets) : edge_u(b) < v} for 0 <= v <= Q: a float estimate of
+// ceil(v buckets / Q), corrected to the exact count (the edges are
+// non-decreasing in b, so each loop only moves toward the answer).
+__device__ __forceinline__ uint32_t edges_below(unsigned long long v, unsigned long long Q, uint32_t log2b,
+                                                uint32_t buckets) {
+  if (v == 0) return 0;
+  const float est = ceilf(__ull2float_rn(v) / __ull2float_rn(Q) * (float)buckets);
+  uint32_t b = (uint32_t)fminf(fmaxf(est, 0.0f), (float)buckets);
+  while (b > 0 && edge_u(b - 1u, Q, log2b, buckets) >= v) --b;
+  while (b < buckets && edge_u(b, Q, log2b, buckets) < v) ++b;
+  return b;
+}
+
+// 3b. scan: the prefix sums of one tile from its offset (no waiting on other
+// tiles: the offsets come from the reduce pass), and the bucket edges that
+// fall in the tile.  Edge b belongs to the particle j with P_{j-1} <= u_b < P_j
+// (P_{-1} = 0), and then jb[b] = #{P <= u_b} = j; the last edge, u = Q - 1,
+// likewise.  Loads and stores of the tile are staged through shared memory so
+// that both are coalesced.
 __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_constant__ StepParams p,
                                                             const __grid_constant__ GlobalParams gp) {
   // the tile's log-weights, then its prefix sums, one padding word every 32
   // floats / 16 doubles so that thread-contiguous accesses hit distinct banks
   __shared__ unsigned long long s_buf[kScanTile + kScanTile / 16];
   __shared__ unsigned long long s_warp[kBlock / 32];
-  __shared__ unsigned long long s_prefix;
-  __shared__ uint32_t s_tile;
   DevState* st = p.st;
-  const uint32_t n = st->n;
   const uint32_t N = p.N;
   const float gmax = st->gmax;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-  if (tid == 0) s_tile = (uint32_t)(atomicAdd(&st->ticket, 1ull) - (unsigned long long)n * gp.nscan);
-  __syncthreads();
-  const uint32_t tile = s_tile;
+  const uint32_t tile = blockIdx.x;
   const uint32_t tbase = tile * kScanTile;
   float* const s_f = reinterpret_cast<float*>(s_buf);
 #pragma unroll
@@ -319,12 +402,7 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
   for (int q = 0; q < kScanItems; ++q) {
     const uint32_t idx = tid * kScanItems + q;
     const float lw = s_f[idx + (idx >> 5)];
-    unsigned long long w = 0;
-    if (gmax != -INFINITY) {
-      const float e = exp_weight(lw - gmax);
-      w = __float2ull_rz(e * 4294967296.0f);
-    }
-    tot += w;
+    tot += (gmax != -INFINITY) ? global_qweight(lw, gmax) : 0ull;
     run[q] = tot;
   }
   // block-wide exclusive scan of the thread totals
@@ -335,85 +413,13 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
     if ((int)lane >= off) incl += v;
   }
   if (lane == 31) s_warp[warp] = incl;
-  __syncthreads();
-  if (warp == 0) {
-    unsigned long long v = (lane < kBlock / 32) ? s_warp[lane] : 0ull;
-#pragma unroll
-    for (int off = 1; off < kBlock / 32; off <<= 1) {
-      const unsigned long long o = __shfl_up_sync(0xffffffffu, v, off);
-      if ((int)lane >= off) v += o;
-    }
-    if (lane < kBlock / 32) s_warp[lane] = v;   // inclusive over warps
-  }
-  __syncthreads();
-  const unsigned long long warp_excl = (warp == 0) ? 0ull : s_warp[warp - 1];
-  const unsigned long long thread_excl = warp_excl + incl - tot;
-  const unsigned long long tile_total = s_warp[kBlock / 32 - 1];
-  // decoupled look-back by warp 0, 32 predecessor tiles per round: every lane
-  // waits (bounded) for its tile's aggregate or inclusive prefix; the nearest
-  // tile with an inclusive prefix ends the walk
-  if (warp == 0) {
-    const uint32_t f_agg = 2u * n + 1u, f_pre = 2u * n + 2u;
-    unsigned long long prefix = 0;
-    if (tile == 0) {
-      if (lane == 0) {
-        gp.incl[0] = tile_total;
-        __threadfence();
-        atomicExch(gp.flag, f_pre);
-      }
-    } else {
-      if (lane == 0) {
-        gp.agg[tile] = tile_total;
-        __threadfence();
-        atomicExch(gp.flag + tile, f_agg);
-      }
-      // test hook: the stalled tile recognises no flag, so its wait runs out
-      const bool stall = gp.stall_tile != 0 && tile == gp.stall_tile;
-      bool timed_out = false;
-      int32_t base = (int32_t)tile - 1;
-      while (true) {
-        const int32_t t = base - (int32_t)lane;
-        uint32_t f = f_pre;                       // before tile 0: an inclusive prefix of 0
-        unsigned long long v = 0;
-        if (t >= 0) {
-          uint32_t spins = 0;
-          f = stall ? 0u : ld_volatile_u32(gp.flag + t);
-          while (f != f_agg && f != f_pre) {
-            if (++spins > kSpinLimit) {
-              timed_out = true;                   // counted as an aggregate of 0
-              break;
-            }
-            __nanosleep(32);
-            f = stall ? 0u : ld_volatile_u32(gp.flag + t);
-          }
-          __threadfence();
-          if (f == f_pre) v = ld_volatile_u64(gp.incl + t);
-          else if (f == f_agg) v = ld_volatile_u64(gp.agg + t);
-        }
-        const unsigned ready = __ballot_sync(0xffffffffu, f == f_pre);
-        const int first = ready ? __ffs(ready) - 1 : 32;   // nearest tile with a prefix
-        unsigned long long c = ((int)lane <= first) ? v : 0ull;
-#pragma unroll
-        for (int off = 16; off; off >>= 1) c += __shfl_xor_sync(0xffffffffu, c, off);
-        prefix += c;
-        if (ready) break;
-        base -= 32;
-      }
-      if (__any_sync(0xffffffffu, timed_out) && lane == 0) atomicOr(&st->status, kStatusTimeout);
-      if (lane == 0) {
-        gp.incl[tile] = prefix + tile_total;
-        __threadfence();
-        atomicExch(gp.flag + tile, f_pre);
-      }
-    }
-    if (lane == 0) s_prefix = prefix;
-  }
-  __syncthreads();
-  const unsigned long long off0 = s_prefix + thread_excl;
+  __syncthreads();                                 // (also: every thread has read its log-weights)
+  unsigned long long lo = __ldcg(gp.toff + tile) + incl - tot;   // P before my first particle
+  for (int w = 0; w < (int)warp; ++w) lo += s_warp[w];
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
     const uint32_t idx = tid * kScanItems + q;
-    s_buf[idx + (idx >> 4)] = off0 + run[q];
+    s_buf[idx + (idx >> 4)] = lo + run[q];
   }
   __syncthreads();
 #pragma unroll
@@ -421,37 +427,35 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
     const uint32_t idx = k * kBlock + tid;
     if (tbase + idx < N) gp.P[tbase + idx] = s_buf[idx + (idx >> 4)];
   }
-}
-
-// jb[b] = #{j : P_j <= u_b} for every bucket edge b = 0 .. buckets, with u_b
-// the smallest u of bucket b (u_buckets = Q - 1, the largest u of all): one
-// warp per edge, 32 probes per round (P is non-decreasing, so the probes at or
-// below u form a prefix of the warp).
-__global__ void __launch_bounds__(kBlock) global_bounds_kernel(const __grid_constant__ StepParams p,
-                                                              const __grid_constant__ GlobalParams gp) {
-  const uint32_t lane = threadIdx.x & 31u;
-  const uint32_t b = (blockIdx.x * kBlock + threadIdx.x) >> 5;
-  if (b > gp.buckets) return;                     // whole warps
-  const uint32_t N = p.N;
-  const unsigned long long Q = __ldcg(gp.P + (N - 1u));
-  uint32_t lo = 0;
+  // bucket edges u_b in [lo, hi): usually none in one thread's 16 particles
+  const unsigned long long Q = __ldcg(gp.toff + gp.nscan);
+  const uint32_t j0 = tbase + tid * kScanItems;
   if (Q != 0) {
-    unsigned long long u = 0;
-    if (b == gp.buckets) u = Q - 1u;
-    else if (gp.log2b) u = __umul64hi((unsigned long long)b << (64u - gp.log2b), Q);
-    // invariant: P_j <= u for j < lo, P_j > u for j >= lo + span
-    uint32_t span = N;
-    while (span) {
-      const uint32_t s = (span - 1u) / 32u + 1u;
-      const unsigned long long off = (unsigned long long)(lane + 1u) * s;
-      const bool le = off <= span && __ldcg(gp.P + lo + (uint32_t)(off - 1u)) <= u;
-      const uint32_t c = __popc(__ballot_sync(0xffffffffu, le));
-      const uint32_t nlo = lo + c * s;
-      span = min(s - 1u, lo + span - nlo);
-      lo = nlo;
+    const unsigned long long hi = lo + tot;
+    if (hi > lo) {
+      const uint32_t L = gp.log2b, B = gp.buckets;
+      const uint32_t be = edges_below(hi, Q, L, B);
+      for (uint32_t b = edges_below(lo, Q, L, B); b < be; ++b) {
+        const unsigned long long u = edge_u(b, Q, L, B);
+        uint32_t c = 0;
+        for (int q = 0; q < kScanItems; ++q) {
+          const uint32_t idx = tid * kScanItems + q;
+          c += (s_buf[idx + (idx >> 4)] <= u) ? 1u : 0u;
+        }
+        gp.jb[b] = j0 + c;
+      }
+      if (lo <= Q - 1u && Q - 1u < hi) {           // the last edge
+        uint32_t c = 0;
+        for (int q = 0; q < kScanItems; ++q) {
+          const uint32_t idx = tid * kScanItems + q;
+          c += (s_buf[idx + (idx >> 4)] <= Q - 1u) ? 1u : 0u;
+        }
+        gp.jb[B] = j0 + c;
+      }
     }
+  } else {                                         // no weight anywhere: every edge is 0
+    for (uint32_t b = tile * kBlock + tid; b <= gp.buckets; b += gridDim.x * kBlock) gp.jb[b] = 0;
   }
-  if (lane == 0) gp.jb[b] = lo;
 }
 
 static_assert(kGuideBins % kBlock == 0, "guide bins are scanned kGuideBins / kBlock per thread");
@@ -619,7 +623,7 @@ static void fill_global(GlobalKernels& gk) {
   gk.weight = reinterpret_cast<const void*>(&global_weight_kernel<D, KIND>);
   gk.scan = reinterpret_cast<const void*>(&global_scan_kernel);
   gk.refine = reinterpret_cast<const void*>(&global_refine_kernel);
-  gk.bounds = reinterpret_cast<const void*>(&global_bounds_kernel);
+  gk.reduce = reinterpret_cast<const void*>(&global_reduce_kernel);
   gk.resolve = reinterpret_cast<const void*>(&global_resolve_kernel<D, KIND>);
   gk.advance = reinterpret_cast<const void*>(&global_advance_kernel);
 }

@@ -14,9 +14,14 @@
 // sum by an in-thread scan plus a shuffle scan over the G lanes.  Prefix sums
 // and states are staged in shared memory in a [member][group] layout so that
 // the ancestor search and the gather read different banks across a warp.
-// Only warp-level synchronisation is needed inside the loop.  Loads and
-// stores go straight to global memory: for a fixed member, consecutive lanes
-// own consecutive groups, i.e. consecutive addresses when s_k >= 32.
+// With one lane per group (G = 1) only warp-level synchronisation is needed
+// inside the loop, and loads and stores go straight to global memory: for a
+// fixed member, consecutive lanes own consecutive groups, i.e. consecutive
+// addresses when s_k >= 32.  With a group spread over G > 1 lanes, a warp's
+// direct accesses would touch one sector per lane (members s_k apart); there
+// the block loads and stores its whole tile of D x A x (groups per iteration)
+// states through the state table in address order (coalesced for every
+// digit), at the price of block-wide barriers.
 //
 // Integer resampling rule (shared with the oracle): delta = fp32(lw - max),
 // e = exp(delta), q = floor(e 2^24), P = inclusive prefix, Q = P_{A-1},
@@ -41,6 +46,78 @@ namespace bfpf {
 // rotation (digit gg.k = gg.j): skipped when the ESS already reached the
 // threshold (the last launch then only mutates), per-particle carried weights
 // in and out, and the ESS of the new stage weights decides the next stage.
+// Cooperative tile of one block iteration (groups g0 .. g0 + GPB - 1 of the
+// digit with stride s = 2^log2s): element (t, member r, group gi) lives at
+// X[t N + off] and in the state table at (t A + r) LD + gi.  When s >= GPB the
+// tile's groups share h and form GPB consecutive columns of every member row
+// (off = base + r s + gi); when s < GPB (then s divides GPB and g0) its particles
+// are the consecutive range of length A GPB from base = h0 A s.  Either way
+// consecutive threads take consecutive addresses.
+// Largest divisor of n that is at most 8.
+constexpr int load_chunk(int n) {
+  int c = n < 8 ? n : 8;
+  while (n % c) --c;
+  return c;
+}
+
+template <int D, int A, int GPB, int LD>
+struct GroupTile {
+  static constexpr uint32_t kRow = (uint32_t)A * GPB;   // elements per state component
+  uint32_t base, log2s, log2as;
+  bool wide_s;                                            // s >= GPB
+  __device__ __forceinline__ GroupTile(uint32_t batch, uint32_t l2s, uint32_t l2as) : log2s(l2s), log2as(l2as) {
+    const uint32_t g0 = batch * GPB;
+    const uint32_t h0 = g0 >> l2s, l0 = g0 & ((1u << l2s) - 1u);
+    wide_s = (1u << l2s) >= (uint32_t)GPB;
+    base = (h0 << l2as) + l0;
+  }
+  // global offset (within one component row) and table index of element e of component t
+  __device__ __forceinline__ void locate(uint32_t t, uint32_t e, uint32_t& off, uint32_t& tix) const {
+    uint32_t r, gi;
+    if (wide_s) {
+      r = e / GPB;
+      gi = e % GPB;
+      off = base + (r << log2s) + gi;
+    } else {
+      r = (e >> log2s) & (A - 1u);
+      gi = ((e >> log2as) << log2s) | (e & ((1u << log2s) - 1u));
+      off = base + e;
+    }
+    tix = (t * A + r) * LD + gi;
+  }
+  __device__ __forceinline__ void load(const float* __restrict__ X, uint32_t N, uint32_t* tab) const {
+    constexpr int PER = (int)(D * kRow / kBlock);
+    static_assert(D * kRow % kBlock == 0, "tile must split evenly over the block");
+    constexpr int CH = load_chunk(PER);             // loads in flight per thread
+#pragma unroll
+    for (int c = 0; c < PER; c += CH) {
+      float v[CH];
+      uint32_t ix[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const uint32_t idx = threadIdx.x + (uint32_t)(c + q) * kBlock;
+        const uint32_t t = idx / kRow, e = idx % kRow;
+        uint32_t off;
+        locate(t, e, off, ix[q]);
+        v[q] = __ldcs(X + (size_t)t * N + off);
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q) tab[ix[q]] = __float_as_uint(v[q]);
+    }
+  }
+  __device__ __forceinline__ void store(float* __restrict__ X, uint32_t N, const uint32_t* tab) const {
+    constexpr int PER = (int)(D * kRow / kBlock);
+#pragma unroll 4
+    for (int q = 0; q < PER; ++q) {
+      const uint32_t idx = threadIdx.x + (uint32_t)q * kBlock;
+      const uint32_t t = idx / kRow, e = idx % kRow;
+      uint32_t off, tix;
+      locate(t, e, off, tix);
+      __stcs(X + (size_t)t * N + off, __uint_as_float(tab[tix]));
+    }
+  }
+};
+
 template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
 __device__ __forceinline__ void step_group_body(const StepParams& p, const GroupGeom& gg) {
   static_assert(A >= 2 && A <= 32 && (A & (A - 1)) == 0, "radix must be a power of two <= 32");
@@ -58,6 +135,8 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
   __shared__ __align__(16) uint32_t s_rows[GPB * RS];
   // states, [t][member][group]: the gather of a warp reads distinct banks
   __shared__ uint32_t s_tab[D * A * LD];
+  // tile through the state table (block barriers) for groups over several lanes
+  constexpr bool COAL = (G > 1) && !ADAPT;
 
   const uint32_t tid = threadIdx.x;
   const uint32_t tg = tid / G, j = tid % G;
@@ -107,7 +186,17 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
     // ---- load my members, weight them (lw = log V + log g_n - mu) ----
     float xv[M][D];
     float lw[M];
-    if (contiguous) {
+    if constexpr (COAL) {
+      __syncthreads();                               // the previous iteration's store has read the table
+      GroupTile<D, A, GPB, LD>(batch, log2s, log2as).load(X, N, s_tab);
+      __syncthreads();
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm) {
+#pragma unroll
+        for (int t = 0; t < D; ++t) xv[mm][t] = __uint_as_float(col[(t * A + j * M + mm) * LD]);
+        lw[mm] = __ldg(lvp + mm * gg.lv_mul);
+      }
+    } else if (contiguous) {
 #pragma unroll
       for (int q = 0; q < M / 4; ++q) {
 #pragma unroll
@@ -218,11 +307,13 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
       for (int mm = 0; mm < M; ++mm)
         if (((j * M + mm) & 3u) == 3u) row[A + ((j * M + mm) >> 2)] = P[mm];
     }
+    if constexpr (!COAL) {                           // (the cooperative load filled the table)
 #pragma unroll
-    for (int mm = 0; mm < M; ++mm) {
-      const uint32_t r = j * M + mm;
+      for (int mm = 0; mm < M; ++mm) {
+        const uint32_t r = j * M + mm;
 #pragma unroll
-      for (int t = 0; t < D; ++t) col[(t * A + r) * LD] = __float_as_uint(xv[mm][t]);
+        for (int t = 0; t < D; ++t) col[(t * A + r) * LD] = __float_as_uint(xv[mm][t]);
+      }
     }
     if constexpr (ADAPT) {           // per-particle carried weights; partial of the new stage weights
       const float lv_new = (Q != 0) ? (mx + logf(s1) - gg.log_a) : -INFINITY;
@@ -348,7 +439,15 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
         coff[mm] = c;
       }
     }
-    if (contiguous) {
+    if constexpr (COAL) {
+      __syncthreads();                               // every gather of the iteration is done
+#pragma unroll
+      for (int mm = 0; mm < M; ++mm)
+#pragma unroll
+        for (int t = 0; t < D; ++t) col[(t * A + j * M + mm) * LD] = __float_as_uint(xo[mm][t]);
+      __syncthreads();
+      GroupTile<D, A, GPB, LD>(batch, log2s, log2as).store(X, N, s_tab);
+    } else if (contiguous) {
 #pragma unroll
       for (int q = 0; q < M / 4; ++q)
 #pragma unroll
