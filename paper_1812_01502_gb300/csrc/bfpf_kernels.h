@@ -37,8 +37,7 @@ const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt, bo
 // taking (StepParams, GlobalParams).
 struct GlobalKernels {
   const void* weight;
-  const void* refine;
-  const void* reduce;
+  const void* refine_reduce;
   const void* scan;
   const void* resolve;
   const void* advance;

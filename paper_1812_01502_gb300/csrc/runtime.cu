@@ -312,6 +312,9 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     while ((2ull << lgN) <= pl.N) ++lgN;            // floor(log2 N)
     while ((2u << lgc) <= pl.stage_cap) ++lgc;      // log2 stage_cap
     pl.log2b = lgN > lgc - 1 ? std::min<uint32_t>(lgN - (lgc - 1), 24u) : 0u;
+    // small populations: at least 2^8 buckets (but at least 256 draws each) so
+    // that the resolve launch has blocks for every SM
+    if (lgN >= 8u) pl.log2b = std::max<uint32_t>(pl.log2b, std::min<uint32_t>(lgN - 8u, 8u));
     pl.buckets = 1u << pl.log2b;
     const uint32_t mu = (uint32_t)((pl.N + pl.buckets - 1) / pl.buckets);
     const uint32_t sd = (uint32_t)std::ceil(std::sqrt((double)mu));
@@ -572,7 +575,7 @@ pf_status finish_plan_global(Plan& pl, const pf_options* opts, int sms, std::str
   if (e == cudaSuccess)
     e = raise_smem_limit(pl.gk.weight, pl.smem_weight);
   if (e == cudaSuccess)
-    e = raise_smem_limit(pl.gk.refine, pl.smem_refine);
+    e = raise_smem_limit(pl.gk.refine_reduce, pl.smem_refine);
   if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nw, pl.gk.weight, kBlock, pl.smem_weight);
   if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
   const int units = (int)((pl.N + kBlock - 1) / kBlock);
@@ -677,9 +680,9 @@ cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
     cudaError_t e = cudaLaunchKernel(h->plan.gk.weight, dim3(h->plan.grid_weight), dim3(kBlock), args,
                                      h->plan.smem_weight, stream);
     if (e == cudaSuccess)
-      e = cudaLaunchKernel(h->plan.gk.refine, dim3((1u << h->plan.cbits) * h->plan.nseg), dim3(kBlock), args,
-                           h->plan.smem_refine, stream);
-    if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.reduce, dim3(h->plan.nscan), dim3(kBlock), args, 0, stream);
+      e = cudaLaunchKernel(h->plan.gk.refine_reduce,
+                           dim3((h->plan.nscan > 1 ? h->plan.nscan : 0u) + (1u << h->plan.cbits) * h->plan.nseg),
+                           dim3(kBlock), args, h->plan.smem_refine, stream);
     if (e == cudaSuccess) e = cudaLaunchKernel(h->plan.gk.scan, dim3(h->plan.nscan), dim3(kBlock), args, 0, stream);
     if (e == cudaSuccess)
       e = cudaLaunchKernel(h->plan.gk.resolve, dim3(h->plan.buckets), dim3(kBlock), args, h->plan.smem_resolve, stream);

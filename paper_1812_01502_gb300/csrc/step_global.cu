@@ -7,7 +7,8 @@
 // The draw follows the same integer rule as the butterfly kernels with one
 // group of N members: q_i = floor(fp32 exp(lw_i - max lw) 2^32), P = inclusive
 // prefix (64-bit), u_i = floor(r_i Q / 2^64) with a 64-bit uniform r_i from
-// counter (i/2, n, 3, 0), ancestor = #{j : P_j <= u_i}.  Six kernels:
+// counter (i/2, n, 3, 0), ancestor = #{j : P_j <= u_i}.  Six phases in
+// five launches (2 and 3 share one):
 //   1. weights: lw_i to memory, block partials -> last block: likelihood
 //      increment, mean, ESS, the global maximum and the one group's weight;
 //      every draw (its index i) is also filed under its coarse bin (the top
@@ -30,7 +31,7 @@
 //      states x[jb[b] .. jb[b+1]] in shared memory, files the staged P_j into
 //      equal bins of the bucket's u interval (a shared-memory histogram and
 //      its scan: a guide table), counts P_j <= u_i there for every particle of
-//      the bucket from its bin's first index (its index was filed by kernels
+//      the bucket from its bin's first index (its index was filed by phases
 //      1 and 2), gathers and mutates, and writes the particle's new state; a
 //      bucket whose index range is longer than the staging buffer, and the
 //      overflow list, search P in global memory (r_i again from its counter);
@@ -247,8 +248,7 @@ __global__ void __launch_bounds__(kBlock) global_weight_kernel(const __grid_cons
 // Fine filing: block (coarse bin cb, segment sg) takes kRefineSeg entries of
 // the bin and files each under its bucket (the next log2b - cbits bits of r),
 // the same way.  Draws of the coarse overflow list are filed one by one.
-__global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_constant__ StepParams p,
-                                                              const __grid_constant__ GlobalParams gp) {
+__device__ __forceinline__ void refine_body(const StepParams& p, const GlobalParams& gp, uint32_t blk, uint32_t nblk) {
   extern __shared__ __align__(16) unsigned char s_dyn[];
   uint2* const s_buf = reinterpret_cast<uint2*>(s_dyn);                 // [kRefineSeg]
   uint32_t* const s_cnt = reinterpret_cast<uint32_t*>(s_buf + kRefineSeg);
@@ -256,7 +256,7 @@ __global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_cons
   const uint32_t n = p.st->n;
   const uint32_t cbits = gp.cbits, fbits = gp.log2b - cbits, nfine = 1u << fbits;
   uint32_t* const s_off = s_cnt + nfine;
-  const uint32_t cb = blockIdx.x / gp.nseg, sg = blockIdx.x % gp.nseg;
+  const uint32_t cb = blk / gp.nseg, sg = blk % gp.nseg;
   const uint32_t cfill = min(__ldcg(gp.ccnt + cb), gp.ccap);
   const uint32_t e0 = sg * kRefineSeg;
   if (e0 < cfill) {                                // block-uniform
@@ -277,33 +277,48 @@ __global__ void __launch_bounds__(kBlock) global_refine_kernel(const __grid_cons
                              gp.ovf, s_cnt, s_off, s_buf);
   }
   const uint32_t nco = __ldcg(gp.ccnt + (1u << cbits));
-  for (uint32_t e = blockIdx.x * kBlock + tid; e < nco; e += gridDim.x * kBlock)
+  for (uint32_t e = blk * kBlock + tid; e < nco; e += nblk * kBlock)
     file_direct(p, gp, __ldcg(gp.covf + e), n);
+}
+
+// floor(e 2^32) for e in [0, 1]: below 1, e 2^32 < 2^32 (the largest float
+// below 1 is 1 - 2^-24) and the 32-bit round-toward-zero conversion is exact;
+// e = 1 (the population's maximum) weighs 2^32.
+__device__ __forceinline__ unsigned long long floor_scaled_2p32(float e) {
+  return e >= 1.0f ? (1ull << 32) : (unsigned long long)__float2uint_rz(e * 4294967296.0f);
 }
 
 // Integer weight of log-weight lw, with the population's maximum log-weight
 // gmax weighing exactly 2^32 (the same on both scan passes).
 __device__ __forceinline__ unsigned long long global_qweight(float lw, float gmax) {
-  return __float2ull_rz(exp_weight(lw - gmax) * 4294967296.0f);
+  return floor_scaled_2p32(exp_weight(lw - gmax));
 }
 
 // 3a. reduce: the sum of the integer weights of every scan tile; the last
 // block to finish turns the tile sums into tile offsets (their exclusive
 // prefix sums) and the total Q, toff[nscan].
-__global__ void __launch_bounds__(kBlock) global_reduce_kernel(const __grid_constant__ StepParams p,
-                                                              const __grid_constant__ GlobalParams gp) {
+__device__ __forceinline__ void reduce_body(const StepParams& p, const GlobalParams& gp, uint32_t blk) {
   __shared__ unsigned long long s_warp[kBlock / 32];
   __shared__ bool s_last;
   const uint32_t N = p.N;
   const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
   const float gmax = p.st->gmax;
-  const uint32_t tbase = blockIdx.x * kScanTile;
+  const uint32_t tbase = blk * kScanTile;
   unsigned long long sum = 0;
   if (gmax != -INFINITY) {
+    const bool vec = (N % 4u) == 0u;
 #pragma unroll
-    for (int k = 0; k < kScanItems; ++k) {         // the scan pass reads the tile again, from L2
-      const uint32_t idx = tbase + k * kBlock + tid;
-      if (idx < N) sum += global_qweight(__ldcg(gp.lw + idx), gmax);
+    for (int k = 0; k < kScanItems / 4; ++k) {     // the scan pass reads the tile again, from L2
+      const uint32_t i4 = tbase + 4u * (k * kBlock + tid);
+      if (vec && i4 + 4u <= N) {
+        const float4 v = __ldcg(reinterpret_cast<const float4*>(gp.lw + i4));
+        sum += global_qweight(v.x, gmax) + global_qweight(v.y, gmax) + global_qweight(v.z, gmax) +
+               global_qweight(v.w, gmax);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (i4 + e < N) sum += global_qweight(__ldcg(gp.lw + i4 + e), gmax);
+      }
     }
   }
 #pragma unroll
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(kBlock) global_reduce_kernel(const __grid_cons
     unsigned long long tsum = 0;
 #pragma unroll
     for (int w = 0; w < kBlock / 32; ++w) tsum += s_warp[w];
-    gp.tsum[blockIdx.x] = tsum;
+    gp.tsum[blk] = tsum;
     __threadfence();
     s_last = atomicAdd(gp.done, 1u) == gp.nscan - 1u;
   }
@@ -326,7 +341,7 @@ __global__ void __launch_bounds__(kBlock) global_reduce_kernel(const __grid_cons
   const uint32_t E = (nt + kBlock - 1u) / kBlock;
   const uint32_t k0 = min(tid * E, nt), k1 = min(k0 + E, nt);
   unsigned long long tot = 0;
-  for (uint32_t k = k0; k < k1; ++k) tot += __ldcg(gp.tsum + k);
+  for (uint32_t k = k0; k < k1; ++k) tot += __ldcg(gp.tsum + k);   // E consecutive sums: one line per thread
   unsigned long long incl = tot;
 #pragma unroll
   for (int off = 1; off < 32; off <<= 1) {
@@ -346,6 +361,17 @@ __global__ void __launch_bounds__(kBlock) global_reduce_kernel(const __grid_cons
     gp.toff[nt] = run;                             // Q: the last thread's running sum ends at the total
     *gp.done = 0;                                  // ready for the next step
   }
+}
+
+// Kernels 2 and 3 in one launch: the refine blocks are bound by instruction
+// issue, the reduce blocks by memory, so the two share the SMs.  The first
+// nred blocks reduce (none when one tile holds every particle: the scan then
+// takes its own total), the rest refine.
+__global__ void __launch_bounds__(kBlock) global_refine_reduce_kernel(const __grid_constant__ StepParams p,
+                                                                     const __grid_constant__ GlobalParams gp) {
+  const uint32_t nred = gp.nscan > 1u ? gp.nscan : 0u;
+  if (blockIdx.x < nred) reduce_body(p, gp, blockIdx.x);
+  else refine_body(p, gp, blockIdx.x - nred, gridDim.x - nred);
 }
 
 // Bucket edge b: the smallest u of bucket b, floor(b 2^(64-log2b) Q / 2^64);
@@ -375,7 +401,7 @@ __device__ __forceinline__ uint32_t edges_below(unsigned long long v, unsigned l
 // (P_{-1} = 0), and then jb[b] = #{P <= u_b} = j; the last edge, u = Q - 1,
 // likewise.  Loads and stores of the tile are staged through shared memory so
 // that both are coalesced.
-__global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_constant__ StepParams p,
+__global__ void __launch_bounds__(kBlock, 4) global_scan_kernel(const __grid_constant__ StepParams p,
                                                             const __grid_constant__ GlobalParams gp) {
   // the tile's log-weights, then its prefix sums, one padding word every 32
   // floats / 16 doubles so that thread-contiguous accesses hit distinct banks
@@ -388,10 +414,20 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
   const uint32_t tile = blockIdx.x;
   const uint32_t tbase = tile * kScanTile;
   float* const s_f = reinterpret_cast<float*>(s_buf);
+  const bool vec = (N % 4u) == 0u;
 #pragma unroll
-  for (int k = 0; k < kScanItems; ++k) {          // coalesced load of the tile
-    const uint32_t idx = k * kBlock + tid;
-    s_f[idx + (idx >> 5)] = (tbase + idx < N) ? __ldcs(gp.lw + tbase + idx) : -INFINITY;
+  for (int k = 0; k < kScanItems / 4; ++k) {      // coalesced load of the tile
+    const uint32_t idx = 4u * (k * kBlock + tid);
+    float v[4];
+    if (vec && tbase + idx + 4u <= N) {
+      const float4 w = __ldcs(reinterpret_cast<const float4*>(gp.lw + tbase + idx));
+      v[0] = w.x; v[1] = w.y; v[2] = w.z; v[3] = w.w;
+    } else {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) v[e] = (tbase + idx + e < N) ? __ldcs(gp.lw + tbase + idx + e) : -INFINITY;
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) s_f[idx + e + ((idx + e) >> 5)] = v[e];
   }
   __syncthreads();
   // integer weights of my 16 consecutive particles and their running sums
@@ -414,8 +450,15 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
   }
   if (lane == 31) s_warp[warp] = incl;
   __syncthreads();                                 // (also: every thread has read its log-weights)
-  unsigned long long lo = __ldcg(gp.toff + tile) + incl - tot;   // P before my first particle
-  for (int w = 0; w < (int)warp; ++w) lo += s_warp[w];
+  // one tile: its own offset (0) and total; else both from the reduce pass
+  const bool single = gp.nscan == 1u;
+  unsigned long long lo = (single ? 0ull : __ldcg(gp.toff + tile)) + incl - tot;   // P before my first particle
+  unsigned long long btot = 0;
+#pragma unroll
+  for (int w = 0; w < kBlock / 32; ++w) {
+    if (w < (int)warp) lo += s_warp[w];
+    btot += s_warp[w];
+  }
 #pragma unroll
   for (int q = 0; q < kScanItems; ++q) {
     const uint32_t idx = tid * kScanItems + q;
@@ -428,7 +471,7 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
     if (tbase + idx < N) gp.P[tbase + idx] = s_buf[idx + (idx >> 4)];
   }
   // bucket edges u_b in [lo, hi): usually none in one thread's 16 particles
-  const unsigned long long Q = __ldcg(gp.toff + gp.nscan);
+  const unsigned long long Q = single ? btot : __ldcg(gp.toff + gp.nscan);
   const uint32_t j0 = tbase + tid * kScanItems;
   if (Q != 0) {
     const unsigned long long hi = lo + tot;
@@ -460,13 +503,15 @@ __global__ void __launch_bounds__(kBlock) global_scan_kernel(const __grid_consta
 
 static_assert(kGuideBins % kBlock == 0, "guide bins are scanned kGuideBins / kBlock per thread");
 
-// Bin of a value v of the bucket's u interval [ulo, ulo + W) among the
-// kGuideBins bins of the guide table: a monotone function of v (every step
-// rounds monotonically), which is all the exact count below relies on.
-__device__ __forceinline__ uint32_t guide_bin(unsigned long long v, unsigned long long ulo, float scale) {
-  const float f = __ull2float_rz(v - ulo) * scale;
-  return min((uint32_t)f, kGuideBins - 1u);
+// Bin of a value v of the bucket's u interval [ulo, ulo + W] among the
+// kGuideBins bins of the guide table: (v - ulo) >> shift, with the shift that
+// makes W >> shift < kGuideBins.  A monotone function of v, which is all the
+// exact count below relies on.
+__device__ __forceinline__ uint32_t guide_bin(unsigned long long v, unsigned long long ulo, uint32_t shift) {
+  return (uint32_t)((v - ulo) >> shift);
 }
+constexpr uint32_t kGuideLog2 = 10;
+static_assert((1u << kGuideLog2) == kGuideBins, "guide bins: a power of two");
 
 // Ancestor, gather and mutation of particle i with uniform r.  Its ancestor
 // lies in [lo, lo + len]: ancestor = lo + #{j in [lo, lo + len) : P_j <= u},
@@ -479,7 +524,7 @@ __device__ __forceinline__ void resolve_draw(const StepParams& p, const GlobalPa
                                              float* __restrict__ Xout, unsigned long long Q, uint32_t n, uint32_t i,
                                              bool staged, uint32_t lo, uint32_t len,
                                              const unsigned long long* sP, const float* sX, const uint32_t* sG,
-                                             unsigned long long ulo, float scale) {
+                                             unsigned long long ulo, uint32_t gshift) {
   constexpr uint32_t SC = global_stage_alloc(D);
   const uint32_t N = p.N;
   const unsigned long long r = draw_uniform(p, i, n);
@@ -489,7 +534,7 @@ __device__ __forceinline__ void resolve_draw(const StepParams& p, const GlobalPa
     const unsigned long long u = __umul64hi(r, Q);
     uint32_t c = 0;
     if (staged) {
-      c = sG[guide_bin(u, ulo, scale)];
+      c = sG[guide_bin(u, ulo, gshift)];
       while (c < len && sP[c] <= u) ++c;
 #pragma unroll
       for (int t = 0; t < D; ++t) xh[t] = sX[t * (SC + 1u) + c];
@@ -548,14 +593,21 @@ __global__ void __launch_bounds__(kBlock) global_resolve_kernel(const __grid_con
   const uint32_t len = __ldcg(gp.jb + b + 1u) - lo;
   const bool staged = Q != 0 && len < gp.stage_cap;
   const size_t s0 = (size_t)b * gp.cap;
-  // the first draw of every thread is loaded before the staging, so that the
-  // two latencies overlap
-  const bool first = tid < filled;
-  const uint32_t e_first = first ? __ldcs(gp.slot + s0 + tid) : 0u;
-  // the bucket's u interval [ulo, ulo + W) and the scale of its guide bins
+  // the first kPre draws of every thread are loaded with the fill count and
+  // the bucket edges (slots past the fill count hold stale indices, never
+  // used), so that the slot, edge and staging latencies overlap
+  constexpr int kPre = 4;
+  uint32_t pre[kPre];
+#pragma unroll
+  for (int k = 0; k < kPre; ++k) {
+    const uint32_t e = tid + k * kBlock;
+    pre[k] = e < gp.cap ? __ldcs(gp.slot + s0 + e) : 0u;
+  }
+  // the bucket's u interval [ulo, uhi] and the shift of its guide bins
   const unsigned long long ulo = (gp.log2b && b) ? __umul64hi((unsigned long long)b << (64u - gp.log2b), Q) : 0ull;
   const unsigned long long uhi = (b + 1u < gp.buckets) ? __umul64hi((unsigned long long)(b + 1u) << (64u - gp.log2b), Q) : Q;
-  const float scale = (float)kGuideBins / fmaxf(__ull2float_ru(uhi - ulo), 1.0f);
+  const uint32_t wbits = 64u - (uint32_t)__clzll(uhi - ulo);    // bit length of the interval's width
+  const uint32_t gshift = wbits > kGuideLog2 ? wbits - kGuideLog2 : 0u;
   if (staged) {
     for (uint32_t j = tid; j < len; j += kBlock) sP[j] = __ldcg(gp.P + lo + j);
 #pragma unroll
@@ -565,7 +617,7 @@ __global__ void __launch_bounds__(kBlock) global_resolve_kernel(const __grid_con
   }
   __syncthreads();
   if (staged) {                                    // guide table: histogram of the bins, then its scan
-    for (uint32_t j = tid; j < len; j += kBlock) atomicAdd(sG + guide_bin(sP[j], ulo, scale), 1u);
+    for (uint32_t j = tid; j < len; j += kBlock) atomicAdd(sG + guide_bin(sP[j], ulo, gshift), 1u);
     __syncthreads();
     constexpr uint32_t E = kGuideBins / kBlock;    // consecutive bins per thread
     uint32_t cnt[E], sum = 0;
@@ -596,15 +648,17 @@ __global__ void __launch_bounds__(kBlock) global_resolve_kernel(const __grid_con
     gp.cnt[b] = 0;                                 // (read above by every thread)
     if (b < (1u << gp.cbits)) gp.ccnt[b] = 0;
   }
-  if (first) resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, e_first, staged, lo, len, sP, sX, sG, ulo, scale);
-  for (uint32_t e = tid + kBlock; e < filled; e += kBlock) {
+#pragma unroll
+  for (int k = 0; k < kPre; ++k)
+    if (tid + k * kBlock < filled) resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, pre[k], staged, lo, len, sP, sX, sG, ulo, gshift);
+  for (uint32_t e = tid + kPre * kBlock; e < filled; e += kBlock) {
     const uint32_t i = __ldcs(gp.slot + s0 + e);
-    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, staged, lo, len, sP, sX, sG, ulo, scale);
+    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, staged, lo, len, sP, sX, sG, ulo, gshift);
   }
   const uint32_t nov = __ldcg(gp.cnt + gp.buckets);
   for (uint32_t e = b * kBlock + tid; e < nov; e += gridDim.x * kBlock) {
     const uint32_t i = __ldcg(gp.ovf + e);
-    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, false, 0u, N, sP, sX, sG, 0ull, 0.0f);
+    resolve_draw<D, KIND>(p, gp, Xin, Xout, Q, n, i, false, 0u, N, sP, sX, sG, 0ull, 0u);
   }
 }
 
@@ -622,8 +676,7 @@ template <int D, int KIND>
 static void fill_global(GlobalKernels& gk) {
   gk.weight = reinterpret_cast<const void*>(&global_weight_kernel<D, KIND>);
   gk.scan = reinterpret_cast<const void*>(&global_scan_kernel);
-  gk.refine = reinterpret_cast<const void*>(&global_refine_kernel);
-  gk.reduce = reinterpret_cast<const void*>(&global_reduce_kernel);
+  gk.refine_reduce = reinterpret_cast<const void*>(&global_refine_reduce_kernel);
   gk.resolve = reinterpret_cast<const void*>(&global_resolve_kernel<D, KIND>);
   gk.advance = reinterpret_cast<const void*>(&global_advance_kernel);
 }

@@ -17,11 +17,11 @@
 // With one lane per group (G = 1) only warp-level synchronisation is needed
 // inside the loop, and loads and stores go straight to global memory: for a
 // fixed member, consecutive lanes own consecutive groups, i.e. consecutive
-// addresses when s_k >= 32.  With a group spread over G > 1 lanes, a warp's
-// direct accesses would touch one sector per lane (members s_k apart); there
-// the block loads and stores its whole tile of D x A x (groups per iteration)
-// states through the state table in address order (coalesced for every
-// digit), at the price of block-wide barriers.
+// addresses when s_k >= 32.  With a group spread over G >= 8 lanes, a warp's
+// direct accesses would use at most half of every sector they touch (members
+// s_k apart); there the block loads and stores its whole tile of
+// D x A x (groups per iteration) states through the state table in address
+// order (coalesced for every digit), at the price of block-wide barriers.
 //
 // Integer resampling rule (shared with the oracle): delta = fp32(lw - max),
 // e = exp(delta), q = floor(e 2^24), P = inclusive prefix, Q = P_{A-1},
@@ -48,7 +48,8 @@ namespace bfpf {
 // in and out, and the ESS of the new stage weights decides the next stage.
 // Cooperative tile of one block iteration (groups g0 .. g0 + GPB - 1 of the
 // digit with stride s = 2^log2s): element (t, member r, group gi) lives at
-// X[t N + off] and in the state table at (t A + r) LD + gi.  When s >= GPB the
+// X[t N + off] and in the state table at (t A + r) LD + gi; a thread takes the
+// same PH elements of every component, located once.  When s >= GPB the
 // tile's groups share h and form GPB consecutive columns of every member row
 // (off = base + r s + gi); when s < GPB (then s divides GPB and g0) its particles
 // are the consecutive range of length A GPB from base = h0 A s.  Either way
@@ -63,57 +64,53 @@ constexpr int load_chunk(int n) {
 template <int D, int A, int GPB, int LD>
 struct GroupTile {
   static constexpr uint32_t kRow = (uint32_t)A * GPB;   // elements per state component
-  uint32_t base, log2s, log2as;
-  bool wide_s;                                            // s >= GPB
-  __device__ __forceinline__ GroupTile(uint32_t batch, uint32_t l2s, uint32_t l2as) : log2s(l2s), log2as(l2as) {
+  static constexpr int PH = (int)(kRow / kBlock);        // elements of a component per thread
+  static constexpr int PER = D * PH;
+  static_assert(kRow % kBlock == 0, "tile rows must split evenly over the block");
+  uint32_t off[PH], tix[PH];   // my elements of component 0: row offset, table index
+  __device__ __forceinline__ GroupTile(uint32_t batch, uint32_t log2s, uint32_t log2as) {
     const uint32_t g0 = batch * GPB;
-    const uint32_t h0 = g0 >> l2s, l0 = g0 & ((1u << l2s) - 1u);
-    wide_s = (1u << l2s) >= (uint32_t)GPB;
-    base = (h0 << l2as) + l0;
-  }
-  // global offset (within one component row) and table index of element e of component t
-  __device__ __forceinline__ void locate(uint32_t t, uint32_t e, uint32_t& off, uint32_t& tix) const {
-    uint32_t r, gi;
-    if (wide_s) {
-      r = e / GPB;
-      gi = e % GPB;
-      off = base + (r << log2s) + gi;
-    } else {
-      r = (e >> log2s) & (A - 1u);
-      gi = ((e >> log2as) << log2s) | (e & ((1u << log2s) - 1u));
-      off = base + e;
+    const uint32_t h0 = g0 >> log2s, l0 = g0 & ((1u << log2s) - 1u);
+    const bool wide_s = (1u << log2s) >= (uint32_t)GPB;
+    const uint32_t base = (h0 << log2as) + l0;
+#pragma unroll
+    for (int ph = 0; ph < PH; ++ph) {
+      const uint32_t e = threadIdx.x + (uint32_t)ph * kBlock;
+      uint32_t r, gi;
+      if (wide_s) {
+        r = e / GPB;
+        gi = e % GPB;
+        off[ph] = base + (r << log2s) + gi;
+      } else {
+        r = (e >> log2s) & (A - 1u);
+        gi = ((e >> log2as) << log2s) | (e & ((1u << log2s) - 1u));
+        off[ph] = base + e;
+      }
+      tix[ph] = r * LD + gi;
     }
-    tix = (t * A + r) * LD + gi;
   }
   __device__ __forceinline__ void load(const float* __restrict__ X, uint32_t N, uint32_t* tab) const {
-    constexpr int PER = (int)(D * kRow / kBlock);
-    static_assert(D * kRow % kBlock == 0, "tile must split evenly over the block");
     constexpr int CH = load_chunk(PER);             // loads in flight per thread
 #pragma unroll
     for (int c = 0; c < PER; c += CH) {
       float v[CH];
-      uint32_t ix[CH];
 #pragma unroll
       for (int q = 0; q < CH; ++q) {
-        const uint32_t idx = threadIdx.x + (uint32_t)(c + q) * kBlock;
-        const uint32_t t = idx / kRow, e = idx % kRow;
-        uint32_t off;
-        locate(t, e, off, ix[q]);
-        v[q] = __ldcs(X + (size_t)t * N + off);
+        const int t = (c + q) / PH, ph = (c + q) % PH;
+        v[q] = __ldcs(X + (size_t)t * N + off[ph]);
       }
 #pragma unroll
-      for (int q = 0; q < CH; ++q) tab[ix[q]] = __float_as_uint(v[q]);
+      for (int q = 0; q < CH; ++q) {
+        const int t = (c + q) / PH, ph = (c + q) % PH;
+        tab[tix[ph] + (uint32_t)(t * A * LD)] = __float_as_uint(v[q]);
+      }
     }
   }
   __device__ __forceinline__ void store(float* __restrict__ X, uint32_t N, const uint32_t* tab) const {
-    constexpr int PER = (int)(D * kRow / kBlock);
 #pragma unroll 4
-    for (int q = 0; q < PER; ++q) {
-      const uint32_t idx = threadIdx.x + (uint32_t)q * kBlock;
-      const uint32_t t = idx / kRow, e = idx % kRow;
-      uint32_t off, tix;
-      locate(t, e, off, tix);
-      __stcs(X + (size_t)t * N + off, __uint_as_float(tab[tix]));
+    for (int el = 0; el < PER; ++el) {
+      const int t = el / PH, ph = el % PH;
+      __stcs(X + (size_t)t * N + off[ph], __uint_as_float(tab[tix[ph] + (uint32_t)(t * A * LD)]));
     }
   }
 };
@@ -135,8 +132,10 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
   __shared__ __align__(16) uint32_t s_rows[GPB * RS];
   // states, [t][member][group]: the gather of a warp reads distinct banks
   __shared__ uint32_t s_tab[D * A * LD];
-  // tile through the state table (block barriers) for groups over several lanes
-  constexpr bool COAL = (G > 1) && !ADAPT;
+  // tile through the state table (block barriers) for groups over 8 or more
+  // lanes: their direct accesses would use at most half of every sector
+  // (with G lanes per group a warp's access spans G runs of 32/G floats)
+  constexpr bool COAL = (G >= 8) && !ADAPT;
 
   const uint32_t tid = threadIdx.x;
   const uint32_t tg = tid / G, j = tid % G;

@@ -124,7 +124,7 @@ def test_lockstep_sv_group_kernel_default_split(bfpf, all_stages):
 
 @pytest.mark.parametrize("d,N,T", [(1, 4096, 5), (1, 1 << 16, 3), (4, 5000, 3), (8, 1 << 14, 2), (0, 1 << 15, 4)])
 def test_lockstep_global_resampling(bfpf, d, N, T):
-    """radices = {N} above one block: the four-kernel global path (d = 0 means SV)."""
+    """radices = {N} above one block: the global path (d = 0 means SV)."""
     model = S.sv_model() if d == 0 else (S.lg_scalar() if d == 1 else S.lg_dense(d, seed=d))
     y = S.simulate(model, T, seed=41)[1]
     f = _filter(bfpf, model, (N,), 606)
@@ -147,7 +147,7 @@ def test_lockstep_global_resampling(bfpf, d, N, T):
     (2, 1 << 15, 2, True, False),      # 16 draws per bucket: the overflow list and global searches
     (0, 1 << 16, 2, True, False),
     (8, 5000, 2, True, True),
-    (1, 1025, 2, False, False),        # one bucket
+    (1, 1025, 2, False, False),        # the smallest global population: one scan tile, four buckets
 ])
 def test_lockstep_global_bucket_paths(bfpf, d, N, T, small, outlier):
     """The global draws are resolved per bucket of their uniform; every layout

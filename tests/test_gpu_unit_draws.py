@@ -148,11 +148,12 @@ def test_tile_kernel_draws_exact(bfpf, name, model, radices, T):
     assert gap <= 0.0
 
 
-@pytest.mark.parametrize("N,T,small", [(1 << 16, 3, False), (1 << 16, 2, True), (1 << 20, 2, False),
-                                       (1 << 24, 2, False)])
+@pytest.mark.parametrize("N,T,small", [(1025, 3, False), (4096, 3, False), (4099, 3, False), (1 << 16, 3, False),
+                                       (1 << 16, 2, True), (1 << 20, 2, False), (1 << 24, 2, False)])
 def test_global_draws_exact(bfpf, N, T, small):
     """One group of all N particles (Algorithm 2): the GPU's 64-bit prefix sums
-    over the whole population and the oracle's 64-bit uniforms."""
+    over the whole population and the oracle's 64-bit uniforms.  N = 1025 and
+    4096 fit one scan tile (no reduce pass); 4099 ends in a ragged tile."""
     model = S.sv_model()
     flags = bfpf.PF_TEST_SMALL_BUCKETS if small else 0
     draws, differ, gap = run_exact(bfpf, model, (N,), 9003, T, check_quant=N <= (1 << 20), extra_flags=flags)
