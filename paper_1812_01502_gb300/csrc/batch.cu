@@ -11,6 +11,9 @@
 // unit finishes its step (likelihood increment, filter mean, ESS) inside its
 // block; with several, every unit writes its partial sums and the last unit to
 // arrive folds them in unit order (last-block-done per filter, deterministic).
+// A digit whose radix is a power of two <= 32 (groups filling whole block
+// iterations) runs the register-resident group code of step_group.cuh
+// instead of the tile code: unit j takes its block iterations j, j + U, ....
 // Units are launched largest first, so that the big filters start at once and
 // small ones fill the machine behind them.
 #include <cfloat>
@@ -19,6 +22,7 @@
 #include "bfpf_batch.cuh"
 #include "bfpf_kernels.h"
 #include "bfpf_model.cuh"
+#include "step_group.cuh"
 #include "step_tile.cuh"
 
 namespace bfpf {
@@ -73,8 +77,37 @@ __device__ __forceinline__ void filter_summaries(const BatchParams& bp, BatchFil
   f.st.mu_f = (float)lme;
 }
 
-// Unit j of U of filter fid at step n.
-template <int D, int KIND>
+// Unit j of U of filter fid at step n on the group path (radix A of digit k).
+template <int D, int KIND, int A>
+__device__ __forceinline__ void batch_group_pass(const BatchParams& bp, BatchFilter& f, uint32_t fid, uint32_t n,
+                                                 uint32_t k, uint32_t j, uint32_t U, unsigned char* smem, Partial& acc,
+                                                 float* accx, uint32_t& status) {
+  constexpr int G = A / group_members_per_lane(A, D);
+  using LY = GroupLayout<D, A, G>;
+  static_assert(4 * (LY::kRowWords + LY::kTabWords) == (int)group_smem_bytes(D, A), "shared-memory size");
+  uint32_t* const s_rows = reinterpret_cast<uint32_t*>(smem);
+  uint32_t* const s_tab = s_rows + LY::kRowWords;
+  GroupCtx c;
+  c.x = f.x;
+  c.lV_in = f.lV[n & 1u];
+  c.lV_out = f.lV[(n & 1u) ^ 1u];
+  c.anc = nullptr;
+  c.prec = nullptr;
+  c.N = f.N;
+  c.n = n;
+  c.t = n;            // one stage per time step
+  c.obs = true;
+  c.mut = true;
+  c.muf = f.st.mu_f;
+  const float* yr = bp.y_ring + ((size_t)fid * bp.ring + n % bp.ring) * bp.dy_max;
+#pragma unroll
+  for (int q = 0; q < kMaxDim; ++q) c.y[q] = (q < (int)f.model.dy) ? yr[q] : 0.0f;
+  const RoundKeys rk = f.rk;    // in registers: the Philox rounds read every key
+  group_iterations<D, KIND, A, G, false>(c, rk, f.model, f.gg[k], j, U, s_rows, s_tab, acc, accx, status);
+}
+
+// Unit j of U of filter fid at step n (GROUP: the digit is on the group path).
+template <int D, int KIND, bool GROUP>
 __device__ __forceinline__ void batch_unit_step(const BatchParams& bp, BatchFilter& f, uint32_t fid, uint32_t n,
                                                 uint32_t j, uint32_t U, unsigned char* smem) {
   __shared__ uint32_t s_last;
@@ -103,7 +136,17 @@ __device__ __forceinline__ void batch_unit_step(const BatchParams& bp, BatchFilt
   float accx[D];
 #pragma unroll
   for (int t = 0; t < D; ++t) accx[t] = 0.0f;
-  tile_steps<D, KIND, false>(ctx, j, U, smem, acc, accx, status);
+  if constexpr (GROUP) {
+    switch (f.geom[k].a) {
+      case 2: batch_group_pass<D, KIND, 2>(bp, f, fid, n, k, j, U, smem, acc, accx, status); break;
+      case 4: batch_group_pass<D, KIND, 4>(bp, f, fid, n, k, j, U, smem, acc, accx, status); break;
+      case 8: batch_group_pass<D, KIND, 8>(bp, f, fid, n, k, j, U, smem, acc, accx, status); break;
+      case 16: batch_group_pass<D, KIND, 16>(bp, f, fid, n, k, j, U, smem, acc, accx, status); break;
+      default: batch_group_pass<D, KIND, 32>(bp, f, fid, n, k, j, U, smem, acc, accx, status); break;
+    }
+  } else {
+    tile_steps<D, KIND, false>(ctx, j, U, smem, acc, accx, status);
+  }
   if (status) atomicOr(&f.st.status, status);
   Partial b;
   float bx[D];
@@ -145,15 +188,34 @@ __device__ __forceinline__ void batch_unit_step(const BatchParams& bp, BatchFilt
 }  // namespace
 
 // One time step of the work units u0 .. u0 + gridDim.x - 1, all of one model
-// kind and state dimension (a kernel per class, so that each keeps the
-// registers its own dimension needs).
-template <int D, int KIND>
-__global__ void __launch_bounds__(kBlock) batch_class_kernel(const __grid_constant__ BatchParams bp, uint32_t u0) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// kind and state dimension (kernels per class, so that each keeps the
+// registers its own dimension needs), split by the path of each unit's digit
+// this step: the tile kernel returns at once for a unit on the group path and
+// the group kernel for a unit on the tile path (all units of a filter take the
+// same path in a step), so that the group code keeps the register budget of
+// the single-filter group kernels.
+template <int D, int KIND, bool GROUP>
+__device__ __forceinline__ void batch_class_body(const BatchParams& bp, uint32_t u0, unsigned char* smem) {
   const uint32_t n = bp.state->n;
   const uint2 un = bp.units[u0 + blockIdx.x];
   const uint32_t fid = un.x, j = un.y & 0xffffu, U = un.y >> 16;
-  batch_unit_step<D, KIND>(bp, bp.filters[fid], fid, n, j, U, smem_raw);
+  BatchFilter& f = bp.filters[fid];
+  const bool on_group = (f.gsel >> (n % f.m)) & 1u;
+  if (on_group != GROUP) return;                  // block-uniform
+  batch_unit_step<D, KIND, GROUP>(bp, f, fid, n, j, U, smem);
+}
+
+template <int D, int KIND>
+__global__ void __launch_bounds__(kBlock, 2) batch_class_kernel(const __grid_constant__ BatchParams bp, uint32_t u0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  batch_class_body<D, KIND, false>(bp, u0, smem_raw);
+}
+
+template <int D, int KIND>
+__global__ void __launch_bounds__(kBlock, 2) batch_group_kernel(const __grid_constant__ BatchParams bp,
+                                                                                uint32_t u0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  batch_class_body<D, KIND, true>(bp, u0, smem_raw);
 }
 
 // After every class of a step: advance the batch's step counter.
@@ -172,6 +234,20 @@ const void* batch_class_kernel_ptr(int kind, int d) {
     case 6: return reinterpret_cast<const void*>(&batch_class_kernel<6, kLinearGaussian>);
     case 7: return reinterpret_cast<const void*>(&batch_class_kernel<7, kLinearGaussian>);
     case 8: return reinterpret_cast<const void*>(&batch_class_kernel<8, kLinearGaussian>);
+    default: return nullptr;
+  }
+}
+const void* batch_group_kernel_ptr(int kind, int d) {
+  if (kind == kStochVol) return d == 1 ? reinterpret_cast<const void*>(&batch_group_kernel<1, kStochVol>) : nullptr;
+  switch (d) {
+    case 1: return reinterpret_cast<const void*>(&batch_group_kernel<1, kLinearGaussian>);
+    case 2: return reinterpret_cast<const void*>(&batch_group_kernel<2, kLinearGaussian>);
+    case 3: return reinterpret_cast<const void*>(&batch_group_kernel<3, kLinearGaussian>);
+    case 4: return reinterpret_cast<const void*>(&batch_group_kernel<4, kLinearGaussian>);
+    case 5: return reinterpret_cast<const void*>(&batch_group_kernel<5, kLinearGaussian>);
+    case 6: return reinterpret_cast<const void*>(&batch_group_kernel<6, kLinearGaussian>);
+    case 7: return reinterpret_cast<const void*>(&batch_group_kernel<7, kLinearGaussian>);
+    case 8: return reinterpret_cast<const void*>(&batch_group_kernel<8, kLinearGaussian>);
     default: return nullptr;
   }
 }

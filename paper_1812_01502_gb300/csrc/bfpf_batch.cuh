@@ -16,6 +16,10 @@ struct BatchFilter {
   DevState st;                  // mu, mu_f, loglik, status of this filter
   ModelParams model;
   DigitGeom geom[kMaxDigits];
+  // digits on the register-resident group path (bit k: digit k; power-of-two
+  // radix <= 32 whose groups fill whole block iterations) and their geometry
+  uint32_t gsel;
+  GroupGeom gg[kMaxDigits];
 };
 
 struct BatchState {

@@ -61,10 +61,12 @@ struct IslandKernels {
 };
 bool select_island_kernels(int d, int kind, IslandKernels& ik);
 
-// Batched filters (batch.cu): batch_class_kernel<D, KIND>(BatchParams, uint32_t u0) runs one
-// time step of the work units u0 .. u0 + grid - 1 (one class of model kind and
-// dimension); batch_advance_kernel(BatchParams) advances the step; batch_init_kernel(BatchParams).
+// Batched filters (batch.cu): batch_class_kernel<D, KIND>(BatchParams, uint32_t u0) and
+// batch_group_kernel<D, KIND>(same) run one time step of the work units u0 .. u0 + grid - 1
+// (one class of model kind and dimension) whose digit is on the tile / the group path;
+// batch_advance_kernel(BatchParams) advances the step; batch_init_kernel(BatchParams).
 const void* batch_class_kernel_ptr(int kind, int d);
+const void* batch_group_kernel_ptr(int kind, int d);
 const void* batch_advance_kernel_ptr();
 const void* batch_init_kernel_ptr();
 

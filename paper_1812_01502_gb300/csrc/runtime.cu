@@ -20,6 +20,7 @@
 #include "bfpf_device.cuh"
 #include "bfpf_global.cuh"
 #include "bfpf_kernels.h"
+#include "step_group_layout.cuh"
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -1402,8 +1403,13 @@ struct pf_batch {
   BatchParams BP{};
   std::vector<BatchFilter> host_filters;    // host copy (pointers, sizes, geometry)
   std::vector<uint2> units;                 // {filter, j | U << 16}, by class, largest work first
-  struct Class { const void* kernel; uint32_t u0, count; };
-  std::vector<Class> classes;               // one kernel launch per class and step
+  struct Class {
+    const void* kernel;                     // tile path
+    const void* gkernel;                    // group path
+    uint32_t u0, count;
+    bool any_tile, any_group;               // some unit of the class takes the path at some step
+  };
+  std::vector<Class> classes;               // one or two kernel launches per class and step
   uint64_t n_host = 0;
   cudaGraphExec_t graph = nullptr;
   std::string err;
@@ -1424,6 +1430,36 @@ inline double batch_work(const Plan& pl) { return (double)pl.N * (pl.d + 1); }
 constexpr double kBatchUnitWork = 32768.0;
 
 // Plan every filter and lay the batch out in one workspace.
+// Group-path geometry of digit k of a batch filter: a power-of-two radix <= 32
+// whose groups fill whole block iterations (members per lane as for a single
+// filter's default split), with its carried weights indexed from digit k - 1.
+bool batch_group_geom(const Plan& pl, int k, GroupGeom& gg) {
+  const DigitGeom& g = pl.geom[k];
+  const uint32_t a = g.a;
+  if (a < 2 || a > 32 || (a & (a - 1)) != 0) return false;
+  const uint32_t G = a / (uint32_t)group_members_per_lane((int)a, pl.d);
+  const uint32_t gpb = kBlock / G;
+  const uint32_t ngroups = pl.N / a;
+  if (ngroups % gpb != 0) return false;
+  std::memset(&gg, 0, sizeof(gg));
+  while ((1u << gg.log2s) < g.s) ++gg.log2s;
+  while ((1u << gg.log2as) < a * g.s) ++gg.log2as;
+  gg.nbatch = ngroups / gpb;
+  const int kp = (k + pl.m - 1) % pl.m;
+  const uint32_t sp = pl.geom[kp].s;
+  if (k == 0) {
+    gg.lv_mul = 1;
+    gg.lv_lmask = 0;
+    gg.lv_mask = sp - 1;          // s_{m-1} = N / a_{m-1}
+  } else {
+    gg.lv_mul = sp;
+    gg.lv_lmask = sp - 1;
+    gg.lv_mask = 0xffffffffu;
+  }
+  gg.log_a = g.log_a;
+  return true;
+}
+
 pf_status plan_batch(int32_t F, const pf_model* models, const int64_t* N, const int32_t* radices, const int32_t* m,
                      const pf_options* opts, std::vector<Plan>& plans, BatchLayout& L, int& ring, int& dy_max,
                      int& d_max, size_t& smem, std::string& msg) {
@@ -1448,6 +1484,9 @@ pf_status plan_batch(int32_t F, const pf_model* models, const int64_t* N, const 
     dy_max = std::max(dy_max, plans[f].dy);
     d_max = std::max(d_max, plans[f].d);
     smem = std::max(smem, plans[f].smem);
+    GroupGeom gg;
+    for (int k = 0; k < plans[f].m; ++k)
+      if (batch_group_geom(plans[f], k, gg)) smem = std::max<size_t>(smem, group_smem_bytes_max(d));
   }
   // Work units: a filter's step is split into U = ceil(work / unit work) blocks
   // (at most the fewest tiles of any of its digits), from the filter's own size
@@ -1579,6 +1618,9 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
     bf.rk = make_round_keys(seeds[f]);
     bf.model = pl.mp;
     std::memcpy(bf.geom, pl.geom, sizeof(bf.geom));
+    bf.gsel = 0;
+    for (int k = 0; k < pl.m; ++k)
+      if (batch_group_geom(pl, k, bf.gg[k])) bf.gsel |= 1u << k;
     bf.U = L.U[f];
     bf.pbase = L.pbase[f];
     const double uw = batch_work(pl) / L.U[f];
@@ -1595,16 +1637,23 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
   for (size_t u = 0; u < work.size(); ++u) {
     if (u == 0 || cls(work[u].second) != cls(work[u - 1].second)) {
       const Plan& pl = plans[work[u].second.x];
-      b->classes.push_back({batch_class_kernel_ptr(pl.kind, pl.d), (uint32_t)u, 0u});
+      b->classes.push_back({batch_class_kernel_ptr(pl.kind, pl.d), batch_group_kernel_ptr(pl.kind, pl.d), (uint32_t)u,
+                            0u, false, false});
     }
-    b->classes.back().count += 1;
+    auto& c = b->classes.back();
+    c.count += 1;
+    const BatchFilter& hf = b->host_filters[work[u].second.x];
+    const uint32_t all = (hf.m >= 32) ? 0xffffffffu : ((1u << hf.m) - 1u);
+    c.any_group = c.any_group || (hf.gsel & all) != 0;
+    c.any_tile = c.any_tile || (hf.gsel & all) != all;
   }
   for (const auto& c : b->classes) {
-    if (!c.kernel) {
+    if (!c.kernel || !c.gkernel) {
       delete b;
       return bfail(nullptr, PF_EINVAL, "unsupported (d, model) combination in the batch");
     }
     e = raise_smem_limit(c.kernel, b->smem);
+    if (e == cudaSuccess) e = raise_smem_limit(c.gkernel, b->smem);
     if (e != cudaSuccess) {
       delete b;
       return bfail(nullptr, PF_ECUDA, std::string("CUDA: ") + cudaGetErrorString(e));
@@ -1659,7 +1708,9 @@ pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_in
     for (auto& c : b->classes) {
       uint32_t u0 = c.u0;
       void* cargs[] = {&b->BP, &u0};
-      cudaError_t le = cudaLaunchKernel(c.kernel, dim3(c.count), dim3(kBlock), cargs, b->smem, s);
+      cudaError_t le = cudaSuccess;
+      if (c.any_tile) le = cudaLaunchKernel(c.kernel, dim3(c.count), dim3(kBlock), cargs, b->smem, s);
+      if (le == cudaSuccess && c.any_group) le = cudaLaunchKernel(c.gkernel, dim3(c.count), dim3(kBlock), cargs, b->smem, s);
       if (le != cudaSuccess) return le;
     }
     void* aargs[] = {&b->BP};

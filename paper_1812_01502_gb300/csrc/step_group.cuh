@@ -35,6 +35,7 @@
 #include "bfpf_epilogue.cuh"
 #include "bfpf_model.cuh"
 #include "step_adaptive.cuh"
+#include "step_group_layout.cuh"
 
 namespace bfpf {
 
@@ -115,23 +116,39 @@ struct GroupTile {
   }
 };
 
-template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
-__device__ __forceinline__ void step_group_body(const StepParams& p, const GroupGeom& gg) {
+// What one stage reads and writes of its filter, besides the model and the
+// round keys (passed separately so that they stay in parameter space).
+struct GroupCtx {
+  float* x;                 // [d][N] states
+  const float* lV_in;       // carried log weights of the previous stage
+  float* lV_out;            // ... of this stage
+  int32_t* anc;             // optional ancestors
+  unsigned long long* prec; // optional prefix sums of the draws (test output)
+  uint32_t N;
+  uint32_t n;               // time step: observation and propagation normals
+  uint32_t t;               // stage counter: resampling words
+  bool obs, mut;            // weight with g_n / mutate in this stage
+  float muf;                // FP32 normaliser subtracted from the log weights
+  float y[kMaxDim];         // observation y_n
+};
+
+// Block iterations first, first + stride, ... < gg.nbatch of one stage on a
+// radix-A digit: every group's weights, draws, gather and mutation; the
+// block's partial sums accumulate into (acc, accx) and status bits into status.
+template <int D, int KIND, int A, int G, bool ADAPT>
+__device__ __forceinline__ void group_iterations(const GroupCtx& c, const RoundKeys& rk, const ModelParams& mp,
+                                                 const GroupGeom& gg, uint32_t first, uint32_t stride,
+                                                 uint32_t* s_rows, uint32_t* s_tab, Partial& acc, float* accx,
+                                                 uint32_t& status) {
   static_assert(A >= 2 && A <= 32 && (A & (A - 1)) == 0, "radix must be a power of two <= 32");
   static_assert(G >= 1 && G <= A && A % G == 0, "bad lanes per group");
+  using LY = GroupLayout<D, A, G>;
   constexpr int M = A / G;                 // members per lane
-  constexpr int GPB = kBlock / G;          // groups per block iteration
-  constexpr int LD = GPB + (G > 1 ? 1 : 0);
+  constexpr int GPB = LY::GPB;
+  constexpr int LD = LY::LD;
+  constexpr int PIV = LY::PIV;
+  constexpr int RS = LY::RS;
   constexpr unsigned FULL = 0xffffffffu;
-  // Prefix-sum rows, one per group: P_0 .. P_{A-1}, then the bucket pivots
-  // P_3, P_7, ... (A >= 8); the row stride RS = 4 mod 8 words puts the 16-byte
-  // loads of 8 lanes (different groups) on distinct banks.
-  constexpr int PIV = (A >= 8) ? A / 4 : 0;
-  constexpr int RS = (A + PIV) + ((12 - (A + PIV) % 8) % 8);
-  static_assert(RS % 8 == 4 && RS >= A + PIV, "row stride");
-  __shared__ __align__(16) uint32_t s_rows[GPB * RS];
-  // states, [t][member][group]: the gather of a warp reads distinct banks
-  __shared__ uint32_t s_tab[D * A * LD];
   // tile through the state table (block barriers) for groups over 8 or more
   // lanes: their direct accesses would use at most half of every sector
   // (with G lanes per group a warp's access spans G runs of 32/G floats)
@@ -139,42 +156,21 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
 
   const uint32_t tid = threadIdx.x;
   const uint32_t tg = tid / G, j = tid % G;
-  const ModelParams& mp = p.model;
-  DevState* st = p.st;
-  if constexpr (ADAPT) {
-    if (st->skip) {
-      if (!gg.last) return;                     // nothing to do, nothing to record
-      adaptive_mutate_only<D, KIND>(p, p.geom[gg.k], st->n);
-      return;
-    }
-  }
-  const Sched sc = ADAPT ? Sched{st->n, st->n * (uint32_t)p.m + gg.j, gg.k, false, gg.last != 0}
-                         : STAGED ? sched_of(p, st) : Sched{st->n, st->n, 0u, true, true};
-  const bool obs = (STAGED || ADAPT) ? sc.obs : true;
-  const bool mut = (STAGED || ADAPT) ? sc.mut : true;
-  const uint32_t n = sc.n;
-  const uint32_t lvsel = ADAPT ? st->lvp : (sc.t & 1u);
-  const float* __restrict__ lV_in = p.lV[lvsel];
-  float* __restrict__ lV_out = p.lV[lvsel ^ 1u];
-  float* __restrict__ X = p.x;
-  const float muf = st->mu_f;
-  const uint32_t N = p.N;
-  float y[kMaxDim];
-#pragma unroll
-  for (int q = 0; q < kMaxDim; ++q) y[q] = (q < mp.dy) ? p.y_ring[(n % kRing) * mp.dy + q] : 0.0f;
-  uint32_t status = 0;
+  const bool obs = c.obs, mut = c.mut;
+  const uint32_t n = c.n;
+  const float* __restrict__ lV_in = c.lV_in;
+  float* __restrict__ lV_out = c.lV_out;
+  float* __restrict__ X = c.x;
+  const float muf = c.muf;
+  const uint32_t N = c.N;
+  const float* y = c.y;
   const uint32_t log2s = gg.log2s, log2as = gg.log2as;
   const uint32_t smask = (1u << log2s) - 1u;
   const bool contiguous = (log2s == 0) && (M % 4 == 0);   // digit 0: members are adjacent
   uint32_t* const col = s_tab + tg;                        // my group's column of the state table
   uint32_t* const row = s_rows + tg * RS;                  // my group's prefix-sum row
 
-  Partial acc{-INFINITY, 0.0f, 0.0f};
-  float accx[D];
-#pragma unroll
-  for (int t = 0; t < D; ++t) accx[t] = 0.0f;
-
-  for (uint32_t batch = blockIdx.x; batch < gg.nbatch; batch += gridDim.x) {
+  for (uint32_t batch = first; batch < gg.nbatch; batch += stride) {
     const uint32_t g = batch * GPB + tg;              // group index h*s + l
     const uint32_t h = g >> log2s;
     const uint32_t l = g & smask;
@@ -289,9 +285,9 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
     }
 #pragma unroll
     for (int mm = 0; mm < M; ++mm) P[mm] += excl;
-    if (p.prec) {                  // test output: the integer prefix sums the draws use
+    if (c.prec) {                  // test output: the integer prefix sums the draws use
 #pragma unroll
-      for (int mm = 0; mm < M; ++mm) p.prec[i0 + (mm << log2s)] = P[mm];
+      for (int mm = 0; mm < M; ++mm) c.prec[i0 + (mm << log2s)] = P[mm];
     }
     if constexpr (M % 4 == 0) {
 #pragma unroll
@@ -351,7 +347,7 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
       constexpr int MQ = (M < 4) ? M : 4;             // members handled in this round
       uint32_t rw[MQ];
       {
-        const uint4 w = philox4x32(make_uint4((pi0 >> 2) + q4, sc.t, kPurposeResample, 0), p.rk);
+        const uint4 w = philox4x32(make_uint4((pi0 >> 2) + q4, c.t, kPurposeResample, 0), rk);
         if constexpr (M >= 4) {
           rw[0] = w.x; rw[1] = w.y; rw[2] = w.z; rw[3] = w.w;
         } else {
@@ -369,12 +365,12 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
         const uint32_t c0 = ((pi0 + 4 * q4) * D) >> 2;
 #pragma unroll
         for (int b = 0; b < MQ * D / 4; ++b) {
-          const uint4 w = philox4x32(make_uint4(c0 + b, n, kPurposePropagate, 0), p.rk);
+          const uint4 w = philox4x32(make_uint4(c0 + b, n, kPurposePropagate, 0), rk);
           normals4_fast(w, z + 4 * b);
         }
       } else if constexpr (4 % (MQ * D) == 0) {       // 1 or 2 normals inside one block
         const uint32_t nu0 = pi0 * D;
-        const uint4 w = philox4x32(make_uint4(nu0 >> 2, n, kPurposePropagate, 0), p.rk);
+        const uint4 w = philox4x32(make_uint4(nu0 >> 2, n, kPurposePropagate, 0), rk);
         float zz[4];
         normals4_fast(w, zz);
         const uint32_t off = nu0 & 3u;
@@ -389,7 +385,7 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
         float zz[4 * NB];
 #pragma unroll
         for (int b = 0; b < NB; ++b) {
-          const uint4 w = philox4x32(make_uint4((nu0 >> 2) + b, n, kPurposePropagate, 0), p.rk);
+          const uint4 w = philox4x32(make_uint4((nu0 >> 2) + b, n, kPurposePropagate, 0), rk);
           normals4_fast(w, zz + 4 * b);
         }
         const uint32_t off = nu0 & 3u;
@@ -459,16 +455,55 @@ __device__ __forceinline__ void step_group_body(const StepParams& p, const Group
 #pragma unroll
         for (int t = 0; t < D; ++t) __stcs(X + (size_t)t * N + i0 + (mm << log2s), xo[mm][t]);
     }
-    if (p.anc) {
+    if (c.anc) {
 #pragma unroll
-      for (int mm = 0; mm < M; ++mm) p.anc[i0 + (mm << log2s)] = (int32_t)(ig + (coff[mm] << log2s));
+      for (int mm = 0; mm < M; ++mm) c.anc[i0 + (mm << log2s)] = (int32_t)(ig + (coff[mm] << log2s));
     }
     __syncwarp();
   }
+}
+
+template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
+__device__ __forceinline__ void step_group_body(const StepParams& p, const GroupGeom& gg) {
+  using LY = GroupLayout<D, A, G>;
+  __shared__ __align__(16) uint32_t s_rows[LY::kRowWords];
+  __shared__ uint32_t s_tab[LY::kTabWords];
+  const ModelParams& mp = p.model;
+  DevState* st = p.st;
   if constexpr (ADAPT) {
-    adaptive_stage_finish<D>(p, acc, accx, status, lvsel, gg.k, gg.last != 0, n);
+    if (st->skip) {
+      if (!gg.last) return;                     // nothing to do, nothing to record
+      adaptive_mutate_only<D, KIND>(p, p.geom[gg.k], st->n);
+      return;
+    }
+  }
+  const Sched sc = ADAPT ? Sched{st->n, st->n * (uint32_t)p.m + gg.j, gg.k, false, gg.last != 0}
+                         : STAGED ? sched_of(p, st) : Sched{st->n, st->n, 0u, true, true};
+  const uint32_t lvsel = ADAPT ? st->lvp : (sc.t & 1u);
+  GroupCtx c;
+  c.x = p.x;
+  c.lV_in = p.lV[lvsel];
+  c.lV_out = p.lV[lvsel ^ 1u];
+  c.anc = p.anc;
+  c.prec = p.prec;
+  c.N = p.N;
+  c.n = sc.n;
+  c.t = sc.t;
+  c.obs = (STAGED || ADAPT) ? sc.obs : true;
+  c.mut = (STAGED || ADAPT) ? sc.mut : true;
+  c.muf = st->mu_f;
+#pragma unroll
+  for (int q = 0; q < kMaxDim; ++q) c.y[q] = (q < mp.dy) ? p.y_ring[(sc.n % kRing) * mp.dy + q] : 0.0f;
+  uint32_t status = 0;
+  Partial acc{-INFINITY, 0.0f, 0.0f};
+  float accx[D];
+#pragma unroll
+  for (int t = 0; t < D; ++t) accx[t] = 0.0f;
+  group_iterations<D, KIND, A, G, ADAPT>(c, p.rk, mp, gg, blockIdx.x, gridDim.x, s_rows, s_tab, acc, accx, status);
+  if constexpr (ADAPT) {
+    adaptive_stage_finish<D>(p, acc, accx, status, lvsel, gg.k, gg.last != 0, sc.n);
   } else {
-    finish_step<D>(p, acc, accx, sc, status, muf);
+    finish_step<D>(p, acc, accx, sc, status, c.muf);
   }
 }
 
@@ -487,13 +522,6 @@ template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
 __global__ void __launch_bounds__(kBlock, 3) step_group_kernel_d5(const __grid_constant__ StepParams p,
                                                                   const __grid_constant__ GroupGeom gg) {
   step_group_body<D, KIND, A, G, STAGED, ADAPT>(p, gg);
-}
-
-// Lanes per group: each lane keeps M = A / G members, M * D <= 16 state values.
-constexpr int group_members_per_lane(int A, int D) {
-  int m = 1;
-  while (m * 2 <= A && m * 2 * D <= 16) m *= 2;
-  return m;
 }
 
 // SMALL: at most two members per lane, for populations too small to fill the
