@@ -451,7 +451,10 @@ def batched_leg(bf, dev, F=4096, T=500):
     import synthetic as S
     specs = S.batched_specs(F, T=T)
     y = torch.tensor(S.simulate_batch(specs, T), dtype=torch.float32, device=dev)
-    b = bf.FilterBatch([(w.model, w.N, w.radices, w.filter_seed) for w in specs], device=dev)
+    fs = [(w.model, w.N, w.radices, w.filter_seed) for w in specs]
+    from paper_1812_01502_gb300 import autotune
+    tuned = autotune.tune_batch(fs, device=dev)          # (tile, unit work) for this batch shape, cached
+    b = bf.FilterBatch(fs, device=dev, tile=int(tuned["tile"]), unit_work=int(tuned["unit_work"]))
     b.run(y[:, :8])                         # graph capture, first touch
     torch.cuda.synchronize(dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -472,9 +475,13 @@ def batched_leg(bf, dev, F=4096, T=500):
     return {"filters": F, "steps": steps, "particle_steps_per_s": ps / (ms * 1e-3), "ms_per_step": ms / steps,
             "hbm_gbs_algorithmic": nbytes / (ms * 1e-3) / 1e9, "total_particles": sum(w.N for w in specs),
             "d": "uniform over {1,4,8}", "N": "2^round(U(8,16))", "outputs_finite": ok,
-            "launches_per_step": len({(w.model.kind, w.model.d) for w in specs}) + 1,
-            "note": "one kernel per class of (model, d) over every filter's work units, then one that "
-                    "advances the step counter; chunks of steps replay as CUDA graphs"}
+            "tuned": {"tile": int(tuned["tile"]), "unit_work": int(tuned["unit_work"]),
+                      "tuned_ms_per_step": tuned.get("ms_per_step"),
+                      "default_ms_per_step": tuned.get("default_ms_per_step")},
+            "launches_per_step": f"up to {2 * len({(w.model.kind, w.model.d) for w in specs}) + 1}",
+            "note": "per class of (model, d) one kernel for the work units whose digit is on the group path "
+                    "and one for those on the tile path, then one that advances the step counter; chunks of "
+                    "steps replay as CUDA graphs; tile size and unit work from the autotuner"}
 
 
 def serving_leg(dev, n_requests=96, chunk_interval=0.01, fractions=(0.25, 0.5, 0.75, 0.9)):
