@@ -1395,6 +1395,8 @@ struct pf_batch {
   int device = 0;
   cudaStream_t stream = nullptr;
   cudaStream_t cap_stream = nullptr;
+  cudaStream_t side = nullptr;              // the tile-path kernels of a step run beside the group path
+  cudaEvent_t fork_ev = nullptr, join_ev = nullptr;
   bool own_ws = false;
   unsigned char* ws = nullptr;
   size_t ws_bytes = 0;
@@ -1406,13 +1408,21 @@ struct pf_batch {
   struct Class {
     const void* kernel;                     // tile path
     const void* gkernel;                    // group path
-    uint32_t u0, count;
-    bool any_tile, any_group;               // some unit of the class takes the path at some step
+    uint32_t u0, count;                     // the class's units
+    uint32_t g0, gcount;                    // units that may be on the group path (a prefix of the class)
+    uint32_t t0, tcount;                    // units that may be on the tile path (a suffix)
   };
   std::vector<Class> classes;               // one or two kernel launches per class and step
   uint64_t n_host = 0;
   cudaGraphExec_t graph = nullptr;
   std::string err;
+  ~pf_batch() {                             // the workspace is freed by its owner's paths
+    if (graph) cudaGraphExecDestroy(graph);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
+    if (side) cudaStreamDestroy(side);
+    if (fork_ev) cudaEventDestroy(fork_ev);
+    if (join_ev) cudaEventDestroy(join_ev);
+  }
 };
 
 namespace {
@@ -1597,6 +1607,9 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
     b->ws_bytes = L.total;
   }
   e = cudaStreamCreateWithFlags(&b->cap_stream, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->side, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->fork_ev, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->join_ev, cudaEventDisableTiming);
   if (e != cudaSuccess) {
     if (b->own_ws) cudaFree(b->ws);
     delete b;
@@ -1626,11 +1639,22 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
     const double uw = batch_work(pl) / L.U[f];
     for (uint32_t j = 0; j < L.U[f]; ++j) work.push_back({-uw, make_uint2((uint32_t)f, j | (L.U[f] << 16))});
   }
-  // classes of (model kind, dimension); inside a class, largest units first
+  // classes of (model kind, dimension); inside a class the units of filters
+  // whose every digit is on the group path first, then those with digits on
+  // both paths, then those on the tile path only (so that each path's kernel
+  // covers one contiguous range of units), each part largest first
   auto cls = [&](const uint2& u) { return plans[u.x].kind * 16 + plans[u.x].d; };
+  auto paths = [&](const uint2& u) {          // 0: group only, 1: both, 2: tile only
+    const BatchFilter& hf = b->host_filters[u.x];
+    const uint32_t all = (hf.m >= 32) ? 0xffffffffu : ((1u << hf.m) - 1u);
+    const uint32_t g = hf.gsel & all;
+    return g == all ? 0 : (g != 0 ? 1 : 2);
+  };
   std::stable_sort(work.begin(), work.end(), [&](const std::pair<double, uint2>& x, const std::pair<double, uint2>& y) {
     const int cx = cls(x.second), cy = cls(y.second);
-    return cx != cy ? cx < cy : x.first < y.first;
+    if (cx != cy) return cx < cy;
+    const int px = paths(x.second), py = paths(y.second);
+    return px != py ? px < py : x.first < y.first;
   });
   b->units.resize(work.size());
   for (size_t u = 0; u < work.size(); ++u) b->units[u] = work[u].second;
@@ -1638,14 +1662,14 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
     if (u == 0 || cls(work[u].second) != cls(work[u - 1].second)) {
       const Plan& pl = plans[work[u].second.x];
       b->classes.push_back({batch_class_kernel_ptr(pl.kind, pl.d), batch_group_kernel_ptr(pl.kind, pl.d), (uint32_t)u,
-                            0u, false, false});
+                            0u, (uint32_t)u, 0u, (uint32_t)u, 0u});
     }
     auto& c = b->classes.back();
     c.count += 1;
-    const BatchFilter& hf = b->host_filters[work[u].second.x];
-    const uint32_t all = (hf.m >= 32) ? 0xffffffffu : ((1u << hf.m) - 1u);
-    c.any_group = c.any_group || (hf.gsel & all) != 0;
-    c.any_tile = c.any_tile || (hf.gsel & all) != all;
+    const int pk = paths(work[u].second);
+    if (pk <= 1) c.gcount = (uint32_t)u + 1u - c.g0;          // group range: [g0, g0 + gcount)
+    if (pk >= 1 && c.tcount == 0) c.t0 = (uint32_t)u;         // tile range: [t0, t0 + tcount)
+    if (pk >= 1) c.tcount = (uint32_t)u + 1u - c.t0;
   }
   for (const auto& c : b->classes) {
     if (!c.kernel || !c.gkernel) {
@@ -1676,7 +1700,6 @@ pf_status pf_batch_create(int32_t F, const pf_model* models, const int64_t* N, c
   auto bail = [&](cudaError_t err, const char* what) {
     std::string m2 = std::string(what) + ": " + cudaGetErrorString(err);
     cudaStreamSynchronize(b->stream);
-    cudaStreamDestroy(b->cap_stream);
     if (b->own_ws) cudaFree(b->ws);
     delete b;
     return bfail(nullptr, PF_ECUDA, m2);
@@ -1704,15 +1727,32 @@ pf_status pf_batch_run(pf_batch* b, const float* y, int32_t T, double* loglik_in
   if (T < 0 || (T > 0 && !y)) return bfail(b, PF_EINVAL, "need T >= 0 and y != NULL");
   const int R = b->ring, F = b->F;
   // one time step: a launch per class of filters, then the step counter
+  // One time step: the tile-path kernels (small filters, short) on the side
+  // stream beside the group-path kernels (they touch disjoint filters), both
+  // joined before the kernel that advances the step counter.
+  bool any_tile = false;
+  for (const auto& c : b->classes) any_tile = any_tile || c.tcount != 0;
   auto launch_step = [&](cudaStream_t s) -> cudaError_t {
-    for (auto& c : b->classes) {
-      uint32_t u0 = c.u0;
-      void* cargs[] = {&b->BP, &u0};
-      cudaError_t le = cudaSuccess;
-      if (c.any_tile) le = cudaLaunchKernel(c.kernel, dim3(c.count), dim3(kBlock), cargs, b->smem, s);
-      if (le == cudaSuccess && c.any_group) le = cudaLaunchKernel(c.gkernel, dim3(c.count), dim3(kBlock), cargs, b->smem, s);
-      if (le != cudaSuccess) return le;
+    cudaError_t le = cudaSuccess;
+    if (any_tile) {
+      le = cudaEventRecord(b->fork_ev, s);
+      if (le == cudaSuccess) le = cudaStreamWaitEvent(b->side, b->fork_ev, 0);
+      for (auto& c : b->classes) {
+        if (le != cudaSuccess || !c.tcount) continue;
+        uint32_t u0 = c.t0;
+        void* cargs[] = {&b->BP, &u0};
+        le = cudaLaunchKernel(c.kernel, dim3(c.tcount), dim3(kBlock), cargs, b->smem, b->side);
+      }
+      if (le == cudaSuccess) le = cudaEventRecord(b->join_ev, b->side);
     }
+    for (auto& c : b->classes) {
+      if (le != cudaSuccess || !c.gcount) continue;
+      uint32_t u0 = c.g0;
+      void* cargs[] = {&b->BP, &u0};
+      le = cudaLaunchKernel(c.gkernel, dim3(c.gcount), dim3(kBlock), cargs, b->smem, s);
+    }
+    if (le == cudaSuccess && any_tile) le = cudaStreamWaitEvent(s, b->join_ev, 0);
+    if (le != cudaSuccess) return le;
     void* aargs[] = {&b->BP};
     return cudaLaunchKernel(batch_advance_kernel_ptr(), dim3(1), dim3(32), aargs, 0, s);
   };
@@ -1803,8 +1843,6 @@ const char* pf_batch_last_error(const pf_batch* b) {
 pf_status pf_batch_destroy(pf_batch* b) {
   if (!b) return PF_OK;
   cudaError_t e = cudaStreamSynchronize(b->stream);
-  if (b->graph) cudaGraphExecDestroy(b->graph);
-  if (b->cap_stream) cudaStreamDestroy(b->cap_stream);
   if (b->own_ws && b->ws) cudaFree(b->ws);
   delete b;
   if (e != cudaSuccess) return bfail(nullptr, PF_ECUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e));
