@@ -237,6 +237,7 @@ __device__ __forceinline__ void group_iterations(const GroupCtx& c, const RoundK
       run += __float2uint_rz(e * 16777216.0f);
       P[mm] = run;
     }
+    float s1_lane = s1;                              // my members' share (the group's, with G = 1)
 #pragma unroll
     for (int off = 1; off < G; off <<= 1) s1 += __shfl_xor_sync(FULL, s1, off);
     if (!(s1 >= 1.0f && s1 <= (float)A)) {
@@ -265,6 +266,7 @@ __device__ __forceinline__ void group_iterations(const GroupCtx& c, const RoundK
         run += __float2uint_rz(e * 16777216.0f);
         P[mm] = run;
       }
+      s1_lane = s1;
 #pragma unroll
       for (int off = 1; off < G; off <<= 1) s1 += __shfl_xor_sync(FULL, s1, off);
       if (!live && j == 0) status |= kStatusZeroGroup;
@@ -277,12 +279,6 @@ __device__ __forceinline__ void group_iterations(const GroupCtx& c, const RoundK
     }
     const uint32_t Q = (G > 1) ? __shfl_sync(FULL, incl, G - 1, G) : incl;
     const uint32_t excl = incl - run;
-#pragma unroll
-    for (int off = 1; off < G; off <<= 1) {
-      s2 += __shfl_xor_sync(FULL, s2, off);
-#pragma unroll
-      for (int t = 0; t < D; ++t) sx[t] += __shfl_xor_sync(FULL, sx[t], off);
-    }
 #pragma unroll
     for (int mm = 0; mm < M; ++mm) P[mm] += excl;
     if (c.prec) {                  // test output: the integer prefix sums the draws use
@@ -326,9 +322,11 @@ __device__ __forceinline__ void group_iterations(const GroupCtx& c, const RoundK
         for (int t = 0; t < D; ++t) zx[t] = 0.0f;
         merge_partial<D>(acc, accx, lv_new + gg.log_a, 1.0f, 1.0f / (float)A, zx);
       }
-    } else if (j == 0) {
-      lV_out[g] = (Q != 0) ? (mx + logf(s1) - gg.log_a) : -INFINITY;
-      merge_partial<D>(acc, accx, mx, s1, s2, sx);
+    } else {
+      if (j == 0) lV_out[g] = (Q != 0) ? (mx + logf(s1) - gg.log_a) : -INFINITY;
+      // every lane folds its own members' sums into its partial (the block's
+      // fold adds the lanes up), so the group needs no cross-lane sums of them
+      merge_partial<D>(acc, accx, mx, s1_lane, s2, sx);
     }
     __syncwarp();
 
