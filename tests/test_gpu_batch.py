@@ -21,6 +21,22 @@ def _specs():
     return out
 
 
+def _specs_group():
+    """Filters whose digits run the group path inside the batch (a power-of-two
+    radix <= 32 whose groups fill whole block iterations: groups per iteration
+    = 256 / lanes per group, lanes = radix / members per lane, members per lane
+    = the largest power of two m <= radix with m d <= 16), at d = 1, 2, 4 and 8,
+    with every radix from 2 to 32, and two filters that mix both paths (a radix
+    3 digit on the tile path)."""
+    shapes = [(8, (32, 32)), (8, (16, 8, 8)), (4, (16, 16, 8)), (4, (16, 16, 16, 3)), (2, (32, 32, 2)),
+              (1, (16, 16, 16)), (1, (2, 4, 32, 16)), (8, (32, 32, 3))]
+    out = []
+    for f, (d, rad) in enumerate(shapes):
+        model = S.sv_model() if (d == 1 and f == 5) else (S.lg_scalar() if d == 1 else S.lg_dense(d, seed=20 + f))
+        out.append((model, int(np.prod(rad)), rad, 9100 + f))
+    return out
+
+
 def _obs(specs, T):
     dy_max = max(s[0].dy for s in specs)
     y = np.zeros((len(specs), T, dy_max), dtype=np.float32)
@@ -29,15 +45,16 @@ def _obs(specs, T):
     return y
 
 
-def test_each_filter_independent_of_the_batch(bfpf):
-    specs = _specs()
+@pytest.mark.parametrize("which", ["mixed", "group"])
+def test_each_filter_independent_of_the_batch(bfpf, which):
+    specs = _specs() if which == "mixed" else _specs_group()
     T = 9
     y = _obs(specs, T)
     b = bfpf.FilterBatch(specs)
     r = b.run(y)
     ll = b.loglik()
     b.close()
-    for f in (0, 3, 5, 9):
+    for f in ((0, 3, 5, 9) if which == "mixed" else (0, 3, 5, 7)):
         one = bfpf.FilterBatch([specs[f]])
         r1 = one.run(y[f:f + 1, :, :specs[f][0].dy])
         assert np.array_equal(r1["inc"][0], r["inc"][f])
@@ -58,11 +75,13 @@ def test_batch_initial_states_equal_single_filter(bfpf):
     b.close()
 
 
-def test_batch_lockstep_against_oracle(bfpf):
+@pytest.mark.parametrize("which", ["mixed", "group"])
+def test_batch_lockstep_against_oracle(bfpf, which):
     """Every step of every filter re-run by the oracle from the batch's own state:
     likelihood increments, means, ESS and new carried weights to the parity
-    tolerances; states of particles whose draw is decidable to 1e-5."""
-    specs = _specs()
+    tolerances; states of particles whose draw is decidable to 1e-5.  "group":
+    filters on the batch's group path (every radix 2 to 32, d = 1 to 8)."""
+    specs = _specs() if which == "mixed" else _specs_group()
     T = 6
     y = _obs(specs, T)
     b = bfpf.FilterBatch(specs)
@@ -93,7 +112,7 @@ def test_batch_lockstep_against_oracle(bfpf):
             rep.merge(LS.Report(draws=N, undecidable=int(np.sum(~dec)), max_state_err=e_x,
                                 max_logweight_err=e_lv, max_inc_err=e_inc, max_mean_err=e_mean))
     b.close()
-    print("batch lockstep", dict(rep))
+    print("batch lockstep", which, dict(rep))
     assert rep["undecidable"] <= 0.02 * rep["draws"]
 
 
