@@ -16,6 +16,28 @@ __device__ __forceinline__ float obs_log_term(const ModelParams& mp, const float
   if constexpr (KIND == kStochVol) {
     return fmaf(-0.5f, x[0], -(y[0] * y[0] * mp.inv2b2) * ex2_ftz(x[0] * -1.4426950408889634f));
   } else {
+    if (mp.flags & kHIdentity) {         // H = I implies dy = d: every bound is D
+      float ss = 0.0f;
+      if (mp.flags & kLrDiagonal) {
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          const float z = mp.Lri[j * kMaxDim + j] * (y[j] - x[j]);
+          ss = fmaf(z, z, ss);
+        }
+      } else {
+        float r[D];
+#pragma unroll
+        for (int j = 0; j < D; ++j) r[j] = y[j] - x[j];
+#pragma unroll
+        for (int j = 0; j < D; ++j) {
+          float z = 0.0f;
+#pragma unroll
+          for (int u = 0; u <= j; ++u) z = fmaf(mp.Lri[j * kMaxDim + u], r[u], z);
+          ss = fmaf(z, z, ss);
+        }
+      }
+      return -0.5f * ss;
+    }
     float r[kMaxDim];
 #pragma unroll
     for (int j = 0; j < kMaxDim; ++j) {
