@@ -276,12 +276,15 @@ __device__ __forceinline__ bool last_block_done(DevState* st) {
 template <int D, bool ADVANCE = true>
 __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, float* accx, const Sched& sc,
                                             uint32_t status, float muf, float* lv_single_out = nullptr) {
-  double S[2 + D];
-  float Mx;
-  if (!fold_partials<D>(p, acc, accx, status, S, Mx)) return;
   DevState* st = p.st;
   const uint32_t n = sc.n;
-  if (!sc.obs) {            // a later stage of the all-stages schedule: no summaries
+  if (!sc.obs) {            // a later stage of the all-stages schedule: no summaries,
+    __shared__ uint32_t s_last_stage;   // only the last block to finish advances the stage
+    if (status) atomicOr(&st->status, status);
+    __syncthreads();
+    if (threadIdx.x == 0) s_last_stage = (atomicAdd(&st->done, 1u) == gridDim.x - 1) ? 1u : 0u;
+    __syncthreads();
+    if (!s_last_stage || threadIdx.x != 0) return;
     st->done = 0;
     __threadfence();
     if (sc.mut) {
@@ -292,6 +295,9 @@ __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, fl
     }
     return;
   }
+  double S[2 + D];
+  float Mx;
+  if (!fold_partials<D>(p, acc, accx, status, S, Mx)) return;
   double lme;
   write_summaries<D>(p, S, Mx, n, muf, &lme);
   st->done = 0;

@@ -231,9 +231,11 @@ __device__ __forceinline__ void group_iterations(const GroupCtx& c, const RoundK
     for (int mm = 0; mm < M; ++mm) {
       const float e = exp_weight(lw[mm] - mx);         // the group maximum weighs exactly 1
       s1 += e;
-      s2 = fmaf(e, e, s2);
+      if (obs) {                                       // the step's summaries: this stage weights with g_n
+        s2 = fmaf(e, e, s2);
 #pragma unroll
-      for (int t = 0; t < D; ++t) sx[t] = fmaf(e, xv[mm][t], sx[t]);
+        for (int t = 0; t < D; ++t) sx[t] = fmaf(e, xv[mm][t], sx[t]);
+      }
       run += __float2uint_rz(e * 16777216.0f);
       P[mm] = run;
     }
@@ -326,7 +328,7 @@ __device__ __forceinline__ void group_iterations(const GroupCtx& c, const RoundK
       if (j == 0) lV_out[g] = (Q != 0) ? (mx + logf(s1) - gg.log_a) : -INFINITY;
       // every lane folds its own members' sums into its partial (the block's
       // fold adds the lanes up), so the group needs no cross-lane sums of them
-      merge_partial<D>(acc, accx, mx, s1_lane, s2, sx);
+      if (obs) merge_partial<D>(acc, accx, mx, s1_lane, s2, sx);
     }
     __syncwarp();
 
