@@ -322,11 +322,13 @@ pf_status pf_philox_blocks(uint64_t seed, uint32_t c0, uint32_t c1, uint32_t c2,
  * dy_max = the largest dy of the batch; outputs are [F][T] (increments, ESS)
  * and [F][T][d_max] (means), d_max = the largest d.  workspace as in pf_create
  * (NULL: the library allocates).  A filter's results do not depend on the
- * other filters of the batch.  One kernel launch runs one time step of every
- * filter (launches captured in a CUDA graph per chunk of opts.chunk_len steps);
- * a filter's step is split over ceil(N (d + 1) / W) thread blocks, at most the
- * fewest tiles of any of its digits, where W = opts.grid if > 0 (particle-
- * dimensions of work per block), else 32768; the blocks of one filter fold their
+ * other filters of the batch.  A time step of every filter is a few kernel
+ * launches (per class of model kind and d, one for the digits on the
+ * register-resident group path and one for the tile path; captured in a CUDA
+ * graph per chunk of opts.chunk_len steps); a filter's step is split over
+ * max(ceil(N (d + 1) / W), ceil(N / 16384)) thread blocks, at most the fewest
+ * tiles of any of its digits, where W = opts.grid if > 0 (particle-dimensions
+ * of work per block), else 32768; the blocks of one filter fold their
  * partial sums in a fixed order, so a filter's results depend only on itself, W
  * and opts.tile (particles per tile, 0 = by state dimension).
  */

@@ -1438,6 +1438,7 @@ struct BatchLayout {
 // thread block (a 2^14-particle filter of dimension 1, or 2^11 particles of dimension 8).
 inline double batch_work(const Plan& pl) { return (double)pl.N * (pl.d + 1); }
 constexpr double kBatchUnitWork = 32768.0;
+constexpr double kBatchUnitParticles = 16384.0;
 
 // Plan every filter and lay the batch out in one workspace.
 // Group-path geometry of digit k of a batch filter: a power-of-two radix <= 32
@@ -1508,7 +1509,10 @@ pf_status plan_batch(int32_t F, const pf_model* models, const int64_t* N, const 
   for (int32_t f = 0; f < F; ++f) {
     uint32_t tiles = 0xffffffffu;
     for (int k = 0; k < plans[f].m; ++k) tiles = std::min(tiles, plans[f].geom[k].ntiles);
-    const double want = std::ceil(batch_work(plans[f]) / unit_work);
+    // at most kBatchUnitParticles particles per unit, so that no unit of a
+    // cheap (small d) filter outweighs an SM's fair share of its class
+    const double want = std::max(std::ceil(batch_work(plans[f]) / unit_work),
+                                 std::ceil((double)plans[f].N / kBatchUnitParticles));
     const uint32_t U = (uint32_t)std::max(1.0, std::min({want, (double)tiles, 65535.0}));
     L.U[f] = U;
     L.pbase[f] = (U > 1) ? L.nslots : 0u;
