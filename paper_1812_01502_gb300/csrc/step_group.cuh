@@ -513,11 +513,10 @@ __global__ void __launch_bounds__(kBlock) step_group_kernel(const __grid_constan
   step_group_body<D, KIND, A, G, STAGED, ADAPT>(p, gg);
 }
 
-// The same for d >= 5 and one stage per launch, with at most 85 registers so
-// that three blocks share an SM (a few bytes of spills; with two blocks per SM
-// the 8-D step was short of warps to hide its latencies).  The staged
-// instantiations keep the unbounded build: bounded, they spill hundreds of
-// bytes per thread.
+// The same for d >= 5, with at most 80 registers so that three blocks share
+// an SM (a few bytes of spills; with two blocks per SM the 8-D step was short
+// of warps to hide its latencies).  The staged instantiations of radices below
+// 16 keep the unbounded build: bounded, they spill about 160 bytes at d = 8.
 template <int D, int KIND, int A, int G, bool STAGED, bool ADAPT = false>
 __global__ void __launch_bounds__(kBlock, 3) step_group_kernel_d5(const __grid_constant__ StepParams p,
                                                                   const __grid_constant__ GroupGeom gg) {
@@ -532,7 +531,7 @@ inline const void* group_kernel_pick(int& G) {
   constexpr int M = (SMALL && MD > 2) ? 2 : MD;
   constexpr int GG = A / M;
   G = GG;
-  if constexpr (D >= 5 && !STAGED)
+  if constexpr (D >= 5 && (!STAGED || A >= 16))
     return reinterpret_cast<const void*>(&step_group_kernel_d5<D, KIND, A, GG, STAGED, ADAPT>);
   return reinterpret_cast<const void*>(&step_group_kernel<D, KIND, A, GG, STAGED, ADAPT>);
 }
