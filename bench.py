@@ -788,10 +788,12 @@ def schedules_leg(bf, w, dev, flush, K=30, W=3):
     """The paper's schedules on the main workload at full size: all stages per
     step and fully adapted resampling (theta = 0.5, and theta > 1, which runs
     every stage), L2 flushed before every timed step.  Algorithmic bytes per
-    step: every stage launch reads and writes the states and its carried
-    weights (compact per group; per particle in the adaptive schedule, whose
-    weight pass reads the states and weights and writes the weights, and whose
-    last launch still reads and writes the states when it was skipped)."""
+    step: every launch reads and writes the states and reads and writes its
+    carried weights (compact per group; in the all-stages schedule a launch
+    runs one stage or several consecutive digits of one radix, pf_describe's
+    "fused" list; per particle in the adaptive schedule, whose weight pass
+    reads the states and weights and writes the weights, and whose last launch
+    still reads and writes the states when it was skipped)."""
     import numpy as np
     import torch
     import synthetic as S
@@ -803,6 +805,12 @@ def schedules_leg(bf, w, dev, flush, K=30, W=3):
                      ("adaptive_0.5", {"adaptive": True, "ess_threshold": 0.5}),
                      ("adaptive_all", {"adaptive": True, "ess_threshold": 1.5})):
         f = bf.ButterflyFilter(w.model, N, w.radices, w.filter_seed, device=dev, **kw)
+        desc = f.describe()
+        launches = int(desc["launches_per_step"])
+        # (first digit, last digit) of each launch of the all-stages schedule
+        spans = [(int(q["k0"]), int(q["k0"]) + int(q["digits"]) - 1) for q in desc.get("fused", [])] \
+            or [(k, k) for k in range(m)]
+        ab = sum(8 * d * N + 4 * (N // w.radices[(k0 - 1) % m]) + 4 * (N // w.radices[k1]) for k0, k1 in spans)
         f.push(yd)
         ms, nbytes, nst = [], [], []
         with torch.cuda.stream(f.stream):
@@ -822,12 +830,12 @@ def schedules_leg(bf, w, dev, flush, K=30, W=3):
                 if kw.get("adaptive"):
                     nbytes.append((4 * d + 8) * N + sj * (8 * d + 8) * N + (8 * d * N if sj < m else 0))
                 else:
-                    nbytes.append(sum(algorithmic_bytes(w, k) for k in range(m)))
+                    nbytes.append(ab)
         f.close()
         t = float(np.mean(ms))
         out[name] = {"ms_per_step": t, "p99_ms": float(np.percentile(ms, 99)), "steps": K,
                      "stages_per_step": float(np.mean(nst)),
-                     "launches_per_step": m + 1 if kw.get("adaptive") else m,
+                     "launches_per_step": launches,
                      "particle_steps_per_s": N / (t * 1e-3),
                      "hbm_gbs_algorithmic": float(np.sum(nbytes)) / (float(np.sum(ms)) * 1e-3) / 1e9}
     return out

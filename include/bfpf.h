@@ -88,8 +88,12 @@ typedef struct {
  * V_s = A_s V_{s-1} (Section 3, eq. (V_defn_proofs)), then mutates.  After the
  * last stage every carried weight is equal (Lemma 3(c)).  Without the flag
  * each step runs the one stage on digit n mod m (the default, cheapest
- * schedule).  Costs m kernel launches per time step.  Cannot be combined
- * with PF_RECORD_ANCESTORS (EINVAL).  Ignored when m = 1. */
+ * schedule).  Consecutive digits of one radix (a power of two <= 32) share a
+ * kernel launch while the particles their stages can exchange fit one
+ * shared-memory tile (4096 particles at d = 1, 2048 at d <= 4, 1024 above);
+ * otherwise one launch per stage, m per time step (pf_describe lists the
+ * launches).  Cannot be combined with PF_RECORD_ANCESTORS (EINVAL).  Ignored
+ * when m = 1. */
 #define PF_ALL_STAGES 2u
 /* Fully adapted augmented resampling (Section 1.2): each time step weights
  * with g_n, then runs the stages of Algorithm 3 on digits 0, 1, ..., m-1 in
@@ -136,6 +140,10 @@ typedef struct {
  * draws go through the overflow list and most buckets search P in global
  * memory.  Results are those of the normal path; only slower. */
 #define PF_TEST_SMALL_BUCKETS 0x40000000u
+/* Test hook for PF_ALL_STAGES: one launch per stage even where consecutive
+ * digits of one radix (a power of two <= 32) would share a fused launch.  The
+ * same filter; with the fused kernels' lane split the same numbers. */
+#define PF_TEST_STAGE_PER_LAUNCH 0x20000000u
 
 typedef struct {
     int32_t tile;        /* target particles per thread-block tile; 0 = automatic            */

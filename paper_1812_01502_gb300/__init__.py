@@ -35,6 +35,7 @@ PF_ROTATE = 8
 PF_ISLANDS = 16
 PF_ISLANDS_PLAIN = 32
 PF_TEST_SMALL_BUCKETS = 0x40000000
+PF_TEST_STAGE_PER_LAUNCH = 0x20000000
 PF_DIGIT_SETS = 64
 PF_RECORD_DRAWS = 128
 STATUS_NAMES = {PF_EINVAL: "PF_EINVAL", PF_ENOMEM: "PF_ENOMEM", PF_ECUDA: "PF_ECUDA",

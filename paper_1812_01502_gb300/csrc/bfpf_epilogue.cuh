@@ -269,13 +269,15 @@ __device__ __forceinline__ bool last_block_done(DevState* st) {
   return s_last_blk && threadIdx.x == 0;
 }
 
-// End of one launch of the one-digit or all-stages schedule.
+// End of one launch of the one-digit or all-stages schedule; the launch ran
+// adv stages (several when the all-stages schedule fuses consecutive digits).
 // ADVANCE = false (global resampling, which finishes the step in a later
 // kernel): the last block leaves n alone and instead writes the global
 // maximum log-weight and the single group's new log weight.
 template <int D, bool ADVANCE = true>
 __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, float* accx, const Sched& sc,
-                                            uint32_t status, float muf, float* lv_single_out = nullptr) {
+                                            uint32_t status, float muf, float* lv_single_out = nullptr,
+                                            uint32_t adv = 1u) {
   DevState* st = p.st;
   const uint32_t n = sc.n;
   if (!sc.obs) {            // a later stage of the all-stages schedule: no summaries,
@@ -291,7 +293,7 @@ __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, fl
       st->stage = 0;
       st->n = n + 1;
     } else {
-      st->stage = st->stage + 1;
+      st->stage = st->stage + adv;
     }
     return;
   }
@@ -307,7 +309,7 @@ __device__ __forceinline__ void finish_step(const StepParams& p, Partial acc, fl
       st->stage = 0;
       st->n = n + 1;
     } else {
-      st->stage = 1;
+      st->stage = adv;
     }
   } else {
     st->gmax = Mx;

@@ -32,6 +32,14 @@ const void* group_kernel_d6(int kind, int a, int* G, bool staged, bool adapt, bo
 const void* group_kernel_d7(int kind, int a, int* G, bool staged, bool adapt, bool small);
 const void* group_kernel_d8(int kind, int a, int* G, bool staged, bool adapt, bool small);
 
+// Fused all-stages launch step_pass_kernel<d, kind, a>(StepParams, PassGeom):
+// consecutive stages of one time step on digits of radix a (a power of two
+// <= 32) over shared-memory tiles.  nullptr if none.
+const void* select_pass_kernel(int d, int kind, int a);
+const void* pass_kernel_d1(int kind, int a);
+const void* pass_kernel_d2_4(int d, int kind, int a);
+const void* pass_kernel_d5_8(int d, int kind, int a);
+
 // Global-resampling comparator (radices = {N}, N > 1024): six kernels per step,
 // launched in the order weight, refine, scan, bounds, resolve, advance, each
 // taking (StepParams, GlobalParams).

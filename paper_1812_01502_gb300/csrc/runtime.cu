@@ -21,6 +21,7 @@
 #include "bfpf_global.cuh"
 #include "bfpf_kernels.h"
 #include "step_group_layout.cuh"
+#include "step_pass_layout.cuh"
 
 #include <nvtx3/nvToolsExt.h>
 
@@ -94,6 +95,14 @@ struct Plan {
   uint32_t log2b = 0, buckets = 1, bucket_cap = 0, stage_cap = 0;   // bucketed draws
   uint32_t cbits = 0, ccap = 0, nseg = 1;                            // coarse bins
   size_t smem_resolve = 0, smem_weight = 0, smem_refine = 0;
+  // All-stages schedule on power-of-two radices <= 32: npass fused launches per
+  // step (step_pass.cuh), each running consecutive digits of one radix; 0 = one
+  // launch per stage.
+  int npass = 0;
+  PassGeom pg[kMaxDigits]{};
+  const void* pass_kernel[kMaxDigits]{};
+  size_t pass_smem[kMaxDigits]{};
+  int pass_grid[kMaxDigits]{};
   Layout lay{};
 };
 
@@ -240,6 +249,8 @@ uint32_t largest_divisor_at_most(uint32_t n, uint32_t limit) {
     if (n % v == 0) return v;
   return 1;
 }
+
+bool plan_passes(Plan& pl, const int32_t* radices, int m);
 
 pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, int32_t m,
                     const pf_options* opts, Plan& pl, std::string& msg) {
@@ -547,9 +558,61 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
   pl.cap = (pl.cap + 3) / 4 * 4;
   pl.smem = (size_t)(d + 1) * pl.cap * 4 + (size_t)pl.cap * (pl.wide ? 8 : 4);
   pl.record = opts && (opts->flags & PF_RECORD_ANCESTORS);
+  if (staged && !pl.sets && !pl.islands && pow2 && !(opts && (opts->flags & PF_TEST_STAGE_PER_LAUNCH))) {
+    bool small_radix = true;
+    for (int k = 0; k < m; ++k) small_radix = small_radix && radices[k] <= 32;
+    if (small_radix && !plan_passes(pl, radices, m)) pl.npass = 0;
+  }
   pl.chunk_len = (opts && opts->chunk_len > 0) ? std::min<int>(opts->chunk_len, (int)kRing) : 64;
   if (!select_kernels(d, pl.kind, pl.wide, pl.ks)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
   return PF_OK;
+}
+
+// Splits the m digits of the all-stages schedule into fused launches: a launch
+// takes consecutive digits of one radix while a tile holding every particle
+// its stages can draw from fits pass_tile_max(d) and keeps runs of at least 16
+// consecutive indices per state row (or the tile is a whole index range).
+// False when a radix has no fused kernel (the schedule then keeps one launch
+// per stage).
+bool plan_passes(Plan& pl, const int32_t* radices, int m) {
+  auto lg2 = [](uint32_t v) { uint32_t l = 0; while ((1u << l) < v) ++l; return l; };
+  const uint32_t Tmax = pass_tile_max(pl.d);
+  int np = 0;
+  for (int k0 = 0; k0 < m;) {
+    const uint32_t A = (uint32_t)radices[k0];
+    const uint32_t S = pl.geom[k0].s;
+    auto fits = [&](uint64_t B) { return B <= Tmax && ((uint64_t)S * B <= Tmax || Tmax / B >= 16u); };
+    uint32_t J = 1, B = A;
+    while (k0 + (int)J < m && (uint32_t)radices[k0 + J] == A && fits((uint64_t)B * A)) {
+      B *= A;
+      ++J;
+    }
+    const void* kern = select_pass_kernel(pl.d, pl.kind, (int)A);
+    if (!kern || !fits(B)) return false;
+    PassGeom& g = pl.pg[np];
+    const bool whole = (uint64_t)S * B <= Tmax;           // L = s_k0: the tile is an index range
+    const uint32_t L = whole ? S : Tmax / B;
+    const uint32_t T = whole ? std::min(Tmax, pl.N) : Tmax;
+    g.k0 = (uint32_t)k0;
+    g.J = J;
+    g.pass = (uint32_t)np;
+    g.log2L = lg2(L);
+    g.log2S = lg2(S);
+    g.log2B = lg2(B);
+    g.log2T = lg2(T);
+    g.log2tl = whole ? 0u : lg2(S / L);
+    g.ntiles = pl.N / T;
+    g.log2sp = lg2(pl.geom[k0 == 0 ? m - 1 : k0 - 1].s);
+    g.nrows = (k0 == 0) ? T / A : T >> (g.log2L + lg2(A));
+    g.log_a = pl.geom[k0].log_a;
+    pl.pass_kernel[np] = kern;
+    pl.pass_smem[np] = pass_smem_layout(pl.d, (int)A, T, g.nrows).total;
+    ++np;
+    k0 += (int)J;
+  }
+  pl.npass = np;
+  for (int q = 0; q < np; ++q) pl.pg[q].npass = (uint32_t)np;
+  return true;
 }
 
 // The dynamic shared-memory limit is an attribute of the kernel, shared by every
@@ -646,6 +709,17 @@ pf_status finish_plan(Plan& pl, const pf_options* opts, std::string& msg) {
     dp.grid = std::max(1, std::min(grid, units));
     pl.max_grid = std::max(pl.max_grid, dp.grid);
   }
+  for (int q = 0; q < pl.npass; ++q) {
+    int per_sm = 0;
+    e = raise_smem_limit(pl.pass_kernel[q], pl.pass_smem[q]);
+    if (e == cudaSuccess)
+      e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, pl.pass_kernel[q], kBlock, pl.pass_smem[q]);
+    if (e != cudaSuccess) { msg = std::string("CUDA: ") + cudaGetErrorString(e); return PF_ECUDA; }
+    if (per_sm < 1) { msg = "fused stage tile does not fit in shared memory"; return PF_EINVAL; }
+    const int grid = (opts && opts->grid > 0) ? opts->grid : per_sm * sms;
+    pl.pass_grid[q] = std::max(1, std::min(grid, (int)pl.pg[q].ntiles));
+    pl.max_grid = std::max(pl.max_grid, pl.pass_grid[q]);
+  }
   const int grid = pl.max_grid;
   pl.grid = grid;
   Layout& L = pl.lay;
@@ -723,6 +797,12 @@ cudaError_t launch_step(pf_handle* h, cudaStream_t stream, uint64_t t) {
     h->launch_j[j - 1] = j - 1;
     void* args[] = {&h->P, &h->launch_j[j - 1]};
     return cudaLaunchKernel(pl.ak.stage, dim3(pl.max_grid), dim3(kBlock), args, pl.smem, stream);
+  }
+  if (h->plan.npass) {      // fused all-stages launch t mod npass of its step
+    Plan& pl = h->plan;
+    const int q = (int)(t % (uint64_t)pl.npass);
+    void* args[] = {&h->P, &pl.pg[q]};
+    return cudaLaunchKernel(pl.pass_kernel[q], dim3(pl.pass_grid[q]), dim3(kBlock), args, pl.pass_smem[q], stream);
   }
   const uint64_t kd = h->plan.sets ? 1 + t % (uint64_t)(h->plan.m - 1) : t % (uint64_t)h->plan.m;
   DigitPlan& dp = h->plan.dp[kd];
@@ -932,13 +1012,14 @@ namespace {
 pf_status enqueue_steps(pf_handle* h, int32_t L) {
   Trace tr("bfpf steps");
   const Plan& pl = h->plan;
-  const uint64_t lps = pl.islands ? 3 : pl.adaptive ? (uint64_t)pl.m + 1 : pl.sps;   // launches per step
+  const uint64_t lps = pl.islands ? 3 : pl.adaptive ? (uint64_t)pl.m + 1
+                                       : pl.npass ? (uint64_t)pl.npass : pl.sps;   // launches per step
   const uint64_t t0 = h->n_host * lps;
   const int64_t launches = (int64_t)L * (int64_t)lps;
   if (L == pl.chunk_len && L > 1) {
     if (h->graphs.empty()) h->graphs.assign(pl.m, nullptr);
     cudaGraphExec_t& exec =
-        h->graphs[pl.islands ? h->n_host & 1u : (pl.adaptive || pl.sets) ? 0 : t0 % (uint64_t)pl.m];
+        h->graphs[pl.islands ? h->n_host & 1u : (pl.adaptive || pl.sets || pl.npass) ? 0 : t0 % (uint64_t)pl.m];
     if (!exec) {
       cudaGraph_t graph = nullptr;
       PF_CUDA(h, cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal));
@@ -1034,7 +1115,9 @@ pf_status pf_get_state(const pf_handle* h, float* x, float* lV, double* scalars)
     const int kp = pl.sets ? (int)(1 + (t + pl.m - 2) % (pl.m - 1)) : (int)((t + pl.m - 1) % pl.m);
     const size_t cnt = pl.global ? 1 : pl.island_adaptive ? pl.N / pl.geom[0].a
                                      : pl.N / (pl.geom[kp].a * pl.geom[kp].w);
-    PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[t & 1u], 4 * cnt, cudaMemcpyDeviceToHost, h->stream));
+    // (fused all-stages launches alternate the buffers per launch: step n starts on (n npass) mod 2)
+    const uint64_t sel = pl.npass ? (uint64_t)st.n * (uint64_t)pl.npass : t;
+    PF_CUDA(h, cudaMemcpyAsync(lV, h->P.lV[sel & 1u], 4 * cnt, cudaMemcpyDeviceToHost, h->stream));
     PF_CUDA(h, cudaStreamSynchronize(h->stream));
   }
   if (scalars) {
@@ -1177,6 +1260,8 @@ pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
   const Plan& pl = h->plan;
   std::string o = "{\"N\": " + std::to_string(pl.N) + ", \"d\": " + std::to_string(pl.d) +
                   ", \"stages_per_step\": " + std::to_string(pl.sps) +
+                  ", \"launches_per_step\": " +
+                  std::to_string(pl.global ? 5 : pl.islands ? 3 : pl.adaptive ? pl.m + 1 : pl.npass ? pl.npass : (int)pl.sps) +
                   ", \"adaptive\": " + (pl.adaptive ? "true" : "false") +
                   ", \"rotate\": " + (pl.rotate ? "true" : "false") +
                   ", \"ess_threshold\": " + std::to_string(pl.adaptive ? pl.theta : 0.0f) +
@@ -1201,7 +1286,19 @@ pf_status pf_describe(const pf_handle* h, char* buf, size_t len) {
          (dp.group ? "\"lanes\": " + std::to_string(dp.lanes) : "\"tile\": " + std::to_string(g.tile_n)) +
          ", \"grid\": " + std::to_string(dp.grid) + "}";
   }
-  o += "]}";
+  o += "]";
+  if (pl.npass) {
+    o += ", \"fused\": [";
+    for (int q = 0; q < pl.npass; ++q) {
+      const PassGeom& g = pl.pg[q];
+      if (q) o += ", ";
+      o += "{\"k0\": " + std::to_string(g.k0) + ", \"digits\": " + std::to_string(g.J) + ", \"tile\": " +
+           std::to_string(1u << g.log2T) + ", \"lows\": " + std::to_string(1u << g.log2L) + ", \"grid\": " +
+           std::to_string(pl.pass_grid[q]) + ", \"smem\": " + std::to_string(pl.pass_smem[q]) + "}";
+    }
+    o += "]";
+  }
+  o += "}";
   const size_t nb = std::min(len - 1, o.size());
   std::memcpy(buf, o.data(), nb);
   buf[nb] = 0;

@@ -122,6 +122,13 @@ const void* select_group_kernel(int d, int kind, int a, int* G, bool staged, boo
   }
 }
 
+const void* select_pass_kernel(int d, int kind, int a) {
+  if (d == 1) return pass_kernel_d1(kind, a);
+  if (d >= 2 && d <= 4) return pass_kernel_d2_4(d, kind, a);
+  if (d >= 5 && d <= 8) return pass_kernel_d5_8(d, kind, a);
+  return nullptr;
+}
+
 cudaError_t launch_philox_blocks(uint64_t seed, uint4 c, uint32_t count, uint32_t* out, cudaStream_t stream) {
   const uint32_t blocks = (count + kBlock - 1) / kBlock;
   philox_blocks_kernel<<<blocks ? (blocks > 4096 ? 4096 : blocks) : 1, kBlock, 0, stream>>>(

@@ -242,7 +242,12 @@ __device__ __forceinline__ void group_iterations(const GroupCtx& c, const RoundK
     float s1_lane = s1;                              // my members' share (the group's, with G = 1)
 #pragma unroll
     for (int off = 1; off < G; off <<= 1) s1 += __shfl_xor_sync(FULL, s1, off);
-    if (!(s1 >= 1.0f && s1 <= (float)A)) {
+    bool redo = !(s1 >= 1.0f && s1 <= (float)A);
+    // with several lanes per group the whole warp takes the rare path when any
+    // group of it needs it, so that its shuffles stay converged (the other
+    // groups recompute the same values)
+    if constexpr (G > 1) redo = __any_sync(FULL, redo);
+    if (redo) {
       // Rare path: a non-finite log-weight (NaN / +inf -> weight zero) or a group
       // whose weights are all zero.  Recompute the group with sanitised weights.
 #pragma unroll

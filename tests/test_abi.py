@@ -75,5 +75,5 @@ def test_binding_flags_match_the_header(bfpf):
         if hasattr(bfpf, name):
             assert getattr(bfpf, name) == val, name
     for name in ("PF_RECORD_ANCESTORS", "PF_ALL_STAGES", "PF_ADAPTIVE", "PF_ROTATE", "PF_ISLANDS",
-                 "PF_ISLANDS_PLAIN", "PF_DIGIT_SETS", "PF_TEST_SMALL_BUCKETS"):
+                 "PF_ISLANDS_PLAIN", "PF_DIGIT_SETS", "PF_TEST_SMALL_BUCKETS", "PF_TEST_STAGE_PER_LAUNCH"):
         assert getattr(bfpf, name) == defines[name], name

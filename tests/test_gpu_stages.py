@@ -9,27 +9,72 @@ import lockstep as LS
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("name,model,radices,T", [
-    ("lg_radix2", S.lg_scalar(), (2,) * 10, 5),
-    ("sv_group", S.sv_model(), (16, 16, 4), 5),
-    ("lg4_group", S.lg_dense(4, seed=3), (8, 8, 4), 4),
-    ("lg8_group", S.lg_dense(8, seed=4), (32, 32), 3),
-    ("lg1_mixed_tile", S.lg_scalar(), (3, 5, 7), 5),
-    ("lg2_tile", S.lg_dense(2, seed=5), (64, 16), 4),
-    ("sv_wide", S.sv_model(), (300, 4), 4),
+# launches: fused launches per step (consecutive digits of one power-of-two
+# radix <= 32 share a launch while their tile fits), or m without fusion
+@pytest.mark.parametrize("name,model,radices,T,launches", [
+    ("lg_radix2", S.lg_scalar(), (2,) * 10, 5, 1),
+    ("sv_group", S.sv_model(), (16, 16, 4), 5, 2),
+    ("lg4_group", S.lg_dense(4, seed=3), (8, 8, 4), 4, 2),
+    ("lg8_group", S.lg_dense(8, seed=4), (32, 32), 3, 1),
+    ("lg8_two_launches", S.lg_dense(8, seed=6), (32, 32, 4), 3, 2),
+    ("sv_three_digits", S.sv_model(), (16, 16, 16, 16), 3, 2),
+    ("lg3_radix4", S.lg_dense(3, seed=7), (4,) * 7, 3, 2),
+    ("lg1_mixed_tile", S.lg_scalar(), (3, 5, 7), 5, 3),
+    ("lg2_tile", S.lg_dense(2, seed=5), (64, 16), 4, 2),
+    ("sv_wide", S.sv_model(), (300, 4), 4, 2),
 ])
-def test_all_stages_lockstep(bfpf, name, model, radices, T):
+@pytest.mark.parametrize("per_launch", [False, True])
+def test_all_stages_lockstep(bfpf, name, model, radices, T, launches, per_launch):
     N = int(np.prod(radices))
     y = S.simulate(model, T, seed=23)[1]
     seed = 777
-    f = bfpf.ButterflyFilter(model, N, radices, seed, all_stages=True)
-    assert f.describe()["stages_per_step"] == len(radices)
+    f = bfpf.ButterflyFilter(model, N, radices, seed, all_stages=True,
+                             extra_flags=bfpf.PF_TEST_STAGE_PER_LAUNCH if per_launch else 0)
+    d = f.describe()
+    assert d["stages_per_step"] == len(radices)
+    assert d["launches_per_step"] == (len(radices) if per_launch else launches), d
     rep = LS.Report()
     for n in range(T):
         rep.merge(LS.check_step_all_stages(f, model, radices, seed, y[n], n))
     f.close()
     print(name, dict(rep))
     assert rep["undecided_lines"] <= max(8, 0.02 * N * T)
+
+
+@pytest.mark.parametrize("model,radices,T", [
+    (S.sv_model(), (16,) * 5, 6),                 # fused launches on digits {0, 1, 2} and {3, 4}
+    (S.lg_dense(8, seed=4), (32, 32, 32), 4),     # {0, 1} and {2}; groups over 16 lanes
+    (S.lg_scalar(), (4,) * 9, 4),                 # {0 .. 5} and {6, 7, 8}
+])
+def test_fused_launches_equal_one_launch_per_stage(bfpf, model, radices, T):
+    """Fused launches split each group over lanes as the one-stage group
+    kernel does, so from the same state the two forms of the schedule give the
+    same particles and carried weights bit for bit (step 0).  The step
+    summaries add the same terms in another block order, so from step 1 on the
+    normaliser mu subtracted from the log-weights may differ in its last bits:
+    then the carried weights agree to rounding and a draw may fall on the other
+    side of a boundary, rarely."""
+    N = int(np.prod(radices))
+    y = S.simulate(model, T, seed=41)[1]
+    a = bfpf.ButterflyFilter(model, N, radices, 99, all_stages=True)
+    b = bfpf.ButterflyFilter(model, N, radices, 99, all_stages=True, extra_flags=bfpf.PF_TEST_STAGE_PER_LAUNCH)
+    assert a.describe()["launches_per_step"] < len(radices) == b.describe()["launches_per_step"]
+    for n in range(T):
+        ma, ia, ea = a.step(y[n])
+        mb, ib, eb = b.step(y[n])
+        xa, lva, _ = a.state()
+        xb, lvb, _ = b.state()
+        if n == 0:
+            assert np.array_equal(xa, xb), f"step {n}: states differ at {np.argwhere(xa != xb)[:5]}"
+            assert np.array_equal(lva, lvb)
+        else:
+            assert np.mean(xa != xb) <= 1e-3, f"step {n}: {np.mean(xa != xb)} of the states differ"
+            assert LS.rel_err(lva, lvb) <= 1e-6
+        assert abs(ia - ib) <= 1e-6 * max(1.0, abs(ib))
+        assert np.allclose(ma, mb, rtol=1e-5, atol=1e-6) and abs(ea - eb) <= 1e-4 * eb
+    assert a.stage_count() == b.stage_count() == T * len(radices)
+    a.close()
+    b.close()
 
 
 def test_all_stages_graph_equals_steps(bfpf):
