@@ -90,9 +90,9 @@ typedef struct {
  * each step runs the one stage on digit n mod m (the default, cheapest
  * schedule).  Consecutive digits of one radix (a power of two <= 32) share a
  * kernel launch while the particles their stages can exchange fit one
- * shared-memory tile (4096 particles at d = 1, 2048 at d <= 4, 1024 above);
- * otherwise one launch per stage, m per time step (pf_describe lists the
- * launches).  Cannot be combined with PF_RECORD_ANCESTORS (EINVAL).  Ignored
+ * shared-memory tile (4096 particles at d = 1, 2048 at d <= 4, 1024 above),
+ * unless N < 2^16 and that saves fewer than half of the launches; otherwise
+ * one launch per stage, m per time step (pf_describe lists the launches).  Cannot be combined with PF_RECORD_ANCESTORS (EINVAL).  Ignored
  * when m = 1. */
 #define PF_ALL_STAGES 2u
 /* Fully adapted augmented resampling (Section 1.2): each time step weights

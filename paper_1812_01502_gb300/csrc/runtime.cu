@@ -562,6 +562,11 @@ pf_status make_plan(const pf_model* model, int64_t N64, const int32_t* radices, 
     bool small_radix = true;
     for (int k = 0; k < m; ++k) small_radix = small_radix && radices[k] <= 32;
     if (small_radix && !plan_passes(pl, radices, m)) pl.npass = 0;
+    // A population below 2^16 whose digits fuse into more than half as many
+    // launches keeps one launch per stage: there the group kernels' split (two
+    // members per lane for small populations) keeps more threads busy than the
+    // fused tiles, and few launches are saved (measured on the 7-D workload).
+    if (pl.npass && pl.N < 65536u && 2 * pl.npass > m) pl.npass = 0;
   }
   pl.chunk_len = (opts && opts->chunk_len > 0) ? std::min<int>(opts->chunk_len, (int)kRing) : 64;
   if (!select_kernels(d, pl.kind, pl.wide, pl.ks)) { msg = "unsupported (d, model) combination"; return PF_EINVAL; }
@@ -590,9 +595,13 @@ bool plan_passes(Plan& pl, const int32_t* radices, int m) {
     const void* kern = select_pass_kernel(pl.d, pl.kind, (int)A);
     if (!kern || !fits(B)) return false;
     PassGeom& g = pl.pg[np];
+    // Tiles of up to Tmax particles, smaller where that leaves fewer than
+    // about 512 tiles (small populations: more thread blocks).
+    uint32_t fill = 1;
+    while (fill * 2u <= pl.N / 512u) fill *= 2u;
     const bool whole = (uint64_t)S * B <= Tmax;           // L = s_k0: the tile is an index range
-    const uint32_t L = whole ? S : Tmax / B;
-    const uint32_t T = whole ? std::min(Tmax, pl.N) : Tmax;
+    const uint32_t L = whole ? S : std::max(16u, std::min(Tmax / B, fill / B));
+    const uint32_t T = whole ? std::max(S * B, std::min(Tmax, fill)) : L * B;
     g.k0 = (uint32_t)k0;
     g.J = J;
     g.pass = (uint32_t)np;

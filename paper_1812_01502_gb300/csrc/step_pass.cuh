@@ -82,9 +82,10 @@ __device__ __forceinline__ uint32_t pass_search(const uint32_t* row, const uint3
   }
 }
 
-// Three blocks per SM for d <= 4 (the tile's shared memory allows it), two above.
+// Three blocks per SM at d = 1 (80 registers), two above (128 registers: the
+// weighting stage holds up to 16 state values of its members in registers).
 template <int D, int KIND, int A>
-__global__ void __launch_bounds__(kBlock, D <= 4 ? 3 : 2) step_pass_kernel(const __grid_constant__ StepParams p,
+__global__ void __launch_bounds__(kBlock, D == 1 ? 3 : 2) step_pass_kernel(const __grid_constant__ StepParams p,
                                                                           const __grid_constant__ PassGeom pg) {
   static_assert(A >= 2 && A <= 32 && (A & (A - 1)) == 0, "radix must be a power of two <= 32");
   constexpr int LA = pass_log2(A);
@@ -93,6 +94,11 @@ __global__ void __launch_bounds__(kBlock, D <= 4 ? 3 : 2) step_pass_kernel(const
   constexpr int MQ = A < 4 ? A : 4;            // members per draw unit (one Philox block)
   constexpr int RS = pass_row_stride(A);
   constexpr int NPV = A <= 4 ? A : A / 4;      // words loaded per unit for the search (pivots incl. Q)
+  // members per thread in the draw phase: up to 16, so that a full tile
+  // still gives every thread of the block some (4096 / 16 = 256 at d = 1)
+  constexpr int MBT = (int)(pass_tile_max(D) / (uint32_t)kBlock);
+  constexpr int MB = A < MBT ? A : (MBT < MQ ? MQ : MBT);
+  constexpr uint32_t NCH = A / MB;             // threads per group there
   constexpr unsigned FULL = 0xffffffffu;
   static_assert(M <= 16 && kBlock % G == 0, "bad weighting split");
   extern __shared__ __align__(16) unsigned char smem[];
@@ -200,20 +206,40 @@ __global__ void __launch_bounds__(kBlock, D <= 4 ? 3 : 2) step_pass_kernel(const
           const bool valid = gi < NG;                // the same for the G lanes of a group
           // lanes past the last group read group 0's states (and write nothing)
           const uint32_t pos0 = ((valid ? gi : 0u) << LA) + jl * M;
-          float lw[M];
+          // the tile is the index range from base_i, and a group's carried
+          // weights (digit m - 1's groups: index i mod s_{m-1}) are consecutive
+          const uint32_t i0 = base_i + pos0;
+          const uint32_t lv0 = i0 & spmask;
+          float lw[M], xv[M][D];
+          if constexpr (M % 4 == 0) {
 #pragma unroll
-          for (int mm = 0; mm < M; ++mm) {
-            if (valid) {
-              const uint32_t pos = pos0 + mm;
-              float xv[D];
+            for (int q = 0; q < M / 4; ++q) {
 #pragma unroll
-              for (int c = 0; c < D; ++c) xv[c] = s_x[c * TP + pass_xpad(pos)];
-              lw[mm] = __ldg(lV_in + (i_of(pos) & spmask));
-              lw[mm] += obs_log_term<D, KIND>(mp, y, xv) - muf;
-            } else {
-              lw[mm] = 0.0f;                         // a finite dummy: no side effects below
+              for (int c = 0; c < D; ++c) {
+                const float4 v = *reinterpret_cast<const float4*>(X + (size_t)c * N + i0 + 4 * q);
+                xv[4 * q][c] = v.x;
+                xv[4 * q + 1][c] = v.y;
+                xv[4 * q + 2][c] = v.z;
+                xv[4 * q + 3][c] = v.w;
+              }
+              const float4 v = __ldg(reinterpret_cast<const float4*>(lV_in + lv0) + q);
+              lw[4 * q] = v.x;
+              lw[4 * q + 1] = v.y;
+              lw[4 * q + 2] = v.z;
+              lw[4 * q + 3] = v.w;
+            }
+          } else {
+#pragma unroll
+            for (int mm = 0; mm < M; ++mm) {
+#pragma unroll
+              for (int c = 0; c < D; ++c) xv[mm][c] = s_x[c * TP + pass_xpad(pos0 + mm)];
+              lw[mm] = __ldg(lV_in + lv0 + mm);
             }
           }
+#pragma unroll
+          for (int mm = 0; mm < M; ++mm)
+            lw[mm] = valid ? lw[mm] + (obs_log_term<D, KIND>(mp, y, xv[mm]) - muf)
+                           : 0.0f;                   // a finite dummy: no side effects below
           float mx = lw[0];
 #pragma unroll
           for (int mm = 1; mm < M; ++mm) mx = fmaxf(mx, lw[mm]);
@@ -230,7 +256,7 @@ __global__ void __launch_bounds__(kBlock, D <= 4 ? 3 : 2) step_pass_kernel(const
             s1 += e;
             s2 = fmaf(e, e, s2);
 #pragma unroll
-            for (int c = 0; c < D; ++c) sx[c] = fmaf(e, s_x[c * TP + pass_xpad(pos0 + mm)], sx[c]);
+            for (int c = 0; c < D; ++c) sx[c] = fmaf(e, xv[mm][c], sx[c]);
             run += __float2uint_rz(e * 16777216.0f);
             P[mm] = run;
           }
@@ -261,7 +287,7 @@ __global__ void __launch_bounds__(kBlock, D <= 4 ? 3 : 2) step_pass_kernel(const
               s1 += e;
               s2 = fmaf(e, e, s2);
 #pragma unroll
-              for (int c = 0; c < D; ++c) sx[c] = fmaf(e, s_x[c * TP + pass_xpad(pos0 + mm)], sx[c]);
+              for (int c = 0; c < D; ++c) sx[c] = fmaf(e, xv[mm][c], sx[c]);
               run += __float2uint_rz(e * 16777216.0f);
               P[mm] = run;
             }
@@ -354,31 +380,17 @@ __global__ void __launch_bounds__(kBlock, D <= 4 ? 3 : 2) step_pass_kernel(const
         }
       }
 
-      // ---- B: one draw per particle, in units of MQ consecutive members of a
-      // group (one Philox block); group gi of the stage has its member 0 at
-      // position base and its row at gi >> log2sig ----
-      for (uint32_t u = tid; u < (T / MQ); u += kBlock) {
+      // ---- B: one draw per particle.  A thread takes MB consecutive members of
+      // one group (MB a power of two dividing A): group gi of the stage has its
+      // member 0 at position base and its row at gi >> log2sig; the words of
+      // MQ members come from one Philox block ----
+      for (uint32_t u = tid; u < NG * NCH; u += kBlock) {
         const uint32_t gi = u & (NG - 1u);
-        const uint32_t r0 = (u >> log2NG) * MQ;
+        const uint32_t rb0 = (u >> log2NG) * MB;
         const uint32_t base = (gi & sigmask) | ((gi >> log2sig) << (log2sig + LA));
         const uint32_t* const row = s_rows + (gi >> log2sig) * RS;
         const uint32_t i0 = i_of(base);
         const uint32_t g = ((i0 >> (log2sk + LA)) << log2sk) | (i0 & skmask);   // the group's number
-        const uint32_t pi0 = g * A + r0;                                         // group-major index of member r0
-        uint32_t rw[MQ];
-        {
-          const uint4 w = philox4x32(make_uint4(pi0 >> 2, t, kPurposeResample, 0), p.rk);
-          if constexpr (MQ == 4) {
-            rw[0] = w.x;
-            rw[1] = w.y;
-            rw[2] = w.z;
-            rw[3] = w.w;
-          } else {
-            const bool hi2 = (pi0 & 2u) != 0u;
-            rw[0] = hi2 ? w.z : w.x;
-            rw[1] = hi2 ? w.w : w.y;
-          }
-        }
         uint32_t piv[NPV];
         if constexpr (A == 2) {
           const uint2 v = *reinterpret_cast<const uint2*>(row);
@@ -405,37 +417,73 @@ __global__ void __launch_bounds__(kBlock, D <= 4 ? 3 : 2) step_pass_kernel(const
           }
         }
         const uint32_t Q = piv[NPV - 1];
-        // propagation normals NQ members at a time (fewer registers at d = 6, 8,
-        // where a pair's normals still start on a Philox block)
-        constexpr int NQ = (D == 6 || D == 8) && MQ == 4 ? 2 : MQ;
+        // new map entries of a stage on the lowest in-tile digit (members
+        // adjacent): gathered in registers and stored 16 bytes at a time
+        constexpr int NPK = (MB >= 8) ? MB / 2 : 1;
+        uint32_t pk[NPK];
 #pragma unroll
-        for (int h = 0; h < MQ / NQ; ++h) {
-          float z[NQ * D];
-          if (last && mut) pass_normals<NQ * D>((pi0 + h * NQ) * D, n, p.rk, z);
+        for (int q = 0; q < NPK; ++q) pk[q] = 0u;
+        const bool packed = (MB >= 8) && log2sig == 0 && !last;
 #pragma unroll
-          for (int mq2 = 0; mq2 < NQ; ++mq2) {
-            const int mq = h * NQ + mq2;
-            const uint32_t r = r0 + mq;
-            uint32_t c = pass_search<A>(row, piv, __umulhi(rw[mq], Q));   // floor(r Q / 2^32) against P
-            if (Q == 0) c = r;                                         // an all-zero group keeps its particles
-            const uint32_t pc = base + (c << log2sig);
-            const uint32_t src = (j == 0) ? pc : (uint32_t)anc_old[pc];
-            if (!last) {
-              anc_new[base + (r << log2sig)] = (uint16_t)src;
+        for (int q4 = 0; q4 < MB / MQ; ++q4) {
+          const uint32_t pi0 = g * A + rb0 + q4 * MQ;       // group-major index of the unit's first member
+          uint32_t rw[MQ];
+          {
+            const uint4 w = philox4x32(make_uint4(pi0 >> 2, t, kPurposeResample, 0), p.rk);
+            if constexpr (MQ == 4) {
+              rw[0] = w.x;
+              rw[1] = w.y;
+              rw[2] = w.z;
+              rw[3] = w.w;
             } else {
-              float xh[D], xo[D];
-#pragma unroll
-              for (int cc = 0; cc < D; ++cc) xh[cc] = s_x[cc * TP + pass_xpad(src)];
-              if (mut) {
-                mutate<D, KIND>(mp, xh, z + mq2 * D, xo);
-              } else {
-#pragma unroll
-                for (int cc = 0; cc < D; ++cc) xo[cc] = xh[cc];
-              }
-              const uint32_t i = i0 + (r << log2sk);
-#pragma unroll
-              for (int cc = 0; cc < D; ++cc) X[(size_t)cc * N + i] = xo[cc];
+              const bool hi2 = (pi0 & 2u) != 0u;
+              rw[0] = hi2 ? w.z : w.x;
+              rw[1] = hi2 ? w.w : w.y;
             }
+          }
+          // propagation normals NQ members at a time (fewer registers at d = 6, 8,
+          // where a pair's normals still start on a Philox block)
+          constexpr int NQ = (D == 6 || D == 8) && MQ == 4 ? 2 : MQ;
+#pragma unroll
+          for (int h = 0; h < MQ / NQ; ++h) {
+            float z[NQ * D];
+            if (last && mut) pass_normals<NQ * D>((pi0 + h * NQ) * D, n, p.rk, z);
+#pragma unroll
+            for (int mq2 = 0; mq2 < NQ; ++mq2) {
+              const int mb = q4 * MQ + h * NQ + mq2;           // member of the thread's run
+              const uint32_t r = rb0 + mb;
+              uint32_t c = pass_search<A>(row, piv, __umulhi(rw[h * NQ + mq2], Q));   // floor(r Q / 2^32) against P
+              if (Q == 0) c = r;                                                  // an all-zero group keeps its particles
+              const uint32_t pc = base + (c << log2sig);
+              const uint32_t src = (j == 0) ? pc : (uint32_t)anc_old[pc];
+              if (!last) {
+                if (packed) {
+                  if constexpr (MB >= 8) pk[mb >> 1] |= src << (16 * (mb & 1));
+                } else {
+                  anc_new[base + (r << log2sig)] = (uint16_t)src;
+                }
+              } else {
+                float xh[D], xo[D];
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) xh[cc] = s_x[cc * TP + pass_xpad(src)];
+                if (mut) {
+                  mutate<D, KIND>(mp, xh, z + mq2 * D, xo);
+                } else {
+#pragma unroll
+                  for (int cc = 0; cc < D; ++cc) xo[cc] = xh[cc];
+                }
+                const uint32_t i = i0 + (r << log2sk);
+#pragma unroll
+                for (int cc = 0; cc < D; ++cc) X[(size_t)cc * N + i] = xo[cc];
+              }
+            }
+          }
+        }
+        if constexpr (MB >= 8) {
+          if (packed) {
+            uint4* dst = reinterpret_cast<uint4*>(anc_new + base + rb0);   // 16-byte aligned: base + rb0 is a multiple of 8
+#pragma unroll
+            for (int q = 0; q < NPK / 4; ++q) dst[q] = make_uint4(pk[4 * q], pk[4 * q + 1], pk[4 * q + 2], pk[4 * q + 3]);
           }
         }
       }

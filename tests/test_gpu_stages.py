@@ -13,10 +13,12 @@ pytestmark = pytest.mark.gpu
 # radix <= 32 share a launch while their tile fits), or m without fusion
 @pytest.mark.parametrize("name,model,radices,T,launches", [
     ("lg_radix2", S.lg_scalar(), (2,) * 10, 5, 1),
-    ("sv_group", S.sv_model(), (16, 16, 4), 5, 2),
-    ("lg4_group", S.lg_dense(4, seed=3), (8, 8, 4), 4, 2),
+    ("sv_group", S.sv_model(), (16, 16, 4), 5, 3),            # N < 2^16, 2 of 3 launches: not fused
+    ("sv_mixed_radices", S.sv_model(), (32, 32, 16, 4), 3, 3),
+    ("lg4_group", S.lg_dense(4, seed=3), (8, 8, 4), 4, 3),
+    ("lg4_two_launches", S.lg_dense(4, seed=3), (8,) * 5, 3, 2),
     ("lg8_group", S.lg_dense(8, seed=4), (32, 32), 3, 1),
-    ("lg8_two_launches", S.lg_dense(8, seed=6), (32, 32, 4), 3, 2),
+    ("lg8_two_launches", S.lg_dense(8, seed=6), (32, 32, 8, 8), 2, 2),
     ("sv_three_digits", S.sv_model(), (16, 16, 16, 16), 3, 2),
     ("lg3_radix4", S.lg_dense(3, seed=7), (4,) * 7, 3, 2),
     ("lg1_mixed_tile", S.lg_scalar(), (3, 5, 7), 5, 3),
@@ -43,7 +45,7 @@ def test_all_stages_lockstep(bfpf, name, model, radices, T, launches, per_launch
 
 @pytest.mark.parametrize("model,radices,T", [
     (S.sv_model(), (16,) * 5, 6),                 # fused launches on digits {0, 1, 2} and {3, 4}
-    (S.lg_dense(8, seed=4), (32, 32, 32), 4),     # {0, 1} and {2}; groups over 16 lanes
+    (S.lg_dense(8, seed=4), (32, 32, 8, 8), 3),   # {0, 1} and {2, 3}; groups over 16 and 4 lanes
     (S.lg_scalar(), (4,) * 9, 4),                 # {0 .. 5} and {6, 7, 8}
 ])
 def test_fused_launches_equal_one_launch_per_stage(bfpf, model, radices, T):
