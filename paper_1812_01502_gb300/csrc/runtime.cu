@@ -601,7 +601,8 @@ bool plan_passes(Plan& pl, const int32_t* radices, int m) {
     while (fill * 2u <= pl.N / 512u) fill *= 2u;
     const bool whole = (uint64_t)S * B <= Tmax;           // L = s_k0: the tile is an index range
     const uint32_t L = whole ? S : std::max(16u, std::min(Tmax / B, fill / B));
-    const uint32_t T = whole ? std::max(S * B, std::min(Tmax, fill)) : L * B;
+    // (at least 4: the tile is loaded in runs of 4 consecutive particles)
+    const uint32_t T = whole ? std::max({4u, S * B, std::min(Tmax, fill)}) : L * B;
     g.k0 = (uint32_t)k0;
     g.J = J;
     g.pass = (uint32_t)np;

@@ -21,6 +21,7 @@ pytestmark = pytest.mark.gpu
     ("lg8_two_launches", S.lg_dense(8, seed=6), (32, 32, 8, 8), 2, 2),
     ("sv_three_digits", S.sv_model(), (16, 16, 16, 16), 3, 2),
     ("lg3_radix4", S.lg_dense(3, seed=7), (4,) * 7, 3, 2),
+    ("lg1_lone_radix2", S.lg_scalar(), (2, 4, 4, 4, 4), 4, 2),  # a one-digit launch of 2 on a tile of 4
     ("lg1_mixed_tile", S.lg_scalar(), (3, 5, 7), 5, 3),
     ("lg2_tile", S.lg_dense(2, seed=5), (64, 16), 4, 2),
     ("sv_wide", S.sv_model(), (300, 4), 4, 2),
