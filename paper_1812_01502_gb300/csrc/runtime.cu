@@ -587,8 +587,16 @@ bool plan_passes(Plan& pl, const int32_t* radices, int m) {
     const uint32_t A = (uint32_t)radices[k0];
     const uint32_t S = pl.geom[k0].s;
     auto fits = [&](uint64_t B) { return B <= Tmax && ((uint64_t)S * B <= Tmax || Tmax / B >= 16u); };
+    // A launch takes another digit only while its tiles stay within cap
+    // particles, so that populations above 1024 keep at least 16 tiles (thread
+    // blocks): one block running a dozen stages on 4096 particles took 48 us a
+    // step where two launches of 16 blocks took 25 us (1-D, radix 2).
+    uint32_t cap = 1024;
+    while (cap * 2u <= pl.N / 16u) cap *= 2u;
+    cap = std::min(cap, Tmax);
+    auto grows = [&](uint64_t B) { return fits(B) && ((uint64_t)S * B <= cap || 16u * B <= cap); };
     uint32_t J = 1, B = A;
-    while (k0 + (int)J < m && (uint32_t)radices[k0 + J] == A && fits((uint64_t)B * A)) {
+    while (k0 + (int)J < m && (uint32_t)radices[k0 + J] == A && grows((uint64_t)B * A)) {
       B *= A;
       ++J;
     }
@@ -599,7 +607,9 @@ bool plan_passes(Plan& pl, const int32_t* radices, int m) {
     // about 512 tiles (small populations: more thread blocks).
     uint32_t fill = 1;
     while (fill * 2u <= pl.N / 512u) fill *= 2u;
-    const bool whole = (uint64_t)S * B <= Tmax;           // L = s_k0: the tile is an index range
+    // L = s_k0 (the tile is an index range) unless that tile would pass the cap
+    // and L < s_k0 keeps within it
+    const bool whole = (uint64_t)S * B <= cap || ((uint64_t)S * B <= Tmax && 16u * B > cap);
     const uint32_t L = whole ? S : std::max(16u, std::min(Tmax / B, fill / B));
     // (at least 4: the tile is loaded in runs of 4 consecutive particles)
     const uint32_t T = whole ? std::max({4u, S * B, std::min(Tmax, fill)}) : L * B;
