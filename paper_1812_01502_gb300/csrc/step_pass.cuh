@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(kBlock, D == 1 ? 3 : 2) step_pass_kernel(const
   constexpr int M = A / G;                     // members per lane there
   constexpr int MQ = A < 4 ? A : 4;            // members per draw unit (one Philox block)
   constexpr int RS = pass_row_stride(A);
-  constexpr int NPV = A <= 4 ? A : A / 4;      // words loaded per unit for the search (pivots incl. Q)
+  constexpr int NPV = A <= 4 ? A : A / 4;      // row words a thread loads for its searches (pivots incl. Q)
   // members per thread in the draw phase: up to 16, so that a full tile
   // still gives every thread of the block some (4096 / 16 = 256 at d = 1)
   constexpr int MBT = (int)(pass_tile_max(D) / (uint32_t)kBlock);

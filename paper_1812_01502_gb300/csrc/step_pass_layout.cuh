@@ -53,8 +53,8 @@ __host__ __device__ constexpr int pass_lanes(int D, int A) {
 }
 
 // Padded index of tile position pos in a state row of the shared tile: one
-// spare word per 32 keeps the strided reads of the weighting stage (lanes
-// A positions apart) on distinct banks.
+// spare word per 32 keeps reads of lanes A positions apart (the weighting
+// stage, when a lane's members are fewer than four) on distinct banks.
 __host__ __device__ constexpr uint32_t pass_xpad(uint32_t pos) { return pos + (pos >> 5); }
 
 struct PassSmem {
