@@ -14,6 +14,8 @@ pytestmark = pytest.mark.gpu
     ("tile_mixed", S.lg_dense(3, seed=2), (3, 5, 7), {}),
     ("global", S.lg_scalar(), (1 << 14,), {}),
     ("all_stages", S.sv_model(), (8, 8, 4), {"all_stages": True}),
+    ("all_stages_one_fused_launch", S.lg_scalar(), (2,) * 10, {"all_stages": True}),
+    ("all_stages_three_fused_launches", S.sv_model(), (32, 32, 16, 4), {"all_stages": True}),
     ("adaptive_rot", S.lg_dense(2, seed=3), (8, 8, 4), {"adaptive": True, "ess_threshold": 0.8, "rotate": True}),
     ("airpf2", S.sv_model(), (32, 64), {"islands": "modified", "adaptive": True, "ess_threshold": 0.5}),
     ("digit_sets", S.lg_scalar(), (16, 2, 2, 2, 2), {"digit_sets": True}),

@@ -80,9 +80,13 @@ def test_fused_launches_equal_one_launch_per_stage(bfpf, model, radices, T):
     b.close()
 
 
-def test_all_stages_graph_equals_steps(bfpf):
-    """Chunks replayed from CUDA graphs (m launches per step) equal single steps."""
-    model, radices = S.sv_model(), (16, 8, 4)
+@pytest.mark.parametrize("model,radices", [
+    (S.sv_model(), (16, 8, 4)),              # one launch per stage
+    (S.lg_scalar(), (2,) * 10),              # one fused launch per step
+    (S.sv_model(), (32, 32, 16, 4)),         # three fused launches per step
+])
+def test_all_stages_graph_equals_steps(bfpf, model, radices):
+    """Chunks replayed from CUDA graphs (every launch of a step) equal single steps."""
     N = int(np.prod(radices))
     y = S.simulate(model, 40, seed=29)[1]
     a = bfpf.ButterflyFilter(model, N, radices, 31, all_stages=True, chunk_len=8)
