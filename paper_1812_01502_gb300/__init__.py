@@ -160,7 +160,9 @@ class ButterflyFilter:
     """A filter handle: N = prod(radices) particles, digit k = n mod m interacts at step n.
 
     all_stages=True runs every stage of Algorithm 3 in each step instead
-    (digits 0..m-1 in turn; m launches per step).  adaptive=True is fully
+    (digits 0..m-1 in turn; consecutive digits of one radix share a launch
+    where their particles fit one shared-memory tile, else m launches per
+    step; describe() lists them).  adaptive=True is fully
     adapted augmented resampling: stages run while the ESS is below
     ``ess_threshold`` (optionally from a rotated start, ``rotate``).
     islands="modified" (or "plain") is AIRPF with radices (M, m): m islands of
