@@ -802,6 +802,8 @@ def schedules_leg(bf, w, dev, flush, K=30, W=3):
     d, N, m = w.model.d, w.N, len(w.radices)
     out = {}
     for name, kw in (("all_stages", {"all_stages": True}),
+                     # the same schedule with one launch per stage (no fused launches), for comparison
+                     ("all_stages_per_launch", {"all_stages": True, "extra_flags": bf.PF_TEST_STAGE_PER_LAUNCH}),
                      ("adaptive_0.5", {"adaptive": True, "ess_threshold": 0.5}),
                      ("adaptive_all", {"adaptive": True, "ess_threshold": 1.5})):
         f = bf.ButterflyFilter(w.model, N, w.radices, w.filter_seed, device=dev, **kw)
